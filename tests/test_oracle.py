@@ -1,0 +1,366 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formulas: they check it against published
+test vectors, closed forms, invariants, finite differences, brute force, and
+independent library routines (torch autograd, torch.optim.Adam, scipy).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2608_12235_b300 import inputs
+
+
+# --------------------------------------------------------------- generators
+def test_splitmix64_published_vector(orc):
+    # First outputs of SplitMix64 seeded with 0, as published with the
+    # reference implementation (Vigna, splitmix64.c) and used in xoshiro seeding.
+    assert orc.splitmix64_at(0, 0) == 0xE220A8397B1DCDAF
+    assert orc.splitmix64_at(0, 1) == 0x6E789E6AA1B965F4
+    assert orc.splitmix64_at(0, 2) == 0x06C45D188009454F
+
+
+def test_uniform_positions(orc):
+    from scipy.stats import kstest
+    x = orc.init_positions(7, 20000, L=[1.0, 2.0, 0.5])
+    assert (x >= 0).all() and (x[:, 0] < 1).all() and (x[:, 1] < 2).all() and (x[:, 2] < 0.5).all()
+    for a, L in enumerate([1.0, 2.0, 0.5]):
+        assert kstest(x[:, a] / L, "uniform").pvalue > 1e-3
+    # distinct seeds give distinct streams
+    assert not np.array_equal(orc.init_positions(1, 10), orc.init_positions(2, 10))
+
+
+def test_diameter_quantiles():
+    from scipy import stats
+    n = 1000
+    u = (np.arange(n) + 0.5) / n
+    # lognormal: ln(D)/alpha are the quantiles of a standard normal truncated to [-a, a]
+    alpha, S = 0.5, 10.0
+    a = math.log(S) / (2 * alpha)
+    D = inputs.lognormal(n, alpha, S)
+    np.testing.assert_allclose(np.log(D) / alpha, stats.truncnorm.ppf(u, -a, a), rtol=1e-9, atol=1e-9)
+    assert D.max() / D.min() <= S
+    # power law D^p on [1, S]: CDF closed form
+    D = inputs.power_law(n, -3.0, 20.0)
+    F = (D ** -2.0 - 1.0) / (20.0 ** -2.0 - 1.0)
+    np.testing.assert_allclose(F, u, rtol=1e-12)
+    # Weibull on [1/sqrt S, sqrt S], lambda = sqrt S: truncated CDF
+    S, k = 100.0, 1.5
+    D = inputs.weibull(n, k, S)
+    wb = stats.weibull_min(k, scale=math.sqrt(S))
+    Ft = (wb.cdf(D) - wb.cdf(1 / math.sqrt(S))) / (wb.cdf(math.sqrt(S)) - wb.cdf(1 / math.sqrt(S)))
+    np.testing.assert_allclose(Ft, u, rtol=1e-9)
+
+
+# --------------------------------------------------------------- primitives
+def test_tree_sum(orc):
+    rng = np.random.default_rng(0)
+    for n in [0, 1, 2, 3, 5, 8, 1000, 4097]:
+        a = rng.standard_normal(n)
+        s = orc.tree_sum(a)
+        assert abs(s - math.fsum(a)) <= 1e-13 * max(1.0, np.abs(a).sum())
+    # integer-valued data is summed exactly in any order
+    a = rng.integers(-1000, 1000, 777).astype(np.float64)
+    assert orc.tree_sum(a) == a.sum()
+    # the shape is the zero-padded pairwise tree: with n = 3 it is (a0 + a1) + a2
+    big = 2.0 ** 53
+    assert orc.tree_sum([big, 1.0, 1.0]) == (big + 1.0) + 1.0 == big
+    assert orc.tree_sum([1.0, 1.0, big]) == big + 2.0
+    assert orc.tree_sum([1.0, big, 1.0, 1.0]) == (1.0 + big) + 2.0
+
+
+def test_cbrt(orc):
+    rng = np.random.default_rng(1)
+    for a in np.concatenate([10.0 ** rng.uniform(-30, 30, 2000), [1.0, 8.0, 27.0, 0.125]]):
+        c = orc.cbrt(a)
+        assert abs(c - np.cbrt(a)) <= 2 * np.spacing(np.cbrt(a))
+    assert orc.cbrt(27.0) == 3.0 and orc.cbrt(0.125) == 0.5 and orc.cbrt(64.0) == 4.0
+
+
+def test_kappa0_sets_phi0(orc):
+    D0 = inputs.lognormal(500, 0.5, 10.0)
+    k = orc.kappa0(D0, 1.0, 0.05)
+    assert abs(orc.phi(D0, 1.0, k) - 0.05) < 1e-14
+    assert abs(math.pi / 6 * np.sum((k * D0) ** 3) - 0.05) < 1e-14
+    D0 = np.ones(100)
+    k2 = orc.kappa0(D0, [2.0, 3.0], 0.3, d=2)
+    assert abs(math.pi / 4 * 100 * k2 ** 2 / 6.0 - 0.3) < 1e-14
+
+
+def test_n_trig_eq_trigger(orc):
+    # Eq. trigger: 4000 Y + X sqrt(N d) - 2000; hand-evaluated for d = 3
+    assert orc.n_trig(1000, 3, 2, 9) == pytest.approx(6000 + 9 * 54.772255750516614, rel=1e-15)
+    assert orc.n_trig(10 ** 6, 3, 2, 9) == pytest.approx(21588.457268119896, rel=1e-14)
+    assert orc.n_trig(10 ** 6, 3, 3, 24) == pytest.approx(51569.21938165305, rel=1e-14)
+
+
+# --------------------------------------------------------------- Eq. energy
+def _two(r, D=(1.0, 1.0), L=10.0):
+    x = np.array([[5.0, 5.0, 5.0], [5.0 + r, 5.0, 5.0]])
+    return x, np.array(D, dtype=float), L
+
+
+def test_two_spheres_closed_form(orc):
+    x, D0, L = _two(0.9)
+    mu = 0.01
+    E, g, dk, md = orc.energy_grad(x, D0, L, kappa=1.0, mu=mu)
+    # delta = 1 - 0.9/1 = 0.1: E = 0.5 * 0.01 - mu * 2
+    assert E == pytest.approx(0.005 - 2 * mu, rel=1e-14)
+    # |dE/dx| = eps delta / d = 0.1, pushing the pair apart
+    np.testing.assert_allclose(g, [[0.1, 0, 0], [-0.1, 0, 0]], atol=1e-15)
+    # dE/dkappa = eps delta (1 - delta)/kappa - mu sum D = 0.09 - 2 mu
+    assert dk == pytest.approx(0.09 - 2 * mu, rel=1e-14)
+    assert md == pytest.approx(0.1, rel=1e-14)
+    # unequal sizes and kappa != 1: d = kappa (D1 + D2)/2 = 0.5 * 3 / 2 = 0.75
+    x, D0, L = _two(0.6, D=(1.0, 2.0))
+    E, g, dk, md = orc.energy_grad(x, D0, L, kappa=0.5, mu=0.0)
+    delta = 1 - 0.6 / 0.75
+    assert E == pytest.approx(0.5 * delta ** 2, rel=1e-14)
+    assert g[0, 0] == pytest.approx(delta / 0.75, rel=1e-14)
+    assert dk == pytest.approx(delta * (1 - delta) / 0.5, rel=1e-14)
+
+
+def test_touching_and_separated_pairs_count_nothing(orc):
+    for r in (1.0, 1.2, 3.0):
+        x, D0, L = _two(r)
+        E, g, dk, md = orc.energy_grad(x, D0, L, kappa=1.0, mu=0.3)
+        assert E == -0.3 * 2.0 and dk == -0.3 * 2.0 and md == 0.0
+        assert not g.any()
+
+
+def test_three_collinear_superposition(orc):
+    x = np.array([[4.0, 5, 5], [4.9, 5, 5], [5.7, 5, 5]])
+    D0 = np.ones(3)
+    E, g, dk, md = orc.energy_grad(x, D0, 10.0, kappa=1.0, mu=0.0)
+    d1, d2 = 1 - 0.9, 1 - 0.8
+    assert E == pytest.approx(0.5 * (d1 ** 2 + d2 ** 2), rel=1e-13)
+    np.testing.assert_allclose(g[:, 0], [d1, -d1 + d2, -d2], rtol=1e-13)
+    assert dk == pytest.approx(d1 * (1 - d1) + d2 * (1 - d2), rel=1e-13)
+    assert md == pytest.approx(d2, rel=1e-13)
+
+
+def test_periodic_minimum_image(orc):
+    # the pair overlaps through the boundary only
+    x = np.array([[0.05, 0.5, 0.5], [0.95, 0.5, 0.5]])
+    E, g, dk, md = orc.energy_grad(x, np.ones(2), 1.0, kappa=0.2, mu=0.0)
+    delta = 1 - 0.1 / 0.2
+    assert E == pytest.approx(0.5 * delta ** 2, rel=1e-12)
+    assert g[0, 0] < 0 < g[1, 0]  # particle 0 is pushed towards -x, across the wall
+
+
+def _random_state(orc, n=300, phi=0.5, S=5.0, seed=3):
+    D0 = inputs.lognormal(n, 0.4, S)
+    k = orc.kappa0(D0, 1.0, phi)
+    x = orc.init_positions(seed, n)
+    return x, D0, k
+
+
+def test_newton_third_law_and_translation(orc):
+    x, D0, k = _random_state(orc)
+    E, g, dk, md = orc.energy_grad(x, D0, 1.0, k, 0.01)
+    assert md > 0.1
+    assert np.abs(g.sum(0)).max() <= 1e-13 * np.abs(g).sum()
+    E2, g2, _, _ = orc.energy_grad(np.mod(x + [0.3, 0.7, 0.11], 1.0), D0, 1.0, k, 0.01)
+    assert E2 == pytest.approx(E, rel=1e-11)
+    np.testing.assert_allclose(g2, g, rtol=1e-8, atol=1e-9 * np.abs(g).max())
+
+
+def test_uniform_scaling_invariance(orc):
+    x, D0, k = _random_state(orc)
+    E, g, _, _ = orc.energy_grad(x, D0, 1.0, k, 0.0)
+    lam = 3.0
+    E2, g2, _, _ = orc.energy_grad(x * lam, D0, lam, k * lam, 0.0)
+    assert E2 == pytest.approx(E, rel=1e-12)
+    np.testing.assert_allclose(g2 * lam, g, rtol=1e-9, atol=1e-12 * np.abs(g).max())
+
+
+def test_central_finite_differences(orc):
+    x, D0, k = _random_state(orc, n=60, phi=0.6, seed=11)
+    mu = 0.02
+    E, g, dk, _ = orc.energy_grad(x, D0, 1.0, k, mu)
+    rng = np.random.default_rng(0)
+    h = 1e-7
+    for _ in range(20):
+        i, a = rng.integers(60), rng.integers(3)
+        if g[i, a] == 0.0:
+            continue
+        xp, xm = x.copy(), x.copy()
+        xp[i, a] += h
+        xm[i, a] -= h
+        fd = (orc.energy_grad(xp, D0, 1.0, k, mu)[0] - orc.energy_grad(xm, D0, 1.0, k, mu)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i, a], rel=2e-5, abs=1e-6 * np.abs(g).max())
+    hk = 1e-7 * k
+    fd = (orc.energy_grad(x, D0, 1.0, k + hk, mu)[0] - orc.energy_grad(x, D0, 1.0, k - hk, mu)[0]) / (2 * hk)
+    assert fd == pytest.approx(dk, rel=1e-5)
+
+
+def _torch_energy(x, D0, L, kappa, mu):
+    n = x.shape[0]
+    i, j = torch.triu_indices(n, n, 1)
+    dx = x[i] - x[j]
+    dx = dx - L * torch.round(dx / L)
+    r = torch.sqrt((dx * dx).sum(1))
+    d = kappa * 0.5 * (D0[i] + D0[j])
+    delta = 1 - r / d
+    return 0.5 * torch.sum(torch.clamp(delta, min=0) ** 2) - mu * kappa * D0.sum()
+
+
+def test_torch_autograd_reference(orc):
+    x, D0, k = _random_state(orc, n=64, phi=0.55, seed=5)
+    mu = 0.01
+    E, g, dk, _ = orc.energy_grad(x, D0, 1.0, k, mu)
+    xt = torch.tensor(x, dtype=torch.float64, requires_grad=True)
+    kt = torch.tensor(k, dtype=torch.float64, requires_grad=True)
+    Et = _torch_energy(xt, torch.tensor(D0), 1.0, kt, mu)
+    Et.backward()
+    assert E == pytest.approx(Et.item(), rel=1e-12)
+    np.testing.assert_allclose(g, xt.grad.numpy(), rtol=1e-10, atol=1e-12 * np.abs(g).max())
+    assert dk == pytest.approx(kt.grad.item(), rel=1e-11)
+
+
+def test_two_dimensional_disks(orc):
+    x = np.array([[1.0, 1.0], [1.8, 1.0]])
+    E, g, dk, md = orc.energy_grad(x, np.ones(2), [3.0, 3.0], kappa=1.0, mu=0.0, d=2)
+    assert E == pytest.approx(0.5 * 0.2 ** 2, rel=1e-13)
+    assert g.shape == (2, 2) and g[0, 0] == pytest.approx(0.2, rel=1e-13)  # descent pushes 0 towards -x
+
+
+# --------------------------------------------------------------- Adam
+def test_adam_matches_torch_optim(orc):
+    rng = np.random.default_rng(2)
+    n, steps = 50, 40
+    p0 = rng.standard_normal(n)
+    grads = rng.standard_normal((steps, n)) * 10.0 ** rng.uniform(-3, 3, (steps, 1))
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    b1 = b2 = 1.0
+    pt = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([pt], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(steps):
+        b1 *= 0.9
+        b2 *= 0.999
+        orc.adam_update(p, m, v, grads[t], 1e-2, b1, b2)
+        pt.grad = torch.tensor(grads[t])
+        opt.step()
+    np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_adam_constant_gradient_step(orc):
+    g = np.array([3.0, -0.5, 1e-3])
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    b1 = b2 = 1.0
+    for t in range(5):
+        b1 *= 0.9
+        b2 *= 0.999
+        before = p.copy()
+        orc.adam_update(p, m, v, g, 0.1, b1, b2)
+        np.testing.assert_allclose(before - p, 0.1 * g / (np.abs(g) + 1e-8), rtol=1e-13)
+
+
+def test_wrap(orc):
+    assert orc.wrap(-1e-20, 1.0) == 0.0  # -tiny + 1 rounds to 1, which maps to 0
+    assert orc.wrap(1.0, 1.0) == 0.0
+    assert orc.wrap(1.25, 1.0) == 0.25
+    assert orc.wrap(-0.25, 1.0) == 0.75
+    assert orc.wrap(0.5, 1.0) == 0.5
+
+
+# --------------------------------------------------------------- neighbour structure
+@pytest.mark.parametrize("n,sig,S,phi,sigma0", [(400, 0.5, 10.0, 0.3, 0.0), (600, 1.0, 100.0, 0.5, 0.002),
+                                                (300, 0.2, 3.0, 0.6, 0.01), (2000, 2.0, 5e4, 0.4, 1e-4)])
+def test_grid_list_equals_definition(orc, n, sig, S, phi, sigma0):
+    D0 = inputs.lognormal(n, sig, S)
+    kb = orc.kappa0(D0, 1.0, phi)
+    x = orc.init_positions(n + 17, n)
+    rp1, c1 = orc.list_brute(x, D0, 1.0, kb, 0.1, sigma0)
+    rp2, c2 = orc.list_grid(x, D0, 1.0, kb, 0.1, sigma0)
+    assert np.array_equal(rp1, rp2) and np.array_equal(c1, c2)
+    # symmetric, no self pairs
+    rows = np.repeat(np.arange(n), np.diff(rp1))
+    pairs = set(zip(rows.tolist(), c1.tolist()))
+    assert all((j, i) in pairs for i, j in pairs) and all(i != j for i, j in pairs)
+    # sampled rows by brute force
+    for i in (0, n // 2, n - 1):
+        assert np.array_equal(orc.row_brute(x, D0, 1.0, kb, 0.1, sigma0, i), c1[rp1[i]:rp1[i + 1]])
+
+
+def test_levels_and_cells_follow_definition(orc):
+    D0 = inputs.lognormal(3000, 1.5, 1e4)
+    kb, s, sg = 0.01, 0.1, 1e-5
+    lvl, rml = orc.levels(D0, kb, s, sg)
+    rho = np.array([orc.rho(d, kb, s, sg) for d in D0])
+    rmax = rho.max()
+    for i in range(0, 3000, 7):
+        k = int(lvl[i])
+        assert math.ldexp(rho[i], k) <= rmax and (k == 31 or math.ldexp(rho[i], k + 1) > rmax)
+    for k in range(len(rml)):
+        assert rml[k] == rho[lvl == k].max()
+        nk = orc.grid_n(1.0, rml[k])
+        assert nk & (nk - 1) == 0 and (nk == 1 or 1.0 / nk >= 2 * rml[k])
+        assert nk == 2 ** 19 or 1.0 / (2 * nk) < 2 * rml[k]
+    x = orc.init_positions(4, 3000)
+    key = orc.cell_keys(x, D0, 1.0, kb, s, sg)
+    assert np.array_equal((key >> np.uint64(57)).astype(int), lvl)
+    for i in range(0, 3000, 11):
+        nk = orc.grid_n(1.0, rml[int(lvl[i])])
+        c = [int((int(key[i]) >> sh) & (2 ** 19 - 1)) for sh in (0, 19, 38)]
+        assert c == [min(int(math.floor(x[i, a] * nk)), nk - 1) for a in range(3)]
+
+
+def test_list_superset_and_list_independence(orc):
+    x, D0, k = _random_state(orc, n=500, phi=0.55, S=20.0, seed=9)
+    rp, col = orc.list_grid(x, D0, 1.0, k, 0.1, 0.001)
+    Eb, gb, dkb, mdb = orc.energy_grad(x, D0, 1.0, k, 0.01)
+    El, gl, dkl, mdl = orc.energy_grad(x, D0, 1.0, k, 0.01, rowptr=rp, col=col)
+    assert Eb == El and dkb == dkl and mdb == mdl and np.array_equal(gb, gl)
+    # a larger skin lists more pairs and changes nothing
+    rp2, col2 = orc.list_grid(x, D0, 1.0, k, 0.3, 0.01)
+    assert col2.size > col.size
+    E2, g2, dk2, md2 = orc.energy_grad(x, D0, 1.0, k, 0.01, rowptr=rp2, col=col2)
+    assert E2 == Eb and dk2 == dkb and np.array_equal(g2, gb)
+
+
+# --------------------------------------------------------------- shrink and phi
+def test_shrink_to_contact(orc):
+    x, D0, k = _random_state(orc, n=400, phi=0.55, S=8.0, seed=13)
+    rp, col = orc.list_grid(x, D0, 1.0, k, 0.1, 0.0)
+    kc = orc.shrink_kappa(x, D0, 1.0, k, rp, col)
+    assert kc < k
+    _, _, _, md = orc.energy_grad(x, D0, 1.0, kc, 0.0)
+    assert md == 0.0
+    # one pair is exactly in contact: a hair larger kappa overlaps
+    _, _, _, md2 = orc.energy_grad(x, D0, 1.0, kc * (1 + 1e-12), 0.0)
+    assert 0 < md2 < 1e-11
+    # without overlaps kappa is kept
+    assert orc.shrink_kappa(x, D0, 1.0, kc * 0.5, rp, col) == kc * 0.5
+
+
+def test_phi_closed_form(orc):
+    assert orc.phi(np.ones(8), 2.0, 1.0) == pytest.approx(8 * math.pi / 6 / 8.0, rel=1e-15)
+    assert orc.phi(np.ones(4), [2.0, 2.0], 1.0, d=2) == pytest.approx(4 * math.pi / 4 / 4.0, rel=1e-15)
+
+
+# --------------------------------------------------------------- the protocol
+def test_run_reaches_the_stopping_criterion(orc):
+    D0 = inputs.lognormal(300, 0.5, 10.0)
+    r = orc.run(D0, seed=0)
+    assert r.stopped and r.max_delta < 5e-4 and r.kappa_c <= r.kappa
+    assert 0.6 < r.phi < 0.72
+    r2 = orc.run(D0, seed=0)
+    assert r2.phi == r.phi and r2.iters == r.iters and np.array_equal(r2.x, r.x)
+    # shrink removes the residual overlap: brute force finds none at kappa_c
+    assert orc.energy_grad(r.x, D0, 1.0, r.kappa_c, 0.0)[3] == 0.0
+    # rung budgets follow Eq. trigger with the minimum count: 2000-long rungs
+    assert r.iters >= 2000 + 3 * 2000 + 2 * 2 * 2000
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("alpha,S,phi_paper", [(0.10, 3.0, 0.641), (0.50, 116.0, 0.698)])
+def test_table1_small_rows(orc, alpha, S, phi_paper):
+    # Table I rows with N = 2000 (3D periodic, truncated lognormal).  The
+    # schedule constants are readings, so the pin is soft: within 0.012.
+    D0 = inputs.lognormal(2000, alpha, S)
+    r = orc.run(D0, seed=1)
+    assert r.stopped
+    assert abs(r.phi - phi_paper) < 0.012
