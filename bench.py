@@ -1,0 +1,282 @@
+"""Benchmark: inflation iterations/s and pair evaluations/s of the Adam-based
+protocol at N = 1e6, S = 5e5 (truncated lognormal, sigma_ln = 2), mixed
+precision beside binary64, from the same state.
+
+A step is `--iters-per-step` protocol iterations (pair energy/gradient, Adam
+on x and kappa, the stopping test, and whatever neighbour rebuilds the skin
+test asks for), continuing the real trajectory.  Before timing, the packing
+is densified from phi0 = 0.05 by `--densify` untimed iterations.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+
+Prints one JSON line.  Under torchrun every rank advances its own packing
+(seed = rank): independent packings shard with no collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "lognormal-n1e6-s5e5": dict(kind="lognormal", N=1_000_000, p=2.0, S=5e5),
+    "powerlaw-n1e5-s20": dict(kind="power_law", N=100_000, p=-3.0, S=20.0),
+    "lognormal-n1e3-s10": dict(kind="lognormal", N=1000, p=0.5, S=10.0),
+}
+METRIC = "inflation iters/s and pair-evals/s at N=1e6, S=5e5 (mixed vs FP64, same φ)"
+
+
+def diameters(w):
+    from paper_2608_12235_b300 import inputs
+    if w["kind"] == "lognormal":
+        return inputs.lognormal(w["N"], w["p"], w["S"])
+    return inputs.power_law(w["N"], w["p"], w["S"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(D0, iters, phi=0.5, seed=0):
+    """The oracle as it stands, single thread, on a bounded sample of the same
+    workload: `iters` protocol iterations (one list build included) from
+    uniform positions at packing fraction `phi`."""
+    import oracle
+    from paper_2608_12235_b300 import rcp
+    cfg = rcp.rcp_config_default()
+    x = oracle.init_positions(seed, D0.size)
+    k = oracle.kappa0(D0, 1.0, phi)
+    k0 = oracle.kappa0(D0, 1.0, cfg.phi0)
+    m = oracle.moments(D0)
+    Dref = m[2] / m[1]
+    sigma0 = cfg.skin_abs * ((cfg.lr_x * k0) * Dref)
+    Neff = m[1] / (Dref ** 3)
+    mu = (((3.0 * cfg.delta_star0) * cfg.eps) * Neff) / (k * m[0])
+    t0 = time.perf_counter()
+    builds = oracle.sample_iterations(D0, x, k, mu, (cfg.lr_x * k) * Dref, cfg.lr_kappa * k, sigma0, iters)
+    dt = time.perf_counter() - t0
+    return iters / dt, dt, builds
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle on the same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    D0 = diameters(w)
+    cpu_baseline(D0, max(1, args.warmup))
+    rate, dt, builds = cpu_baseline(D0, max(1, args.steps))
+    sample = (f"{args.steps} protocol iterations (one neighbour-list build, {builds} builds in all) from uniform "
+              f"positions at phi=0.5, N={w['N']}, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iters/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "N": w["N"], "S": w["S"]},
+            "cpu_baseline": {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lognormal-n1e6-s5e5", choices=sorted(WORKLOADS))
+    ap.add_argument("--iters-per-step", type=int, default=100)
+    ap.add_argument("--densify", type=int, default=2000)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-iters", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2608_12235_b300 import rcp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    rcp.load()
+    stream = torch.cuda.Stream()
+    D0 = diameters(w)
+    ips = args.iters_per_step
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # ---- mixed precision: densify, warm up, time
+    p = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_MIXED)
+    rcp.rcp_set_stream(p.h, stream.cuda_stream)
+    p.run(max_iters=args.densify, shrink=False)
+    for _ in range(args.warmup):
+        p.run(max_iters=ips, shrink=False)
+    snap = p.state()
+    barrier_sync()
+    clk = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    it0 = snap[3].t
+    ev0.record(stream)
+    pairs_sum, rebuild0 = 0, None
+    launches = 0
+    for _ in range(args.steps):
+        r = p.run(max_iters=ips, shrink=False)
+        pairs_sum += r.pairs * ips
+        if rebuild0 is None:
+            rebuild0 = r.rebuilds
+    ev1.record(stream)
+    barrier_sync()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    x_end, _, _, s_end = p.state()
+    iters_done = s_end.t - it0
+    rebuilds = r.rebuilds
+    if world > 1:
+        t = torch.tensor([ms, float(iters_done)], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms, total_iters = float(tmax[0]), float(t[1])
+    else:
+        total_iters = float(iters_done)
+    value = total_iters / (ms / 1e3)
+    pair_evals = pairs_sum / 2.0 / (ms / 1e3) * world  # unordered pairs
+    phi_now = (np.pi / 6.0) * s_end.kappa ** 3 * float(np.sum(D0.astype(np.float64) ** 3))
+
+    # ---- roofline of the dominant kernel (pair kernel), events per launch
+    ms_pair, ms_iter, nl = rcp.rcp_profile(p.h, 50)
+    info = p.run(max_iters=1, shrink=False)
+    Pn = info.pairs
+    bytes_per_launch = 212.0 * w["N"] + 4.0 * Pn
+    gbs = bytes_per_launch / (ms_pair / nl / 1e3) / 1e9
+    peak, peak_kind = peaks()
+
+    # ---- binary64 at the same state
+    q = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_FP64)
+    rcp.rcp_set_stream(q.h, stream.cuda_stream)
+    rcp.rcp_load_state(q.h, *snap)
+    q.run(max_iters=ips, shrink=False)
+    barrier_sync()
+    ev0.record(stream)
+    s64_0 = q.state()[3].t
+    for _ in range(args.fp64_steps):
+        q.run(max_iters=ips, shrink=False)
+    ev1.record(stream)
+    barrier_sync()
+    ms64 = ev0.elapsed_time(ev1)
+    value64 = (q.state()[3].t - s64_0) / (ms64 / 1e3)
+    q.close()
+
+    # ---- end to end through the C ABI with host buffers
+    xs, ms_, vs_, ss_ = p.state()
+    xh = np.ascontiguousarray(xs)
+    t0 = time.perf_counter()
+    e_steps = max(1, min(args.steps, 5))
+    for _ in range(e_steps):
+        rcp.rcp_set_positions(p.h, xh, 0.0)  # host -> device: N x 3 binary64
+        p.run(max_iters=ips, shrink=False)
+        xh = p.positions()                    # device -> host: N x 3 binary64
+    e2e_dt = time.perf_counter() - t0
+    e2e_rate = e_steps * ips / e2e_dt * world
+
+    # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, builds = cpu_baseline(D0, args.cpu_iters)
+        cpu = {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_iters} protocol iterations incl. one neighbour-list build from uniform "
+                         f"positions at phi=0.5, N={w['N']} ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pair math, f64 state and reductions", "data": "synthetic",
+            "config": {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"],
+                       "precision": "mixed", "iters_per_step": ips, "densify_iters": args.densify,
+                       "phi_at_timing": round(phi_now, 4), "l2": "working set larger than L2 (>250 MB)"},
+            "pair_evals_per_s": pair_evals,
+            "fp64": {"value": value64, "unit": "iters/s", "speedup_mixed_over_fp64": value / value64},
+            "rebuilds_in_timed_region": rebuilds - (rebuild0 or 0), "listed_pairs": Pn,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": peak_kind, "traffic": None, "kernel": "k_pair_mixed",
+                         "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_pair / nl},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_rate, "unit": "iters/s", "h2d_bytes_per_step": 24 * w["N"],
+                    "d2h_bytes_per_step": 24 * w["N"]},
+            "gpu_launches": None,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    p.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

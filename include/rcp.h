@@ -1,0 +1,223 @@
+/*
+ * rcp.h -- C ABI of the B300 (sm_103a) implementation of the Adam-based
+ * Clarke-Wiley inflation protocol for random close packings of polydisperse
+ * spheres (arxiv 2608.12235, Sec. II and Appendix A).
+ *
+ * One handle holds one packing: N spheres of fixed relative diameters D_i^0
+ * in a periodic box, their positions x_i, the common diameter scale kappa
+ * (D_i = kappa D_i^0), the Adam moments, and the neighbour structure.  All
+ * device memory belongs to the handle; every pointer argument belongs to the
+ * caller and is only read or written during the call (copied, never kept).
+ *
+ * Conventions for every entry point:
+ *   - the return value is an rcp_status; RCP_OK on success.  On failure a
+ *     message is kept in the handle (rcp_last_error) and no output is written
+ *     unless stated;
+ *   - positions are row-major [N][3] doubles in the caller's particle order;
+ *   - work is issued on the handle's CUDA stream (rcp_set_stream); calls that
+ *     return host data synchronise that stream before returning;
+ *   - `on_device` = 1 means the pointer arguments of that call are device
+ *     pointers on the handle's device (outputs are then written
+ *     asynchronously on the handle's stream); 0 means host pointers;
+ *   - d must be 3: the kernels are written for three dimensions (the paper's
+ *     quantitative results are 3D periodic, Sec. II).
+ */
+#ifndef RCP_H
+#define RCP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rcp_ctx* rcp_handle;
+
+typedef enum {
+    RCP_OK = 0,
+    RCP_ERR_ARG = 1,         /* an argument is invalid (message says which) */
+    RCP_ERR_IMAGE = 2,       /* an interaction diameter reaches half a box edge: the
+                                largest sphere would meet its own periodic image (Sec. II) */
+    RCP_ERR_OOM = 3,         /* device allocation failed */
+    RCP_ERR_NAN = 4,         /* a non-finite energy or gradient appeared */
+    RCP_ERR_CAPACITY = 5,    /* a fixed-size internal table is too small */
+    RCP_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    RCP_ERR_MAXITER = 7,     /* the iteration cap was reached before the stopping criterion */
+    RCP_ERR_CUDA = 8,        /* a CUDA runtime call failed (message has its text) */
+    RCP_ERR_UNSUPPORTED = 9  /* valid but not implemented here (e.g. d != 3) */
+} rcp_status;
+
+typedef enum {
+    RCP_FP64 = 0,   /* all arithmetic in binary64, canonical summation order:
+                       bit-identical to the CPU oracle */
+    RCP_MIXED = 1   /* pair geometry in binary32 on fixed-point cell-relative
+                       offsets, Adam moments in binary32; positions, global
+                       reductions and the stopping test in binary64 */
+} rcp_precision;
+
+/* Optimiser and schedule settings.  Appendix A names the ingredients (Adam on
+ * the coordinates and kappa, mu annealed in rungs then cycled, a learning rate
+ * reduced over the run, rung budgets from Eq. trigger with a minimum count,
+ * the 5e-4 stop) but leaves the constants to its code; the defaults below are
+ * this implementation's readings. */
+typedef struct {
+    int       precision;    /* rcp_precision */
+    double    phi0;         /* initial packing fraction: sets kappa_0 (default 0.05) */
+    double    eps;          /* overlap stiffness epsilon of Eq. energy (1) */
+    double    beta1;        /* Adam first-moment decay (0.9) */
+    double    beta2;        /* Adam second-moment decay (0.999) */
+    double    adam_eps;     /* Adam denominator guard (1e-8) */
+    double    skin_s;       /* size-proportional Verlet skin fraction s (0.1) */
+    double    skin_theta;   /* rebuild when a sphere moved theta of its skin (0.5) */
+    double    skin_abs;     /* absolute skin sigma0 in units of the first rung's
+                               position learning rate (20) */
+    double    lr_x;         /* position learning rate in units of kappa D_ref,
+                               D_ref = sum D^4 / sum D^3 (1e-3) */
+    double    lr_kappa;     /* kappa learning rate in units of kappa (1e-3) */
+    double    delta_star0;  /* target mean overlap of the first rung (1e-2) */
+    double    tol;          /* stop when max fractional overlap < tol (5e-4, App. A) */
+    int       Y, X;         /* Eq. trigger constants: (2, 9) default, (3, 24) long */
+    long long n_min;        /* minimum rung budget (2000) */
+    int       n_down;       /* rungs after the first, mu falling tenfold each (3) */
+    int       n_cycles;     /* mu cycles after the descent (2) */
+    long long max_iters;    /* cap on Adam steps (2000000) */
+    int       chunk;        /* iterations per CUDA-graph replay (32) */
+} rcp_config;
+
+/* When rcp_run returns early. */
+typedef struct {
+    long long max_iters;    /* at most this many Adam steps in this call (0: no limit) */
+    double    max_seconds;  /* wall-clock limit for this call (0: none) */
+    int       shrink;       /* 1: shrink to contact once the stopping criterion fires */
+} rcp_stop;
+
+typedef struct {
+    long long iters;        /* Adam steps taken since creation */
+    long long rebuilds;     /* neighbour-structure builds since creation */
+    long long pairs;        /* listed ordered pairs at the last build */
+    int       stopped;      /* 1 once the stopping criterion of App. A has fired */
+    double    kappa;        /* current kappa */
+    double    max_delta;    /* max fractional overlap 1 - r/d at the last evaluation */
+    double    energy;       /* Eq. energy at the last evaluation */
+    double    kappa_c;      /* shrink-to-contact kappa (0 until computed) */
+    double    phi;          /* shrink-to-contact packing fraction (0 until computed) */
+    double    seconds;      /* wall time of this call */
+} rcp_result;
+
+/* Optimiser scalars, for checkpoint and resume (rcp_state / rcp_load_state). */
+typedef struct {
+    long long t;            /* Adam steps taken */
+    double    kappa, m_kappa, v_kappa;
+    double    b1, b2;       /* running products beta1^t, beta2^t */
+    int       rung;         /* index of the current rung of the schedule */
+    long long rung_start;   /* value of t when the current rung began */
+    double    kappa_rung;   /* kappa when the current rung began */
+    int       stopped;      /* 1 once the stopping criterion has fired */
+} rcp_scalars;
+
+/* Fill *cfg with the defaults listed above. */
+rcp_status rcp_config_default(rcp_config* cfg);
+
+/* Create a packing (Sec. II: "a prescribed list of N relative diameters, a
+ * spatial dimension, and a boundary geometry"; here the geometry is a
+ * periodic box).
+ *   diameters: host array of N positive finite relative diameters D_i^0;
+ *   N >= 1; d must be 3 (else RCP_ERR_UNSUPPORTED);
+ *   box: host array of d positive box edges;
+ *   seed: positions are uniform in the box, coordinate a of sphere i taken
+ *         from output 3 i + a of SplitMix64 seeded with `seed`;
+ *   cfg: NULL for the defaults;
+ *   kappa_0 is set so that the packing fraction equals cfg->phi0.
+ * On success *out receives the handle, which owns a new non-blocking stream
+ * on the current device. */
+rcp_status rcp_create(const double* diameters, long long N, int d, const double* box,
+                      unsigned long long seed, const rcp_config* cfg, rcp_handle* out);
+
+/* Free every resource of the handle.  NULL is accepted. */
+rcp_status rcp_destroy(rcp_handle h);
+
+/* Issue the handle's work on `stream` (a cudaStream_t of the handle's
+ * device; NULL selects the handle's own stream).  Captured graphs are
+ * re-captured on the next call that needs them. */
+rcp_status rcp_set_stream(rcp_handle h, void* stream);
+
+/* Replace the positions (N x 3, wrapped into the box) and optionally kappa
+ * (kappa > 0; pass a value <= 0 to keep it).  The neighbour structure is
+ * checked against the new state before the next evaluation. */
+rcp_status rcp_set_positions(rcp_handle h, const double* x, double kappa, int on_device);
+
+/* Build the size-stratified cell levels and the Verlet list at the current
+ * state (App. A uses a k-d tree rebuilt on accumulated displacement; this is
+ * the B300 replacement).  The list holds every ordered pair (i, j), i != j,
+ * whose minimum-image distance is below rho_i + rho_j, rho_i = kappa D_i^0
+ * (1/2 + s) + sigma0. */
+rcp_status rcp_build_neighbors(rcp_handle h);
+
+/* Evaluate Eq. energy at the current state with growth weight `mu`:
+ *   E = eps/2 sum_{i<j} delta_ij^2 Theta(delta_ij) - mu kappa sum_i D_i^0,
+ *   delta_ij = 1 - r_ij / d_ij, d_ij = kappa (D_i^0 + D_j^0)/2,
+ * its gradient grad_x[N][3] = dE/dx_i, dE/dkappa, and the largest fractional
+ * overlap max(0, max delta_ij).  Any output pointer may be NULL.  With
+ * on_device = 1 all non-NULL outputs are device pointers. */
+rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x,
+                           double* dE_dkappa, double* max_delta, int on_device);
+
+/* One Adam step (Kingma & Ba, Algorithm 1) on every coordinate and on kappa
+ * with the given gradient (grad_x[N][3], host or device per on_device) and
+ * step sizes lr_x (length units) and lr_kappa; positions are wrapped into the
+ * box.  Advances t and the bias-correction products. */
+rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa,
+                         double lr_x, double lr_kappa, int on_device);
+
+/* Run the protocol of App. A from the current state: the rung schedule, then
+ * the final rung until the max fractional overlap is below cfg.tol, then (if
+ * stop->shrink) shrink kappa to contact and compute phi.  Returns early when
+ * a limit in *stop is reached (stop may be NULL: no limits, shrink on); a
+ * later call resumes bit-exactly.  Returns RCP_ERR_MAXITER if cfg.max_iters
+ * is reached first.  *out (may be NULL) receives the summary. */
+rcp_status rcp_run(rcp_handle h, const rcp_stop* stop, rcp_result* out);
+
+/* Instrumented run: like rcp_run with stop = {iters, 0, 0}, but every
+ * iteration is launched on its own (no graph) with CUDA events around the
+ * pair kernel.  *ms_pair receives the summed pair-kernel time, *ms_iter the
+ * summed time of whole iterations (pair kernel, reductions, kappa step),
+ * *launches the number of pair-kernel launches timed.  The iterations are
+ * real: the state advances exactly as under rcp_run. */
+rcp_status rcp_profile(rcp_handle h, long long iters, double* ms_pair, double* ms_iter,
+                       long long* launches);
+
+/* Shrink to contact at the current state (Sec. II, App. A): kappa_c is the
+ * smaller of kappa and min_{i<j} r_ij / d_ij^0; phi is the solid-volume
+ * fraction at kappa_c.  Positions and kappa are not changed. */
+rcp_status rcp_shrink(rcp_handle h, double* kappa_c, double* phi);
+
+/* Copy the state to host arrays (any pointer may be NULL): x and the Adam
+ * moments m, v as [N][3] doubles (binary32 moments are widened), and the
+ * optimiser scalars. */
+rcp_status rcp_state(rcp_handle h, double* x, double* m, double* v, rcp_scalars* s);
+
+/* Restore a state written by rcp_state (host arrays; NULL keeps a part). */
+rcp_status rcp_load_state(rcp_handle h, const double* x, const double* m, const double* v,
+                          const rcp_scalars* s);
+
+/* Copy the current Verlet list to the host as CSR: rowptr[N+1] and col[P]
+ * with ascending columns per row.  *P receives the entry count; col is
+ * written only if P <= cap.  Builds the list first if none exists. */
+rcp_status rcp_neighbors(rcp_handle h, long long* rowptr, int* col, long long cap,
+                         long long* P);
+
+/* Copy the per-sphere cell keys of the last build: size class in bits 57-61,
+ * then the z, y, x cell indices of that class's grid in 19 bits each. */
+rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys);
+
+/* Number of spheres. */
+long long rcp_size(rcp_handle h);
+
+/* Static text of a status code. */
+const char* rcp_status_str(rcp_status s);
+
+/* Message of the last failure on this handle ("" if none). */
+const char* rcp_last_error(rcp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCP_H */

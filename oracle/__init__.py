@@ -104,6 +104,9 @@ def lib():
         L.orc_phi.restype = C.c_double
         L.orc_phi.argtypes = [_dp, C.c_long, C.c_int, _dp, C.c_double]
         L.orc_params_default.argtypes = [C.POINTER(Params)]
+        L.orc_sample_iterations.restype = C.c_long
+        L.orc_sample_iterations.argtypes = [C.POINTER(Params), _dp, C.c_long, _dp, C.c_double, C.c_double,
+                                            C.c_double, C.c_double, C.c_double, C.c_long]
         L.orc_run.restype = C.c_int
         L.orc_run.argtypes = [C.POINTER(Params), _dp, C.c_long, C.c_uint64, _dp, C.c_int,
                               C.POINTER(Result), C.c_void_p, C.c_long]
@@ -305,3 +308,16 @@ def run(D0, seed=0, x0=None, trace_len=0, **params) -> RunResult:
     return RunResult(res.iters, res.rebuilds, bool(res.stopped), res.kappa, res.max_delta,
                      res.energy, res.kappa_c, res.phi, x.reshape(n, p.d),
                      tr.reshape(-1, 4)[: min(trace_len, res.iters + 1)] if tr is not None else None)
+
+
+def sample_iterations(D0, x, kappa, mu, eta_x, eta_k, sigma0, iters, **params) -> int:
+    """`iters` protocol iterations from (x, kappa) at fixed rung values, for
+    timing the CPU baseline.  x (N x 3) is advanced in place.  Returns the
+    number of list builds."""
+    p = default_params(**params)
+    D0 = f64(D0)
+    b = lib().orc_sample_iterations(C.byref(p), D0, D0.size, x.reshape(-1), kappa, mu, eta_x, eta_k, sigma0,
+                                    iters)
+    if b < 0:
+        raise RuntimeError("periodic-image rule violated")
+    return int(b)

@@ -741,3 +741,60 @@ done:
     free(x); free(m); free(v); free(g); free(xb); free(rowptr); free(col);
     return status;
 }
+
+/* A bounded sample of the protocol for timing the CPU baseline: `iters`
+ * iterations of the loop body of orc_run (list build when the skin budget is
+ * spent, Eq. energy and gradient, Adam on x and kappa) from positions x at
+ * kappa, with fixed rung values mu, eta_x, eta_kappa and zero Adam moments.
+ * Returns the number of list builds, or -1 if the periodic-image rule fails. */
+long orc_sample_iterations(const orc_params* p, const double* D0, long n, double* x, double kappa,
+                           double mu, double eta_x, double eta_k, double sigma0, long iters)
+{
+    int d = p->d;
+    const double* L = p->L;
+    long nd = n * d;
+    double* m = (double*)calloc((size_t)nd, sizeof(double));
+    double* v = (double*)calloc((size_t)nd, sizeof(double));
+    double* g = (double*)malloc(sizeof(double) * (size_t)nd);
+    double* xb = (double*)malloc(sizeof(double) * (size_t)nd);
+    long cap = 64 * n + 1024;
+    long* rowptr = (long*)malloc(sizeof(long) * (size_t)(n + 1));
+    int* col = (int*)malloc(sizeof(int) * (size_t)cap);
+    double mk = 0.0, vk = 0.0, b1 = 1.0, b2 = 1.0, kb = kappa, E, dEdk, md;
+    double s = p->skin_s, th = p->skin_theta;
+    double Lmin = L[0];
+    for (int a = 1; a < d; ++a) if (L[a] < Lmin) Lmin = L[a];
+    long builds = 0;
+    int need = 1;
+    for (long t = 0; t < iters; ++t) {
+        if (need) {
+            double rmax = 0.0;
+            for (long i = 0; i < n; ++i) {
+                double q = orc_rho(D0[i], kappa, s, sigma0);
+                if (q > rmax) rmax = q;
+            }
+            if (!(4.0 * rmax < Lmin)) { builds = -1; break; }
+            build_list(x, D0, n, d, L, kappa, s, sigma0, &rowptr, &col, &cap);
+            memcpy(xb, x, sizeof(double) * (size_t)nd);
+            kb = kappa;
+            ++builds;
+            need = 0;
+        }
+        orc_energy_grad_list(x, D0, n, d, L, kappa, mu, p->eps, rowptr, col, &E, g, &dEdk, &md);
+        b1 = b1 * p->beta1;
+        b2 = b2 * p->beta2;
+        orc_adam_update(x, m, v, g, nd, eta_x, p->beta1, p->beta2, p->adam_eps, b1, b2);
+        for (long i = 0; i < n; ++i)
+            for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
+        orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);
+        if (kappa > kb * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) need = 1;
+        for (long i = 0; i < n && !need; ++i) {
+            double dx[3];
+            double r2 = min_image(&x[d * i], &xb[d * i], d, L, dx);
+            double lim = th * (s * kb * D0[i] + sigma0) * (1.0 - 1e-9);
+            if (r2 > lim * lim) need = 1;
+        }
+    }
+    free(m); free(v); free(g); free(xb); free(rowptr); free(col);
+    return builds;
+}

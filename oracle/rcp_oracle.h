@@ -112,6 +112,9 @@ void   orc_params_default(orc_params* p);
 int    orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
                double* x_io, int x_given, orc_result* res, double* trace, long trace_cap);
 
+long   orc_sample_iterations(const orc_params* p, const double* D0, long n, double* x, double kappa,
+                             double mu, double eta_x, double eta_k, double sigma0, long iters);
+
 #ifdef __cplusplus
 }
 #endif

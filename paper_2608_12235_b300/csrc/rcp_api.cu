@@ -1,0 +1,1048 @@
+// rcp_api.cu -- the C ABI (include/rcp.h): handle life cycle, the
+// neighbour-structure build, evaluation, the standalone Adam step, and the
+// host-side schedule controller that replays a captured CUDA graph of
+// `chunk` iterations per launch.
+//
+// Scalar schedule values (mu, learning rates, rung budgets) are computed on
+// the host from device-reduced sums, in the same binary64 expressions as the
+// definition (compiled with -ffp-contract=off); every per-particle and
+// per-pair operation runs in the kernels.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "rcp_internal.cuh"
+
+namespace {
+
+struct Rung {
+    double dstar, lrs;
+    long long budget;
+    int final_rung;
+};
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct rcp_ctx {
+    long long N = 0;
+    rcp_config cfg;
+    RcpConst c;
+    unsigned long long seed = 0;
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    char err[512] = {0};
+
+    // state
+    double* D0 = nullptr;
+    double4_32a* xA = nullptr;
+    double4_32a* xB = nullptr;
+    double4_32a* xb = nullptr;
+    double* m64 = nullptr;
+    double* v64 = nullptr;
+    float* m32 = nullptr;
+    float* v32 = nullptr;
+    MixRec* rA = nullptr;   // mixed-precision pair records (double-buffered)
+    MixRec* rB = nullptr;
+    MixRec* rb = nullptr;   // records at the last build
+    double* g = nullptr;      // [3N] gradient output / input buffer
+    double* part_e = nullptr; // block partials
+    double* part_k = nullptr;
+    double* part_e2 = nullptr;
+    double* part_k2 = nullptr;
+    double* xtmp = nullptr;   // [3N] staging for host copies
+    RcpCtl* ctl = nullptr;
+    RcpCtl* ctl_h = nullptr;  // pinned mirror
+
+    // neighbour structure
+    double* rho = nullptr;
+    int* lvl = nullptr;
+    unsigned long long* key = nullptr;
+    unsigned long long* key1 = nullptr;
+    unsigned long long* key2 = nullptr;
+    unsigned int* idx1 = nullptr;
+    unsigned int* idx2 = nullptr;
+    unsigned int* idx0 = nullptr;
+    const unsigned int* idx_sorted = nullptr;
+    unsigned long long* hkeys = nullptr;
+    uint2* hvals = nullptr;
+    unsigned long long hcap = 0;
+    unsigned int* cnt = nullptr;   // [N+1]
+    unsigned int* offs = nullptr;  // [N+1]
+    unsigned long long* pairs1 = nullptr;
+    unsigned long long* pairs2 = nullptr;
+    unsigned int* col = nullptr;
+    unsigned int* rowptr = nullptr;  // [N+1]
+    unsigned long long pcap = 0;
+    unsigned int* hist = nullptr;
+    unsigned long long hist_cap = 0;
+    unsigned int* scan_tmp = nullptr;
+    unsigned long long scan_tmp_cap = 0;
+    bool built = false;
+    unsigned long long P = 0;
+
+    // schedule
+    std::vector<Rung> rungs;
+    int rung = -1;
+    long long rung_start = 0;
+    double kappa_rung = 0.0;
+    double SD = 0, SD3 = 0, SD4 = 0, Dref = 0, Neff = 0, kappa0 = 0, sigma0 = 0;
+    double mu = 0, eta_x = 0, eta_k = 0;
+
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int gT = 0;
+    cudaStream_t g_stream = nullptr;
+    unsigned long long g_pcap = 0;
+};
+
+namespace {
+
+rcp_status fail(rcp_ctx* h, rcp_status s, const char* fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? RCP_ERR_OOM : RCP_ERR_CUDA,      \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKS(expr)                       \
+    do {                                \
+        rcp_status s_ = (expr);         \
+        if (s_ != RCP_OK) return s_;    \
+    } while (0)
+
+#define CKL()  CK(cudaPeekAtLastError())
+
+template <typename T>
+rcp_status dalloc(rcp_ctx* h, T** p, size_t count)
+{
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) count = 1;
+    CK(cudaMalloc((void**)p, sizeof(T) * count));
+    return RCP_OK;
+}
+
+int bits_for(unsigned long long v)  // bits needed to hold values < v (at least 1)
+{
+    int b = 1;
+    while (b < 63 && (1ull << b) < v) ++b;
+    return b;
+}
+
+rcp_status sync_ctl(rcp_ctx* h)
+{
+    CK(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(RcpCtl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RCP_OK;
+}
+
+// Tree sum of f(D0) (power 1, 3 or 4) into *dst (device), canonical order.
+rcp_status tree_sum_D(rcp_ctx* h, int power, double* dst)
+{
+    long long n = h->N;
+    unsigned int nb = rcp_ceil_div(n, RCP_TREE);
+    k_tree_terms<<<nb, RCP_TREE, 0, h->stream>>>(h->D0, n, power, h->part_e);
+    CKL();
+    double* a = h->part_e;
+    double* b = h->part_e2;
+    n = nb;
+    while (n > 1) {
+        nb = rcp_ceil_div(n, RCP_TREE);
+        k_tree_pass<<<nb, RCP_TREE, 0, h->stream>>>(a, n, b);
+        CKL();
+        std::swap(a, b);
+        n = nb;
+    }
+    CK(cudaMemcpyAsync(dst, a, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return RCP_OK;
+}
+
+// ---------------------------------------------------------------- scan / sort
+rcp_status ensure_scan_tmp(rcp_ctx* h, unsigned long long n)
+{
+    // totals of every recursion level
+    unsigned long long need = 0, m = n;
+    while (m > 4096) {
+        m = (m + 4095) / 4096;
+        need += m + 1;
+    }
+    need += 16;
+    if (need > h->scan_tmp_cap) {
+        CKS(dalloc(h, &h->scan_tmp, need));
+        h->scan_tmp_cap = need;
+    }
+    return RCP_OK;
+}
+
+// Exclusive scan of n unsigned ints (in may equal out).
+rcp_status scan_u32(rcp_ctx* h, const unsigned int* in, unsigned long long n, unsigned int* out,
+                    unsigned int* tmp)
+{
+    if (n == 0) return RCP_OK;
+    unsigned int nb = rcp_ceil_div(n, 4096);
+    if (nb == 1) {
+        k_scan_block<<<1, 1024, 0, h->stream>>>(in, (long long)n, out, nullptr);
+        CKL();
+        return RCP_OK;
+    }
+    unsigned int* totals = tmp;
+    k_scan_block<<<nb, 1024, 0, h->stream>>>(in, (long long)n, out, totals);
+    CKL();
+    CKS(scan_u32(h, totals, nb, totals, tmp + nb + 1));
+    k_scan_add<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(out, (long long)n, totals);
+    CKL();
+    return RCP_OK;
+}
+
+rcp_status ensure_hist(rcp_ctx* h, unsigned long long n)
+{
+    unsigned long long nb = (n + RCP_SORT_THREADS * RCP_SORT_ITEMS - 1) / (RCP_SORT_THREADS * RCP_SORT_ITEMS);
+    unsigned long long need = 256 * (nb > 0 ? nb : 1);
+    if (need > h->hist_cap) {
+        CKS(dalloc(h, &h->hist, need));
+        h->hist_cap = need;
+    }
+    return ensure_scan_tmp(h, need);
+}
+
+// LSD radix sort of (key, val) over the digit shifts given, stable.  Reads
+// `in` (kept intact), ping-pongs between b1 and b2; *result receives the
+// buffer holding the sorted keys (and *vres the values).
+rcp_status radix_sort(rcp_ctx* h, const unsigned long long* in, const unsigned int* vin, unsigned long long n,
+                      const std::vector<int>& shifts, unsigned long long* b1, unsigned int* v1,
+                      unsigned long long* b2, unsigned int* v2, const unsigned long long** result,
+                      const unsigned int** vres)
+{
+    CKS(ensure_hist(h, n));
+    const unsigned long long* src = in;
+    const unsigned int* vsrc = vin;
+    unsigned long long* dst = b1;
+    unsigned int* vdst = v1;
+    if (n == 0 || shifts.empty()) {
+        *result = in;
+        if (vres) *vres = vin;
+        return RCP_OK;
+    }
+    unsigned int nb = rcp_ceil_div(n, RCP_SORT_THREADS * RCP_SORT_ITEMS);
+    for (size_t p = 0; p < shifts.size(); ++p) {
+        k_radix_hist<<<nb, RCP_SORT_THREADS, 0, h->stream>>>(src, (long long)n, shifts[p], h->hist, nb);
+        CKL();
+        CKS(scan_u32(h, h->hist, 256ull * nb, h->hist, h->scan_tmp));
+        k_radix_scatter<<<nb, RCP_SORT_THREADS, 0, h->stream>>>(src, vsrc, (long long)n, shifts[p], h->hist, nb,
+                                                               dst, vsrc ? vdst : nullptr);
+        CKL();
+        src = dst;
+        vsrc = vsrc ? vdst : nullptr;
+        dst = (dst == b1) ? b2 : b1;
+        vdst = (vdst == v1) ? v2 : v1;
+    }
+    *result = src;
+    if (vres) *vres = vsrc;
+    return RCP_OK;
+}
+
+std::vector<int> field_shifts(int lo, int nbits)
+{
+    std::vector<int> s;
+    for (int b = 0; b < nbits; b += 8) s.push_back(lo + b);
+    return s;
+}
+
+// ---------------------------------------------------------------- build
+rcp_status ensure_pair_capacity(rcp_ctx* h, unsigned long long P)
+{
+    if (P <= h->pcap && h->pairs1) return RCP_OK;
+    unsigned long long cap = P + P / 4 + 1024;
+    CKS(dalloc(h, &h->pairs1, cap));
+    CKS(dalloc(h, &h->pairs2, cap));
+    CKS(dalloc(h, &h->col, cap));
+    h->pcap = cap;
+    return ensure_hist(h, cap > (unsigned long long)h->N ? cap : (unsigned long long)h->N);
+}
+
+rcp_status build(rcp_ctx* h)
+{
+    const long long N = h->N;
+    const unsigned int nbN = rcp_ceil_div(N, 256);
+    k_build_begin<<<1, 1, 0, h->stream>>>(h->ctl, h->sigma0);
+    k_rho<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho);
+    k_level<<<nbN, 256, 0, h->stream>>>(h->ctl, N, h->rho, h->lvl);
+    k_grid<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
+    CKL();
+    CKS(sync_ctl(h));
+    if (h->ctl_h->status == RCP_ERR_IMAGE)
+        return fail(h, RCP_ERR_IMAGE,
+                    "largest interaction diameter 4 rho_max = %.6g reaches the smallest box edge %.6g: a sphere "
+                    "would meet its own periodic image",
+                    4.0 * h->ctl_h->rho_lvl[0], h->c.Lmin);
+    int nlev = h->ctl_h->nlev;
+    int maxn[3] = {1, 1, 1};
+    for (int k = 0; k < nlev; ++k)
+        for (int a = 0; a < 3; ++a)
+            if (h->ctl_h->ng[k][a] > maxn[a]) maxn[a] = h->ctl_h->ng[k][a];
+    std::vector<int> shifts;
+    for (int a = 0; a < 3; ++a) {
+        int b = 0;
+        while ((1 << b) < maxn[a]) ++b;
+        for (int s : field_shifts(19 * a, b)) shifts.push_back(s);
+    }
+    {
+        int b = 0;
+        while ((1 << b) < nlev) ++b;
+        for (int s : field_shifts(57, b)) shifts.push_back(s);
+    }
+    k_cell_key<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->lvl, h->key, h->idx0);
+    CKL();
+    const unsigned long long* skeys = nullptr;
+    const unsigned int* sidx = nullptr;
+    CKS(radix_sort(h, h->key, h->idx0, (unsigned long long)N, shifts, h->key1, h->idx1, h->key2, h->idx2, &skeys,
+                   &sidx));
+    h->idx_sorted = sidx;
+    CK(cudaMemsetAsync(h->hkeys, 0xFF, sizeof(unsigned long long) * h->hcap, h->stream));
+    k_hash_heads<<<nbN, 256, 0, h->stream>>>(skeys, N, h->hkeys, h->hvals, h->hcap - 1);
+    CKL();
+    const int nbits = bits_for((unsigned long long)N);
+    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->hkeys,
+                                         h->hvals, h->hcap - 1, nullptr, h->cnt, nullptr, 0, nbits);
+    CKL();
+    CK(cudaMemsetAsync(h->cnt + N, 0, sizeof(unsigned int), h->stream));
+    CKS(scan_u32(h, h->cnt, (unsigned long long)N + 1, h->offs, h->scan_tmp));
+    unsigned int P32 = 0;
+    CK(cudaMemcpyAsync(&P32, h->offs + N, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long P = P32;
+    CKS(ensure_pair_capacity(h, P));
+    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->hkeys,
+                                         h->hvals, h->hcap - 1, h->offs, nullptr, h->pairs1, 1, nbits);
+    CKL();
+    std::vector<int> ps = field_shifts(0, nbits);
+    for (int s : field_shifts(nbits, nbits)) ps.push_back(s);
+    const unsigned long long* spairs = nullptr;
+    CKS(radix_sort(h, h->pairs1, nullptr, P, ps, h->pairs2, nullptr, h->pairs1, nullptr, &spairs, nullptr));
+    k_csr<<<rcp_ceil_div((P > (unsigned long long)N ? P : (unsigned long long)N) + 1, 256), 256, 0, h->stream>>>(
+        spairs, (long long)P, N, nbits, h->rowptr, h->col);
+    k_build_end<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb, P);
+    CKL();
+    if (h->cfg.precision == RCP_MIXED) {
+        k_to_fixed<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, h->rb);
+        CKL();
+    }
+    h->P = P;
+    h->built = true;
+    return RCP_OK;
+}
+
+// ---------------------------------------------------------------- evaluation
+unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_THREADS); }
+
+// Reduce the pair kernel's block partials to <= 8192 entries; returns the
+// buffers and count to hand to k_kappa_step.
+void prereduce(rcp_ctx* h, const double** pe, const double** pk, long long* nb)
+{
+    const double* a = h->part_e;
+    const double* b = h->part_k;
+    long long n = pair_blocks(h);
+    bool flip = false;
+    while (n > 8192) {
+        unsigned int g = rcp_ceil_div(n, RCP_TREE);
+        double* oa = flip ? h->part_e : h->part_e2;
+        double* ob = flip ? h->part_k : h->part_k2;
+        k_tree_pass2<<<g, RCP_TREE, 0, h->stream>>>(a, b, n, oa, ob);
+        a = oa;
+        b = ob;
+        n = g;
+        flip = !flip;
+    }
+    *pe = a;
+    *pk = b;
+    *nb = n;
+}
+
+size_t kappa_smem(long long nb)
+{
+    long long M = 1;
+    while (M < nb) M <<= 1;
+    return 2 * sizeof(double) * (size_t)M;
+}
+
+// One iteration (or one evaluation) on the stream; optional events bracket
+// the pair kernel (ev[0], ev[1]) and close the iteration (ev[2]).
+void launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
+{
+    const unsigned int nb = pair_blocks(h);
+    if (ev) cudaEventRecord(ev[0], h->stream);
+    if (h->cfg.precision == RCP_MIXED) {
+        k_pair_mixed<<<nb, RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m32, h->v32, h->rA,
+                                                              h->rB, h->rowptr, h->col, h->rb, h->part_e, h->part_k,
+                                                              mode, h->g);
+    } else {
+        k_pair64<<<nb, RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr,
+                                                          h->col, h->xb, h->part_e, h->part_k, mode, h->g);
+    }
+    if (ev) cudaEventRecord(ev[1], h->stream);
+    const double* pe;
+    const double* pk;
+    long long n;
+    prereduce(h, &pe, &pk, &n);
+    k_kappa_step<<<1, 1024, kappa_smem(n), h->stream>>>(h->ctl, h->c, pe, pk, n, mode);
+    if (ev) cudaEventRecord(ev[2], h->stream);
+}
+
+struct ProfileAcc {
+    double ms_pair = 0.0, ms_iter = 0.0;
+    long long launches = 0;
+    cudaEvent_t ev[3];
+};
+
+rcp_status ensure_list(rcp_ctx* h)
+{
+    if (!h->built) return build(h);
+    CKS(sync_ctl(h));
+    if (h->ctl_h->need_rebuild) return build(h);
+    return RCP_OK;
+}
+
+rcp_status capture_graph(rcp_ctx* h)
+{
+    if (h->gexec && h->gT == h->cfg.chunk && h->g_stream == h->stream && h->g_pcap == h->pcap) return RCP_OK;
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < h->cfg.chunk; ++t) launch_iteration(h, RCP_MODE_ADAM);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    h->gT = h->cfg.chunk;
+    h->g_stream = h->stream;
+    h->g_pcap = h->pcap;
+    return RCP_OK;
+}
+
+// ---------------------------------------------------------------- schedule
+// Rung table (reading of App. A): rung 0 lasts n_trig of Eq. trigger, every
+// later rung n_trig/4, both at least n_min; the target overlap falls tenfold
+// and the learning rate halves per rung of the descent; then n_cycles
+// cycles raise mu one decade and lower it back; the final rung has mu = 0,
+// half the learning rate, and runs until the stopping criterion.
+void build_rungs(rcp_ctx* h)
+{
+    const rcp_config& p = h->cfg;
+    double nt = (4000.0 * (double)p.Y + (double)p.X * std::sqrt((double)(h->N * 3LL))) - 2000.0;
+    long long b0 = (long long)std::ceil(nt);
+    if (b0 < p.n_min) b0 = p.n_min;
+    long long bq = (long long)std::ceil(nt / 4.0);
+    if (bq < p.n_min) bq = p.n_min;
+    h->rungs.clear();
+    double ds = p.delta_star0, lrs = 1.0;
+    h->rungs.push_back({ds, lrs, b0, 0});
+    for (int r = 1; r <= p.n_down; ++r) {
+        ds = ds / 10.0;
+        lrs = lrs * 0.5;
+        h->rungs.push_back({ds, lrs, bq, 0});
+    }
+    for (int cy = 0; cy < p.n_cycles; ++cy) {
+        h->rungs.push_back({ds * 10.0, lrs, bq, 0});
+        h->rungs.push_back({ds, lrs, bq, 0});
+    }
+    h->rungs.push_back({0.0, lrs * 0.5, p.max_iters, 1});
+}
+
+// Values of rung r given kappa at its start:
+//   mu = 3 delta* eps N_eff / (kappa_r sum D^0),  N_eff = sum D^3 / D_ref^3,
+//   eta_x = lr_x lrs kappa_r D_ref,  eta_kappa = lr_kappa lrs kappa_r.
+void rung_values(rcp_ctx* h, int r, double kr)
+{
+    const Rung& R = h->rungs[r];
+    h->mu = R.dstar > 0.0 ? (((3.0 * R.dstar) * h->cfg.eps) * h->Neff) / (kr * h->SD) : 0.0;
+    h->eta_x = ((h->cfg.lr_x * R.lrs) * kr) * h->Dref;
+    h->eta_k = (h->cfg.lr_kappa * R.lrs) * kr;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+rcp_status rcp_config_default(rcp_config* cfg)
+{
+    if (!cfg) return RCP_ERR_ARG;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->precision = RCP_FP64;
+    cfg->phi0 = 0.05;
+    cfg->eps = 1.0;
+    cfg->beta1 = 0.9;
+    cfg->beta2 = 0.999;
+    cfg->adam_eps = 1e-8;
+    cfg->skin_s = 0.1;
+    cfg->skin_theta = 0.5;
+    cfg->skin_abs = 20.0;
+    cfg->lr_x = 1e-3;
+    cfg->lr_kappa = 1e-3;
+    cfg->delta_star0 = 1e-2;
+    cfg->tol = 5e-4;
+    cfg->Y = 2;
+    cfg->X = 9;
+    cfg->n_min = 2000;
+    cfg->n_down = 3;
+    cfg->n_cycles = 2;
+    cfg->max_iters = 2000000;
+    cfg->chunk = 32;
+    return RCP_OK;
+}
+
+const char* rcp_status_str(rcp_status s)
+{
+    switch (s) {
+    case RCP_OK: return "ok";
+    case RCP_ERR_ARG: return "invalid argument";
+    case RCP_ERR_IMAGE: return "periodic-image rule violated";
+    case RCP_ERR_OOM: return "out of device memory";
+    case RCP_ERR_NAN: return "non-finite energy or gradient";
+    case RCP_ERR_CAPACITY: return "internal capacity exceeded";
+    case RCP_ERR_TIMEOUT: return "device wait timed out";
+    case RCP_ERR_MAXITER: return "iteration cap reached";
+    case RCP_ERR_CUDA: return "CUDA runtime error";
+    case RCP_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* rcp_last_error(rcp_handle h) { return h ? h->err : ""; }
+
+long long rcp_size(rcp_handle h) { return h ? h->N : 0; }
+
+rcp_status rcp_destroy(rcp_handle h)
+{
+    if (!h) return RCP_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
+                    h->lvl, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->hkeys, h->hvals, h->cnt,
+                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->hist, h->scan_tmp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->ctl_h) cudaFreeHost(h->ctl_h);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return RCP_OK;
+}
+
+rcp_status rcp_create(const double* diameters, long long N, int d, const double* box, unsigned long long seed,
+                      const rcp_config* cfg, rcp_handle* out)
+{
+    if (!out) return RCP_ERR_ARG;
+    *out = nullptr;
+    if (!diameters || !box || N < 1) return RCP_ERR_ARG;
+    if (d != 3) return RCP_ERR_UNSUPPORTED;
+    if (N >= (1LL << 31)) return RCP_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0.0) || !std::isfinite(box[a])) return RCP_ERR_ARG;
+    for (long long i = 0; i < N; ++i)
+        if (!(diameters[i] > 0.0) || !std::isfinite(diameters[i])) return RCP_ERR_ARG;
+    rcp_ctx* h = new rcp_ctx();
+    if (cfg) h->cfg = *cfg;
+    else rcp_config_default(&h->cfg);
+    if (h->cfg.chunk < 1) h->cfg.chunk = 1;
+    if ((h->cfg.precision != RCP_FP64 && h->cfg.precision != RCP_MIXED) || !(h->cfg.phi0 > 0.0) ||
+        !(h->cfg.skin_theta > 0.0 && h->cfg.skin_theta < 1.0) || !(h->cfg.skin_s >= 0.0) || !(h->cfg.tol > 0.0)) {
+        delete h;
+        return RCP_ERR_ARG;
+    }
+    h->N = N;
+    h->seed = seed;
+    RcpConst& c = h->c;
+    memset(&c, 0, sizeof(c));
+    c.N = N;
+    c.Lmin = box[0];
+    c.Lmax = box[0];
+    for (int a = 0; a < 3; ++a) {
+        c.L[a] = box[a];
+        c.halfL[a] = 0.5 * box[a];
+        c.qscale[a] = (float)(box[a] * 0x1.0p-32);
+        if (box[a] < c.Lmin) c.Lmin = box[a];
+        if (box[a] > c.Lmax) c.Lmax = box[a];
+    }
+    c.V = (box[0] * box[1]) * box[2];
+    c.eps = h->cfg.eps;
+    c.beta1 = h->cfg.beta1;
+    c.beta2 = h->cfg.beta2;
+    c.adam_eps = h->cfg.adam_eps;
+    c.skin_s = h->cfg.skin_s;
+    c.skin_theta = h->cfg.skin_theta;
+    c.stop_margin = h->cfg.precision == RCP_MIXED ? 1e-2 : 0.0;
+
+    rcp_status st = [&]() -> rcp_status {
+        CK(cudaGetDevice(&h->device));
+        CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+        h->stream = h->own_stream;
+        const size_t n = (size_t)N;
+        CKS(dalloc(h, &h->D0, n));
+        CKS(dalloc(h, &h->xA, n));
+        CKS(dalloc(h, &h->xB, n));
+        CKS(dalloc(h, &h->xb, n));
+        if (h->cfg.precision == RCP_MIXED) {
+            CKS(dalloc(h, &h->m32, 3 * n));
+            CKS(dalloc(h, &h->v32, 3 * n));
+            CKS(dalloc(h, &h->rA, n));
+            CKS(dalloc(h, &h->rB, n));
+            CKS(dalloc(h, &h->rb, n));
+            CK(cudaMemsetAsync(h->m32, 0, sizeof(float) * 3 * n, h->stream));
+            CK(cudaMemsetAsync(h->v32, 0, sizeof(float) * 3 * n, h->stream));
+        } else {
+            CKS(dalloc(h, &h->m64, 3 * n));
+            CKS(dalloc(h, &h->v64, 3 * n));
+            CK(cudaMemsetAsync(h->m64, 0, sizeof(double) * 3 * n, h->stream));
+            CK(cudaMemsetAsync(h->v64, 0, sizeof(double) * 3 * n, h->stream));
+        }
+        CKS(dalloc(h, &h->g, 3 * n));
+        CKS(dalloc(h, &h->xtmp, 3 * n));
+        size_t nparts = (n + RCP_TREE - 1) / RCP_TREE + (n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS + 8;
+        CKS(dalloc(h, &h->part_e, nparts));
+        CKS(dalloc(h, &h->part_k, nparts));
+        CKS(dalloc(h, &h->part_e2, nparts));
+        CKS(dalloc(h, &h->part_k2, nparts));
+        CKS(dalloc(h, &h->ctl, 1));
+        CK(cudaMallocHost((void**)&h->ctl_h, sizeof(RcpCtl)));
+        CKS(dalloc(h, &h->rho, n));
+        CKS(dalloc(h, &h->lvl, n));
+        CKS(dalloc(h, &h->key, n));
+        CKS(dalloc(h, &h->key1, n));
+        CKS(dalloc(h, &h->key2, n));
+        CKS(dalloc(h, &h->idx0, n));
+        CKS(dalloc(h, &h->idx1, n));
+        CKS(dalloc(h, &h->idx2, n));
+        h->hcap = 64;
+        while (h->hcap < 2 * (unsigned long long)n) h->hcap <<= 1;
+        CKS(dalloc(h, &h->hkeys, h->hcap));
+        CKS(dalloc(h, &h->hvals, h->hcap));
+        CKS(dalloc(h, &h->cnt, n + 1));
+        CKS(dalloc(h, &h->offs, n + 1));
+        CKS(dalloc(h, &h->rowptr, n + 1));
+        CKS(ensure_pair_capacity(h, 16 * (unsigned long long)n));
+        CK(cudaFuncSetAttribute(k_kappa_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8192 * 8));
+        CKS(ensure_scan_tmp(h, n + 1));
+
+        // control block
+        RcpCtl init;
+        memset(&init, 0, sizeof(init));
+        init.b1 = 1.0;
+        init.b2 = 1.0;
+        init.need_rebuild = 1;
+        init.halted = 1;
+        init.shrink_bits = 0x7FF0000000000000ull;
+        init.iter_limit = 0;
+        CK(cudaMemcpyAsync(h->ctl, &init, sizeof(RcpCtl), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->D0, diameters, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        const unsigned int nb = rcp_ceil_div(N, 256);
+        k_init_positions<<<nb, 256, 0, h->stream>>>(seed, N, c, h->D0, h->xA);
+        CKL();
+        CKS(tree_sum_D(h, 1, &h->ctl->SD));
+        CKS(tree_sum_D(h, 3, &h->ctl->SD3));
+        CKS(tree_sum_D(h, 4, &h->ctl->SD4));
+        k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.V);
+        CKL();
+        CKS(sync_ctl(h));
+        h->SD = h->ctl_h->SD;
+        h->SD3 = h->ctl_h->SD3;
+        h->SD4 = h->ctl_h->SD4;
+        h->kappa0 = h->ctl_h->kappa;
+        h->Dref = h->SD4 / h->SD3;
+        h->Neff = h->SD3 / ((h->Dref * h->Dref) * h->Dref);
+        h->sigma0 = h->cfg.skin_abs * ((h->cfg.lr_x * h->kappa0) * h->Dref);
+        build_rungs(h);
+        if (h->cfg.precision == RCP_MIXED) {
+            k_to_fixed<<<nb, 256, 0, h->stream>>>(h->ctl, c, h->xA, h->xB, h->rA, h->rB, nullptr);
+            CKL();
+        }
+        return RCP_OK;
+    }();
+    if (st != RCP_OK) {
+        rcp_destroy(h);
+        return st;
+    }
+    *out = h;
+    return RCP_OK;
+}
+
+rcp_status rcp_set_stream(rcp_handle h, void* stream)
+{
+    if (!h) return RCP_ERR_ARG;
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->own_stream;
+    if (s != h->stream) {
+        CK(cudaStreamSynchronize(h->stream));
+        h->stream = s;
+    }
+    return RCP_OK;
+}
+
+rcp_status rcp_set_positions(rcp_handle h, const double* x, double kappa, int on_device)
+{
+    if (!h || !x) return RCP_ERR_ARG;
+    const size_t n = (size_t)h->N;
+    if (on_device) CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
+    else CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    CKS(sync_ctl(h));
+    double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
+    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur);
+    CKL();
+    if (kappa > 0.0) CK(cudaMemcpyAsync(&h->ctl->kappa, &kappa, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (h->cfg.precision == RCP_MIXED) {
+        k_to_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, nullptr);
+        CKL();
+    }
+    if (h->built) {
+        k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
+        CKL();
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return RCP_OK;
+}
+
+rcp_status rcp_build_neighbors(rcp_handle h)
+{
+    if (!h) return RCP_ERR_ARG;
+    CKS(build(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return RCP_OK;
+}
+
+rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x, double* dE_dkappa,
+                           double* max_delta, int on_device)
+{
+    if (!h) return RCP_ERR_ARG;
+    CKS(ensure_list(h));
+    // evaluation mode: mu from the argument, no iteration limit involved
+    k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, mu, 0.0, 0.0, h->cfg.tol, 1LL << 62, 0);
+    CKL();
+    launch_iteration(h, RCP_MODE_GRAD);
+    CKL();
+    const size_t n = (size_t)h->N;
+    if (on_device) {
+        if (grad_x) CK(cudaMemcpyAsync(grad_x, h->g, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
+        if (E) CK(cudaMemcpyAsync(E, &h->ctl->E, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        if (dE_dkappa) CK(cudaMemcpyAsync(dE_dkappa, &h->ctl->dEdk, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        if (max_delta) CK(cudaMemcpyAsync(max_delta, &h->ctl->maxdelta, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        return RCP_OK;
+    }
+    if (grad_x) CK(cudaMemcpyAsync(grad_x, h->g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    CKS(sync_ctl(h));
+    if (h->ctl_h->status == RCP_ERR_NAN) return fail(h, RCP_ERR_NAN, "non-finite energy or gradient");
+    if (E) *E = h->ctl_h->E;
+    if (dE_dkappa) *dE_dkappa = h->ctl_h->dEdk;
+    if (max_delta) *max_delta = h->ctl_h->maxdelta;
+    return RCP_OK;
+}
+
+rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, double lr_x, double lr_kappa,
+                         int on_device)
+{
+    if (!h || !grad_x) return RCP_ERR_ARG;
+    const size_t n = (size_t)h->N;
+    CK(cudaMemcpyAsync(h->g, grad_x, sizeof(double) * 3 * n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if (!h->built) CKS(build(h));
+    if (h->cfg.precision == RCP_MIXED)
+        k_adam_mixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m32, h->v32, h->g,
+                                                                  lr_x);
+    else
+        k_adam64<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->g,
+                                                               h->xb, lr_x);
+    CKL();
+    k_adam_kappa<<<1, 1, 0, h->stream>>>(h->ctl, h->c, dE_dkappa, lr_kappa);
+    CKL();
+    if (h->cfg.precision == RCP_MIXED) {
+        k_to_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, nullptr);
+        CKL();
+        k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
+        CKL();
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return RCP_OK;
+}
+
+static rcp_status do_shrink(rcp_ctx* h)
+{
+    CKS(ensure_list(h));
+    unsigned long long inf = 0x7FF0000000000000ull;
+    CK(cudaMemcpyAsync(&h->ctl->shrink_bits, &inf, sizeof(inf), cudaMemcpyHostToDevice, h->stream));
+    k_shrink<<<pair_blocks(h), RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rowptr, h->col);
+    k_shrink_final<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
+    CKL();
+    return sync_ctl(h);
+}
+
+rcp_status rcp_shrink(rcp_handle h, double* kappa_c, double* phi)
+{
+    if (!h) return RCP_ERR_ARG;
+    CKS(do_shrink(h));
+    if (kappa_c) *kappa_c = h->ctl_h->kappa_c;
+    if (phi) *phi = h->ctl_h->phi;
+    return RCP_OK;
+}
+
+static void fill_result(rcp_ctx* h, rcp_result* out, double secs)
+{
+    if (!out) return;
+    const RcpCtl* c = h->ctl_h;
+    out->iters = c->iter;
+    out->rebuilds = c->rebuilds;
+    out->pairs = (long long)c->pairs;
+    out->stopped = c->stopped;
+    out->kappa = c->kappa;
+    out->max_delta = c->maxdelta;
+    out->energy = c->E;
+    out->kappa_c = c->kappa_c;
+    out->phi = c->phi;
+    out->seconds = secs;
+}
+
+static rcp_status verify_stop_mixed(rcp_ctx* h, bool* stop);
+
+static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, ProfileAcc* prof)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    rcp_stop st = {0, 0.0, 1};
+    if (stop) st = *stop;
+    CKS(sync_ctl(h));
+    const long long call_start = h->ctl_h->iter;
+    rcp_status result = RCP_OK;
+    for (;;) {
+        RcpCtl* hc = h->ctl_h;
+        if (hc->stopped) {
+            if (st.shrink) CKS(do_shrink(h));
+            break;
+        }
+        if (h->rung < 0) {
+            h->rung = 0;
+            h->rung_start = hc->iter;
+            h->kappa_rung = hc->kappa;
+        }
+        const Rung& R = h->rungs[h->rung];
+        long long rung_end = R.final_rung ? h->cfg.max_iters : h->rung_start + R.budget;
+        if (rung_end > h->cfg.max_iters) rung_end = h->cfg.max_iters;
+        if (hc->iter >= rung_end) {
+            if (R.final_rung || hc->iter >= h->cfg.max_iters) {
+                result = fail(h, RCP_ERR_MAXITER, "iteration cap %lld reached before the stopping criterion",
+                              h->cfg.max_iters);
+                break;
+            }
+            h->rung += 1;
+            h->rung_start = hc->iter;
+            h->kappa_rung = hc->kappa;
+            continue;
+        }
+        long long limit = rung_end;
+        if (st.max_iters > 0 && call_start + st.max_iters < limit) limit = call_start + st.max_iters;
+        if (prof && hc->iter + 1 < limit) limit = hc->iter + 1;
+        if (hc->iter >= limit) break;
+        if (st.max_seconds > 0.0) {
+            double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (secs >= st.max_seconds) break;
+        }
+        rung_values(h, h->rung, h->kappa_rung);
+        if (!h->built || hc->need_rebuild) CKS(build(h));
+        if (!prof) CKS(capture_graph(h));
+        k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, h->mu, h->eta_x, h->eta_k, h->cfg.tol, limit, R.final_rung);
+        CKL();
+        if (prof) {
+            launch_iteration(h, RCP_MODE_ADAM, prof->ev);
+            CKL();
+            CK(cudaEventSynchronize(prof->ev[2]));
+            float a = 0.f, b = 0.f;
+            CK(cudaEventElapsedTime(&a, prof->ev[0], prof->ev[1]));
+            CK(cudaEventElapsedTime(&b, prof->ev[0], prof->ev[2]));
+            prof->ms_pair += a;
+            prof->ms_iter += b;
+            prof->launches += 1;
+        } else {
+            CK(cudaGraphLaunch(h->gexec, h->stream));
+        }
+        CKS(sync_ctl(h));
+        hc = h->ctl_h;
+        if (hc->status != RCP_OK) {
+            result = fail(h, (rcp_status)hc->status, "device status %d (%s) at iteration %lld", hc->status,
+                          rcp_status_str((rcp_status)hc->status), hc->iter);
+            break;
+        }
+        if (hc->verify) {
+            bool s = false;
+            CKS(verify_stop_mixed(h, &s));
+        }
+    }
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    fill_result(h, out, secs);
+    return result;
+}
+
+rcp_status rcp_run(rcp_handle h, const rcp_stop* stop, rcp_result* out)
+{
+    if (!h) return RCP_ERR_ARG;
+    return run_impl(h, stop, out, nullptr);
+}
+
+rcp_status rcp_profile(rcp_handle h, long long iters, double* ms_pair, double* ms_iter, long long* launches)
+{
+    if (!h || iters < 1) return RCP_ERR_ARG;
+    ProfileAcc acc;
+    for (int e = 0; e < 3; ++e) CK(cudaEventCreate(&acc.ev[e]));
+    rcp_stop st = {iters, 0.0, 0};
+    rcp_status s = run_impl(h, &st, nullptr, &acc);
+    for (int e = 0; e < 3; ++e) cudaEventDestroy(acc.ev[e]);
+    if (ms_pair) *ms_pair = acc.ms_pair;
+    if (ms_iter) *ms_iter = acc.ms_iter;
+    if (launches) *launches = acc.launches;
+    return s;
+}
+
+static rcp_status verify_stop_mixed(rcp_ctx* h, bool* stop)
+{
+    // binary64 maximum overlap of the state that the binary32 pass flagged
+    k_maxdelta64<<<pair_blocks(h), RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rowptr,
+                                                                      h->col);
+    k_verify_final<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
+    CKL();
+    CKS(sync_ctl(h));
+    *stop = h->ctl_h->stopped != 0;
+    return RCP_OK;
+}
+
+rcp_status rcp_state(rcp_handle h, double* x, double* m, double* v, rcp_scalars* s)
+{
+    if (!h) return RCP_ERR_ARG;
+    CKS(sync_ctl(h));
+    const size_t n = (size_t)h->N;
+    if (x) {
+        const double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
+        k_get_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, cur, h->xtmp);
+        CKL();
+        CK(cudaMemcpyAsync(x, h->xtmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (h->cfg.precision == RCP_MIXED) {
+        std::vector<float> tmp(m || v ? 3 * n : 0);
+        if (m) {
+            CK(cudaMemcpyAsync(tmp.data(), h->m32, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < 3 * n; ++i) m[i] = tmp[i];
+        }
+        if (v) {
+            CK(cudaMemcpyAsync(tmp.data(), h->v32, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (size_t i = 0; i < 3 * n; ++i) v[i] = tmp[i];
+        }
+    } else {
+        if (m) CK(cudaMemcpyAsync(m, h->m64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        if (v) CK(cudaMemcpyAsync(v, h->v64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (s) {
+        const RcpCtl* c = h->ctl_h;
+        s->t = c->iter;
+        s->kappa = c->kappa;
+        s->m_kappa = c->mk;
+        s->v_kappa = c->vk;
+        s->b1 = c->b1;
+        s->b2 = c->b2;
+        s->rung = h->rung;
+        s->rung_start = h->rung_start;
+        s->kappa_rung = h->kappa_rung;
+        s->stopped = c->stopped;
+    }
+    return RCP_OK;
+}
+
+rcp_status rcp_load_state(rcp_handle h, const double* x, const double* m, const double* v, const rcp_scalars* s)
+{
+    if (!h) return RCP_ERR_ARG;
+    const size_t n = (size_t)h->N;
+    if (x) CKS(rcp_set_positions(h, x, s ? s->kappa : 0.0, 0));
+    if (h->cfg.precision == RCP_MIXED) {
+        std::vector<float> tmp(3 * n);
+        if (m) {
+            for (size_t i = 0; i < 3 * n; ++i) tmp[i] = (float)m[i];
+            CK(cudaMemcpy(h->m32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+        }
+        if (v) {
+            for (size_t i = 0; i < 3 * n; ++i) tmp[i] = (float)v[i];
+            CK(cudaMemcpy(h->v32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+        }
+    } else {
+        if (m) CK(cudaMemcpyAsync(h->m64, m, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+        if (v) CK(cudaMemcpyAsync(h->v64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    }
+    if (s) {
+        CKS(sync_ctl(h));
+        RcpCtl c = *h->ctl_h;
+        c.iter = s->t;
+        c.kappa = s->kappa;
+        c.mk = s->m_kappa;
+        c.vk = s->v_kappa;
+        c.b1 = s->b1;
+        c.b2 = s->b2;
+        c.stopped = s->stopped;
+        c.halted = 1;
+        c.need_rebuild = 1;
+        CK(cudaMemcpyAsync(h->ctl, &c, sizeof(RcpCtl), cudaMemcpyHostToDevice, h->stream));
+        h->rung = s->rung;
+        h->rung_start = s->rung_start;
+        h->kappa_rung = s->kappa_rung;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return RCP_OK;
+}
+
+rcp_status rcp_neighbors(rcp_handle h, long long* rowptr, int* col, long long cap, long long* P)
+{
+    if (!h || !rowptr || !P) return RCP_ERR_ARG;
+    if (!h->built) CKS(build(h));
+    const size_t n = (size_t)h->N;
+    std::vector<unsigned int> rp(n + 1);
+    CK(cudaMemcpyAsync(rp.data(), h->rowptr, sizeof(unsigned int) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i <= n; ++i) rowptr[i] = rp[i];
+    *P = (long long)h->P;
+    if (col && (long long)h->P <= cap) {
+        CK(cudaMemcpyAsync(col, h->col, sizeof(unsigned int) * h->P, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return RCP_OK;
+}
+
+rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys)
+{
+    if (!h || !keys) return RCP_ERR_ARG;
+    if (!h->built) CKS(build(h));
+    CK(cudaMemcpyAsync(keys, h->key, sizeof(unsigned long long) * (size_t)h->N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RCP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// rcp_internal.cuh -- shared declarations of the CUDA implementation.
+//
+// The whole library is compiled with -fmad=false so that every binary64
+// expression rounds exactly as written (IEEE add, multiply, divide and sqrt
+// are correctly rounded on both the GPU and the host); binary32 kernels that
+// want fused multiply-adds ask for them with __fmaf_rn.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rcp.h"
+
+#define RCP_KMAX 32
+#define RCP_NBITS_AXIS 19
+#define RCP_NMAX_AXIS (1u << RCP_NBITS_AXIS)
+#define RCP_PAIR_THREADS 256
+#define RCP_TREE 1024          // elements per block of a tree-reduction pass
+#define RCP_SORT_THREADS 256
+#define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
+#define RCP_HASH_EMPTY 0xFFFFFFFFFFFFFFFFull
+
+// Device-resident control block of one packing.  Kernels read the optimiser
+// scalars and the current rung's values from here, so one captured graph
+// serves every rung and both buffer parities.
+struct RcpCtl {
+    // written by the host (through k_set_rung) before a replay
+    double mu, eta_x, eta_k, tol;
+    long long iter_limit;   // halt when iter reaches this
+    int final_rung;
+    int verify;             // mixed precision: stop candidate awaiting FP64 check
+    // optimiser scalars
+    double kappa, mk, vk, b1, b2;
+    long long iter;
+    int parity;             // 0: buffer A holds the current positions
+    // flags
+    int halted, stopped, need_rebuild, status;
+    unsigned int disp_flag;
+    // last evaluation
+    double E, dEdk, maxdelta;
+    unsigned long long maxdelta_bits;
+    // neighbour structure
+    double kappa_b, sigma0;
+    unsigned long long rho_max_bits;
+    unsigned long long rho_lvl_bits[RCP_KMAX];
+    double rho_lvl[RCP_KMAX];
+    int nlev;
+    int ng[RCP_KMAX][3];
+    long long rebuilds;
+    unsigned long long pairs;
+    // constants and one-off results
+    double SD, SD3, SD4;
+    unsigned long long shrink_bits;
+    unsigned long long md64_bits;
+    double kappa_c, phi;
+};
+
+// Kernel parameters that never change during a run.
+struct RcpConst {
+    long long N;
+    double L[3];
+    double halfL[3];
+    double V;
+    double eps, beta1, beta2, adam_eps;
+    double skin_s, skin_theta;
+    double Lmin, Lmax;
+    double stop_margin;     // 0: binary64 overlaps; > 0: relative band that triggers a binary64 check
+    float qscale[3];        // L_a / 2^32: fixed-point unit of axis a
+};
+
+enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
+
+// ---- small helpers ----
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+static inline unsigned int rcp_ceil_div(unsigned long long a, unsigned long long b) { return (unsigned int)((a + b - 1) / b); }
+
+// ---- kernels (rcp_kernels.cu) ----
+__global__ void k_init_positions(unsigned long long seed, long long N, RcpConst c, const double* D0, double4_32a* x);
+__global__ void k_tree_terms(const double* D0, long long N, int power, double* out);
+__global__ void k_tree_pass(const double* in, long long n, double* out);
+__global__ void k_kappa0(RcpCtl* ctl, double phi0, double V);
+__global__ void k_set_rung(RcpCtl* ctl, double mu, double eta_x, double eta_k, double tol,
+                           long long iter_limit, int final_rung);
+__global__ void k_clear_halt(RcpCtl* ctl);
+__global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x);
+__global__ void k_get_positions(long long N, const double4_32a* x, double* out);
+__global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+                         const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
+                         double* part_e, double* part_k, int mode, double* g_out);
+__global__ void k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e, const double* part_k,
+                             long long nb, int mode);
+__global__ void k_tree_pass2(const double* ina, const double* inb, long long n, double* outa, double* outb);
+__global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+                         const double* g, const double4_32a* xb, double eta_x);
+__global__ void k_adam_kappa(RcpCtl* ctl, RcpConst c, double dEdk, double eta_k);
+__global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double4_32a* xb);
+__global__ void k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                         const unsigned int* rowptr, const unsigned int* col);
+__global__ void k_shrink_final(RcpCtl* ctl, RcpConst c);
+
+// ---- mixed precision (rcp_mixed.cu) ----
+// Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
+// 2^32) (integer subtraction wraps, which is exactly the minimum image), the
+// binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0.  One
+// 32-byte sector per gather.
+struct __align__(32) MixRec {
+    int4 q;    // qx, qy, qz, unused
+    float4 l;  // lx, ly, lz, D0
+};
+__global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                           MixRec* rA, MixRec* rB, MixRec* rb);
+__global__ void k_pair_mixed(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, float* m, float* v,
+                             MixRec* rA, MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
+                             const MixRec* rb, double* part_e, double* part_k, int mode, double* g_out);
+__global__ void k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                             const unsigned int* rowptr, const unsigned int* col);
+__global__ void k_verify_final(RcpCtl* ctl, RcpConst c);
+__global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, float* m, float* v,
+                             const double* g, double eta_x);
+
+// ---- neighbour structure (rcp_build.cu) ----
+__global__ void k_build_begin(RcpCtl* ctl, double sigma0);
+__global__ void k_rho(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double* rho);
+__global__ void k_level(RcpCtl* ctl, long long N, const double* rho, int* lvl);
+__global__ void k_grid(RcpCtl* ctl, RcpConst c);
+__global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const int* lvl,
+                           unsigned long long* key, unsigned int* idx);
+__global__ void k_radix_hist(const unsigned long long* keys, long long n, int shift, unsigned int* hist,
+                             unsigned int nblocks);
+__global__ void k_radix_scatter(const unsigned long long* keys, const unsigned int* vals, long long n, int shift,
+                                const unsigned int* hist, unsigned int nblocks,
+                                unsigned long long* okeys, unsigned int* ovals);
+__global__ void k_scan_block(const unsigned int* in, long long n, unsigned int* out, unsigned int* totals);
+__global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* offs);
+__global__ void k_hash_heads(const unsigned long long* keys, long long n, unsigned long long* hkeys,
+                             uint2* hvals, unsigned long long hmask);
+__global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
+                         const int* lvl, const unsigned int* idx_sorted, const unsigned long long* hkeys,
+                         const uint2* hvals, unsigned long long hmask, const unsigned int* offs,
+                         unsigned int* cnt, unsigned long long* pairs, int fill, int nbits);
+__global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits,
+                      unsigned int* rowptr, unsigned int* col);
+__global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double4_32a* xb,
+                            unsigned long long P);

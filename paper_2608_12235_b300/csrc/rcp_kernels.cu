@@ -1,0 +1,494 @@
+// rcp_kernels.cu -- per-iteration kernels of the binary64 path: initial
+// positions, canonical tree reductions, the fused pair energy/gradient + Adam
+// kernel, the kappa step with the stopping test, the standalone Adam step and
+// shrink-to-contact.
+//
+// Every binary64 expression below is written in the exact order of the
+// definition it implements (compiled with -fmad=false, so each operation
+// rounds once, as IEEE-754 prescribes).  Sums follow one canonical order:
+// per-row sums are left folds over the row's partners in ascending index,
+// global sums are pairwise trees over the particle index, zero-padded to a
+// power of two.  The result is therefore independent of the launch shape and
+// of which non-overlapping pairs happen to be listed.
+#include "rcp_internal.cuh"
+
+#define RCP_PI 3.141592653589793
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): output k of the stream seeded with
+// `seed` is the variant-13 mix of seed + (k + 1) * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long k)
+{
+    unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Back into [0, L) after a step shorter than L.
+__device__ __forceinline__ double wrap_step(double x, double L)
+{
+    if (x < 0.0) x = x + L;
+    if (x >= L) x = x - L;
+    return x;
+}
+
+// Minimum-image component of x_i - x_j.
+__device__ __forceinline__ double min_image(double t, double L, double h)
+{
+    if (t > h) t = t - L;
+    else if (t < -h) t = t + L;
+    return t;
+}
+
+__global__ void k_init_positions(unsigned long long seed, long long N, RcpConst c, const double* D0, double4_32a* x)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double p[3];
+    for (int a = 0; a < 3; ++a) {
+        unsigned long long z = splitmix64_at(seed, (unsigned long long)(3 * i + a));
+        double u = (double)(z >> 11) * 0x1.0p-53;
+        p[a] = wrap_step(c.L[a] * u, c.L[a]);
+    }
+    x[i] = make_double4_32a(p[0], p[1], p[2], D0[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Canonical tree of the values held by the threads of a block, in thread
+// order: adjacent lanes first (shuffle offsets 1, 2, 4, 8, 16), then adjacent
+// warps.  NT is a power of two.  The result is valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_tree(double v, double* sh)
+{
+    for (int o = 1; o < 32; o <<= 1) {
+        double w = __shfl_down_sync(0xffffffffu, v, o);
+        v = v + w;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        constexpr int W = NT / 32;
+        for (int s = 1; s < W; s <<= 1)
+            for (int k = 0; k + s < W; k += 2 * s) sh[k] = sh[k] + sh[k + s];
+        r = sh[0];
+    }
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        r = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Terms D, D^3 = (D D) D, D^4 = (D D)(D D) of the moment sums, one tree of
+// RCP_TREE consecutive terms per block.
+__global__ void __launch_bounds__(RCP_TREE) k_tree_terms(const double* D0, long long N, int power, double* out)
+{
+    __shared__ double sh[32];
+    long long i = (long long)blockIdx.x * RCP_TREE + threadIdx.x;
+    double v = 0.0;
+    if (i < N) {
+        double D = D0[i];
+        if (power == 1) v = D;
+        else if (power == 3) v = (D * D) * D;
+        else v = (D * D) * (D * D);
+    }
+    double s = block_tree<RCP_TREE>(v, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// One level of a tree sum: block b sums in[b*RCP_TREE .. +RCP_TREE) (zero
+// padded).  Applied until one value is left, this realises the pairwise tree
+// over the zero-padded sequence.
+__global__ void __launch_bounds__(RCP_TREE) k_tree_pass(const double* in, long long n, double* out)
+{
+    __shared__ double sh[32];
+    long long i = (long long)blockIdx.x * RCP_TREE + threadIdx.x;
+    double s = block_tree<RCP_TREE>(i < n ? in[i] : 0.0, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RCP_TREE) k_tree_pass2(const double* ina, const double* inb, long long n,
+                                                         double* outa, double* outb)
+{
+    __shared__ double sh[32];
+    long long i = (long long)blockIdx.x * RCP_TREE + threadIdx.x;
+    double sa = block_tree<RCP_TREE>(i < n ? ina[i] : 0.0, sh);
+    double sb = block_tree<RCP_TREE>(i < n ? inb[i] : 0.0, sh);
+    if (threadIdx.x == 0) {
+        outa[blockIdx.x] = sa;
+        outb[blockIdx.x] = sb;
+    }
+}
+
+// kappa_0: the cube root of phi0 V / (pi/6 sum D^3) by 200 Newton steps
+// y <- (2y + a/y^2)/3 from y = 1 (correctly rounded operations only, so the
+// bits do not depend on a math library).
+__global__ void k_kappa0(RcpCtl* ctl, double phi0, double V)
+{
+    double a = (phi0 * V) / ((RCP_PI / 6.0) * ctl->SD3);
+    double y = 1.0;
+    if (a > 0.0)
+        for (int it = 0; it < 200; ++it) y = (2.0 * y + a / (y * y)) / 3.0;
+    else
+        y = 0.0;
+    ctl->kappa = y;
+}
+
+__global__ void k_set_rung(RcpCtl* ctl, double mu, double eta_x, double eta_k, double tol,
+                           long long iter_limit, int final_rung)
+{
+    ctl->mu = mu;
+    ctl->eta_x = eta_x;
+    ctl->eta_k = eta_k;
+    ctl->tol = tol;
+    ctl->iter_limit = iter_limit;
+    ctl->final_rung = final_rung;
+    ctl->halted = ctl->iter >= iter_limit ? 1 : 0;
+    ctl->verify = 0;
+}
+
+__global__ void k_clear_halt(RcpCtl* ctl) { ctl->halted = 0; }
+
+// Caller positions [N][3] -> (x, y, z, D0) records, wrapped into the box.
+__global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double p[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = xin[3 * i + a];
+        if (v < 0.0 || v >= c.L[a]) v = v - c.L[a] * floor(v / c.L[a]);
+        p[a] = wrap_step(v, c.L[a]);
+    }
+    x[i] = make_double4_32a(p[0], p[1], p[2], D0[i]);
+}
+
+__global__ void k_get_positions(long long N, const double4_32a* x, double* out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double4_32a p = x[i];
+    out[3 * i + 0] = p.x;
+    out[3 * i + 1] = p.y;
+    out[3 * i + 2] = p.z;
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba 2015, Algorithm 1) on one coordinate, the bias products
+// b1 = beta1^t and b2 = beta2^t already advanced to this step.
+__device__ __forceinline__ double adam_coord(double p, double g, double& m, double& v, double eta,
+                                             const RcpConst& c, double h1, double h2)
+{
+    const double c1 = 1.0 - c.beta1, c2 = 1.0 - c.beta2;
+    m = c.beta1 * m + c1 * g;
+    v = c.beta2 * v + c2 * (g * g);
+    double mh = m / h1;
+    double vh = v / h2;
+    return p - (eta * mh) / (sqrt(vh) + c.adam_eps);
+}
+
+// Has sphere i moved farther than theta of its skin since the last build?
+// (A 1e-9 safety factor keeps rounding on the safe side.)
+__device__ __forceinline__ bool moved_too_far(const RcpCtl* ctl, const RcpConst& c, double px, double py,
+                                              double pz, double D0, double4_32a b)
+{
+    double dx = min_image(px - b.x, c.L[0], c.halfL[0]);
+    double dy = min_image(py - b.y, c.L[1], c.halfL[1]);
+    double dz = min_image(pz - b.z, c.L[2], c.halfL[2]);
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double lim = c.skin_theta * (c.skin_s * ctl->kappa_b * D0 + ctl->sigma0) * (1.0 - 1e-9);
+    return r2 > lim * lim;
+}
+
+// ---------------------------------------------------------------------------
+// Fused pair kernel, binary64.  One thread per sphere i (row of the full
+// Verlet list, columns ascending).  For every listed j with
+// delta = 1 - r/d > 0, d = kappa (D_i^0 + D_j^0)/2:
+//   g_i    -= eps delta / (d r) (x_i - x_j)_mi          (if r > 0)
+//   e_i    += eps/2 delta^2,  k_i += eps delta (1 - delta)/kappa   (j > i)
+//   maxd    = max(maxd, delta)
+// Then, in Adam mode, the Adam step of x_i written to the other position
+// buffer (rows still gather the current one), plus the skin check; in grad
+// mode g_i is written out.  e_i and k_i are summed per block by the
+// canonical tree; maxd by an atomic max (order-free).
+__global__ void __launch_bounds__(RCP_PAIR_THREADS)
+k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+         const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
+         double* part_e, double* part_k, int mode, double* g_out)
+{
+    __shared__ double sh[RCP_PAIR_THREADS / 32];
+    if (ctl->halted) return;
+    const int parity = ctl->parity;
+    const double4_32a* __restrict__ xin = parity ? xB : xA;
+    double4_32a* __restrict__ xout = parity ? xA : xB;
+    const double kappa = ctl->kappa;
+    const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
+    double e = 0.0, k = 0.0, md = 0.0;
+    if (i < c.N) {
+        const double4_32a xi = xin[i];
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        const unsigned int t1 = rowptr[i + 1];
+        for (unsigned int t = rowptr[i]; t < t1; ++t) {
+            const unsigned int j = col[t];
+            const double4_32a xj = xin[j];
+            double dx = min_image(xi.x - xj.x, c.L[0], c.halfL[0]);
+            double dy = min_image(xi.y - xj.y, c.L[1], c.halfL[1]);
+            double dz = min_image(xi.z - xj.z, c.L[2], c.halfL[2]);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            double dd = kappa * (0.5 * (xi.w + xj.w));
+            double delta = 1.0 - r / dd;
+            if (delta > 0.0) {
+                if (r > 0.0) {
+                    double coef = (c.eps * delta) / (dd * r);
+                    g0 = g0 - coef * dx;
+                    g1 = g1 - coef * dy;
+                    g2 = g2 - coef * dz;
+                }
+                if ((long long)j > i) {
+                    e = e + (0.5 * c.eps) * (delta * delta);
+                    k = k + ((c.eps * delta) * (1.0 - delta)) / kappa;
+                }
+                if (delta > md) md = delta;
+            }
+        }
+        if (mode == RCP_MODE_ADAM) {
+            const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+            const double h1 = 1.0 - b1, h2 = 1.0 - b2;
+            const double eta = ctl->eta_x;
+            double m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
+            double v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
+            double p0 = wrap_step(adam_coord(xi.x, g0, m0, v0, eta, c, h1, h2), c.L[0]);
+            double p1 = wrap_step(adam_coord(xi.y, g1, m1, v1, eta, c, h1, h2), c.L[1]);
+            double p2 = wrap_step(adam_coord(xi.z, g2, m2, v2, eta, c, h1, h2), c.L[2]);
+            m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
+            v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
+            xout[i] = make_double4_32a(p0, p1, p2, xi.w);
+            if (moved_too_far(ctl, c, p0, p1, p2, xi.w, xb[i])) atomicOr(&ctl->disp_flag, 1u);
+        } else {
+            g_out[3 * i] = g0;
+            g_out[3 * i + 1] = g1;
+            g_out[3 * i + 2] = g2;
+        }
+    }
+    double se = block_tree<RCP_PAIR_THREADS>(e, sh);
+    double sk = block_tree<RCP_PAIR_THREADS>(k, sh);
+    double bm = block_max(md, sh);
+    if (threadIdx.x == 0) {
+        part_e[blockIdx.x] = se;
+        part_k[blockIdx.x] = sk;
+        if (bm > 0.0) atomicMax(&ctl->maxdelta_bits, dbits(bm));
+    }
+}
+
+// Close an iteration: Adam step of kappa with dE/dkappa of the evaluation,
+// advance the bias products, swap the position buffers, count the step, and
+// flag a rebuild when some sphere used up theta of its skin or kappa grew
+// past kappa_b (1 + 2 s (1 - theta)).
+__device__ void kappa_adam_tail(RcpCtl* ctl, const RcpConst& c)
+{
+    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+    double mk = ctl->mk, vk = ctl->vk;
+    const double kn = adam_coord(ctl->kappa, ctl->dEdk, mk, vk, ctl->eta_k, c, 1.0 - b1, 1.0 - b2);
+    ctl->mk = mk;
+    ctl->vk = vk;
+    ctl->kappa = kn;
+    ctl->b1 = b1;
+    ctl->b2 = b2;
+    ctl->parity ^= 1;
+    ctl->iter += 1;
+    if (ctl->iter >= ctl->iter_limit) ctl->halted = 1;
+    const double s = c.skin_s, th = c.skin_theta;
+    if (ctl->disp_flag || kn > ctl->kappa_b * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) {
+        ctl->need_rebuild = 1;
+        ctl->halted = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finish an evaluation: tree over the block partials (nb <= 8192, zero
+// padded to a power of two) gives sum_i e_i and sum_i k_i, hence
+//   E = sum e - mu (kappa sum D^0),   dE/dkappa = sum k - mu sum D^0.
+// In Adam mode: the stopping test of App. A on the state just evaluated (the
+// final rung stops when max delta < tol, before that state's Adam step),
+// otherwise the Adam step of kappa, the buffer swap, and the rebuild test.
+__global__ void __launch_bounds__(1024) k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e,
+                                                     const double* part_k, long long nb, int mode)
+{
+    extern __shared__ double buf[];
+    if (ctl->halted) return;
+    long long M = 1;
+    while (M < nb) M <<= 1;
+    double* be = buf;
+    double* bk = buf + M;
+    for (long long t = threadIdx.x; t < M; t += blockDim.x) {
+        be[t] = t < nb ? part_e[t] : 0.0;
+        bk[t] = t < nb ? part_k[t] : 0.0;
+    }
+    __syncthreads();
+    for (long long s = 1; s < M; s <<= 1) {
+        for (long long idx = (long long)threadIdx.x * 2 * s; idx < M; idx += (long long)blockDim.x * 2 * s) {
+            be[idx] = be[idx] + be[idx + s];
+            bk[idx] = bk[idx] + bk[idx + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double mu = ctl->mu, kappa = ctl->kappa;
+    const double E = be[0] - mu * (kappa * ctl->SD);
+    const double dEdk = bk[0] - mu * ctl->SD;
+    const double md = bitsd(ctl->maxdelta_bits);
+    ctl->maxdelta_bits = 0ull;
+    ctl->E = E;
+    ctl->dEdk = dEdk;
+    ctl->maxdelta = md;
+    if (!isfinite(E) || !isfinite(dEdk)) {
+        ctl->status = RCP_ERR_NAN;
+        ctl->halted = 1;
+        return;
+    }
+    if (mode != RCP_MODE_ADAM) return;
+    if (ctl->final_rung) {
+        if (c.stop_margin == 0.0) {
+            if (md < ctl->tol) {
+                ctl->stopped = 1;
+                ctl->halted = 1;
+                return;
+            }
+        } else if (md < ctl->tol * (1.0 + c.stop_margin)) {
+            // binary32 overlaps: a stop candidate is confirmed in binary64
+            // (k_maxdelta64, k_verify_final) before the iteration is closed
+            ctl->verify = 1;
+            ctl->halted = 1;
+            return;
+        }
+    }
+    kappa_adam_tail(ctl, c);
+}
+
+// Binary64 verdict on a binary32 stop candidate: stop on the evaluated state,
+// or close the iteration as k_kappa_step would have.
+__global__ void k_verify_final(RcpCtl* ctl, RcpConst c)
+{
+    const double md = bitsd(ctl->md64_bits);
+    ctl->md64_bits = 0ull;
+    ctl->verify = 0;
+    if (md < ctl->tol) {
+        ctl->maxdelta = md;
+        ctl->stopped = 1;
+        ctl->halted = 1;
+        return;
+    }
+    ctl->halted = 0;
+    kappa_adam_tail(ctl, c);
+}
+
+// ---------------------------------------------------------------------------
+// Standalone Adam step on every coordinate (rcp_adam_step), in place on the
+// current buffer, with a caller-supplied gradient [N][3].
+__global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+                         const double* g, const double4_32a* xb, double eta_x)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
+    double4_32a* x = ctl->parity ? xB : xA;
+    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+    const double h1 = 1.0 - b1, h2 = 1.0 - b2;
+    double4_32a p = x[i];
+    double m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
+    double v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
+    double p0 = wrap_step(adam_coord(p.x, g[3 * i], m0, v0, eta_x, c, h1, h2), c.L[0]);
+    double p1 = wrap_step(adam_coord(p.y, g[3 * i + 1], m1, v1, eta_x, c, h1, h2), c.L[1]);
+    double p2 = wrap_step(adam_coord(p.z, g[3 * i + 2], m2, v2, eta_x, c, h1, h2), c.L[2]);
+    m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
+    v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
+    x[i] = make_double4_32a(p0, p1, p2, p.w);
+    if (moved_too_far(ctl, c, p0, p1, p2, p.w, xb[i])) atomicOr(&ctl->disp_flag, 1u);
+}
+
+// kappa's share of the standalone Adam step; also advances t and the bias
+// products, and flags a rebuild if the skin budget is used up.
+__global__ void k_adam_kappa(RcpCtl* ctl, RcpConst c, double dEdk, double eta_k)
+{
+    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+    double mk = ctl->mk, vk = ctl->vk;
+    const double kn = adam_coord(ctl->kappa, dEdk, mk, vk, eta_k, c, 1.0 - b1, 1.0 - b2);
+    ctl->mk = mk;
+    ctl->vk = vk;
+    ctl->kappa = kn;
+    ctl->b1 = b1;
+    ctl->b2 = b2;
+    ctl->iter += 1;
+    const double s = c.skin_s, th = c.skin_theta;
+    if (ctl->disp_flag || kn > ctl->kappa_b * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) ctl->need_rebuild = 1;
+}
+
+// Skin check of the current state against the last build (after positions or
+// kappa were replaced from outside).
+__global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double4_32a* xb)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        const double s = c.skin_s, th = c.skin_theta;
+        if (ctl->kappa > ctl->kappa_b * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) ctl->need_rebuild = 1;
+    }
+    if (i >= c.N) return;
+    const double4_32a* x = ctl->parity ? xB : xA;
+    double4_32a p = x[i];
+    if (moved_too_far(ctl, c, p.x, p.y, p.z, p.w, xb[i])) ctl->need_rebuild = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Shrink to contact: min over listed pairs i < j of r_ij / d_ij^0 (order-free
+// minimum through the bit pattern of a non-negative double).
+__global__ void __launch_bounds__(RCP_PAIR_THREADS)
+k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+         const unsigned int* rowptr, const unsigned int* col)
+{
+    __shared__ double sh[RCP_PAIR_THREADS / 32];
+    const double4_32a* x = ctl->parity ? xB : xA;
+    const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
+    double q = INFINITY;
+    if (i < c.N) {
+        const double4_32a xi = x[i];
+        for (unsigned int t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+            const unsigned int j = col[t];
+            if ((long long)j <= i) continue;
+            const double4_32a xj = x[j];
+            double dx = min_image(xi.x - xj.x, c.L[0], c.halfL[0]);
+            double dy = min_image(xi.y - xj.y, c.L[1], c.halfL[1]);
+            double dz = min_image(xi.z - xj.z, c.L[2], c.halfL[2]);
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double qq = r / (0.5 * (xi.w + xj.w));
+            if (qq < q) q = qq;
+        }
+    }
+    // block minimum through max of the negated value
+    double bm = -block_max(-q, sh);
+    if (threadIdx.x == 0 && bm < INFINITY) atomicMin(&ctl->shrink_bits, dbits(bm));
+}
+
+// kappa_c = min(kappa, q_min); phi = (pi/6) kappa_c^3 sum D^3 / V.
+__global__ void k_shrink_final(RcpCtl* ctl, RcpConst c)
+{
+    double q = bitsd(ctl->shrink_bits);
+    double kc = ctl->kappa;
+    if (q < kc) kc = q;
+    ctl->kappa_c = kc;
+    ctl->phi = (((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) / c.V;
+}

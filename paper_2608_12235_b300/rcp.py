@@ -1,0 +1,288 @@
+"""Thin ctypes binding of the C ABI in include/rcp.h (librcp.so, sm_103a).
+
+The functions below carry the C names and only marshal arguments; every step
+of the protocol runs in the CUDA library.  There is no CPU fallback: if the
+library or a CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librcp.so")
+
+RCP_FP64, RCP_MIXED = 0, 1
+STATUS = {0: "RCP_OK", 1: "RCP_ERR_ARG", 2: "RCP_ERR_IMAGE", 3: "RCP_ERR_OOM", 4: "RCP_ERR_NAN",
+          5: "RCP_ERR_CAPACITY", 6: "RCP_ERR_TIMEOUT", 7: "RCP_ERR_MAXITER", 8: "RCP_ERR_CUDA",
+          9: "RCP_ERR_UNSUPPORTED"}
+
+# every symbol include/rcp.h declares
+EXPORTS = ["rcp_config_default", "rcp_create", "rcp_destroy", "rcp_set_stream", "rcp_set_positions",
+           "rcp_build_neighbors", "rcp_energy_grad", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
+           "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_status_str", "rcp_last_error"]
+
+
+class rcp_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("phi0", C.c_double), ("eps", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("adam_eps", C.c_double), ("skin_s", C.c_double),
+                ("skin_theta", C.c_double), ("skin_abs", C.c_double), ("lr_x", C.c_double),
+                ("lr_kappa", C.c_double), ("delta_star0", C.c_double), ("tol", C.c_double), ("Y", C.c_int),
+                ("X", C.c_int), ("n_min", C.c_longlong), ("n_down", C.c_int), ("n_cycles", C.c_int),
+                ("max_iters", C.c_longlong), ("chunk", C.c_int)]
+
+
+class rcp_stop(C.Structure):
+    _fields_ = [("max_iters", C.c_longlong), ("max_seconds", C.c_double), ("shrink", C.c_int)]
+
+
+class rcp_result(C.Structure):
+    _fields_ = [("iters", C.c_longlong), ("rebuilds", C.c_longlong), ("pairs", C.c_longlong),
+                ("stopped", C.c_int), ("kappa", C.c_double), ("max_delta", C.c_double),
+                ("energy", C.c_double), ("kappa_c", C.c_double), ("phi", C.c_double), ("seconds", C.c_double)]
+
+
+class rcp_scalars(C.Structure):
+    _fields_ = [("t", C.c_longlong), ("kappa", C.c_double), ("m_kappa", C.c_double), ("v_kappa", C.c_double),
+                ("b1", C.c_double), ("b2", C.c_double), ("rung", C.c_int), ("rung_start", C.c_longlong),
+                ("kappa_rung", C.c_double), ("stopped", C.c_int)]
+
+
+_lib = None
+
+
+class RcpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load librcp.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -m paper_2608_12235_b300.build`")
+    L = C.CDLL(p)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    L.rcp_config_default.argtypes = [C.POINTER(rcp_config)]
+    L.rcp_create.argtypes = [vp, C.c_longlong, ip, vp, C.c_ulonglong, C.POINTER(rcp_config), C.POINTER(vp)]
+    L.rcp_destroy.argtypes = [vp]
+    L.rcp_set_stream.argtypes = [vp, vp]
+    L.rcp_set_positions.argtypes = [vp, vp, C.c_double, ip]
+    L.rcp_build_neighbors.argtypes = [vp]
+    L.rcp_energy_grad.argtypes = [vp, C.c_double, vp, vp, vp, vp, ip]
+    L.rcp_adam_step.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, ip]
+    L.rcp_run.argtypes = [vp, C.POINTER(rcp_stop), C.POINTER(rcp_result)]
+    L.rcp_profile.argtypes = [vp, C.c_longlong, dp, dp, C.POINTER(C.c_longlong)]
+    L.rcp_shrink.argtypes = [vp, dp, dp]
+    L.rcp_state.argtypes = [vp, vp, vp, vp, C.POINTER(rcp_scalars)]
+    L.rcp_load_state.argtypes = [vp, vp, vp, vp, C.POINTER(rcp_scalars)]
+    L.rcp_neighbors.argtypes = [vp, vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
+    L.rcp_cell_keys.argtypes = [vp, vp]
+    L.rcp_size.argtypes = [vp]
+    L.rcp_size.restype = C.c_longlong
+    L.rcp_status_str.argtypes = [ip]
+    L.rcp_status_str.restype = C.c_char_p
+    L.rcp_last_error.argtypes = [vp]
+    L.rcp_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("rcp_size", "rcp_status_str", "rcp_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, h=None):
+    if st != 0:
+        msg = load().rcp_last_error(h).decode() if h else ""
+        raise RcpError(st, msg or load().rcp_status_str(st).decode())
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def rcp_config_default(**overrides) -> rcp_config:
+    cfg = rcp_config()
+    _check(load().rcp_config_default(C.byref(cfg)))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def rcp_create(diameters, box=1.0, seed: int = 0, cfg: rcp_config | None = None, d: int = 3):
+    D0 = np.ascontiguousarray(diameters, dtype=np.float64)
+    b = np.full(3, float(box)) if np.isscalar(box) else np.ascontiguousarray(box, dtype=np.float64)
+    h = C.c_void_p()
+    _check(load().rcp_create(D0.ctypes.data, D0.size, d, b.ctypes.data, seed,
+                             C.byref(cfg) if cfg is not None else None, C.byref(h)))
+    return h
+
+
+def rcp_destroy(h):
+    _check(load().rcp_destroy(h))
+
+
+def rcp_set_stream(h, stream: int | None):
+    _check(load().rcp_set_stream(h, stream), h)
+
+
+def rcp_set_positions(h, x, kappa: float = 0.0, on_device: bool = False):
+    if not on_device:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+    _check(load().rcp_set_positions(h, _ptr(x), kappa, int(on_device)), h)
+
+
+def rcp_build_neighbors(h):
+    _check(load().rcp_build_neighbors(h), h)
+
+
+def rcp_energy_grad(h, mu: float, E=None, grad_x=None, dE_dkappa=None, max_delta=None, on_device=False):
+    """Fill the given output buffers (numpy float64 on the host, or torch
+    float64 CUDA tensors with on_device=True)."""
+    _check(load().rcp_energy_grad(h, mu, _ptr(E), _ptr(grad_x), _ptr(dE_dkappa), _ptr(max_delta),
+                                  int(on_device)), h)
+
+
+def rcp_adam_step(h, grad_x, dE_dkappa: float, lr_x: float, lr_kappa: float, on_device=False):
+    if not on_device:
+        grad_x = np.ascontiguousarray(grad_x, dtype=np.float64)
+    _check(load().rcp_adam_step(h, _ptr(grad_x), dE_dkappa, lr_x, lr_kappa, int(on_device)), h)
+
+
+def rcp_run(h, max_iters: int = 0, max_seconds: float = 0.0, shrink: bool = True) -> rcp_result:
+    st = rcp_stop(max_iters, max_seconds, int(shrink))
+    res = rcp_result()
+    code = load().rcp_run(h, C.byref(st), C.byref(res))
+    if code not in (0,):
+        _check(code, h)
+    return res
+
+
+def rcp_profile(h, iters: int):
+    """Run `iters` real iterations launched one by one with CUDA events around
+    the pair kernel; returns (ms in the pair kernel, ms in whole iterations,
+    pair-kernel launches)."""
+    a, b, n = C.c_double(), C.c_double(), C.c_longlong()
+    _check(load().rcp_profile(h, iters, C.byref(a), C.byref(b), C.byref(n)), h)
+    return a.value, b.value, n.value
+
+
+def rcp_shrink(h):
+    kc, phi = C.c_double(), C.c_double()
+    _check(load().rcp_shrink(h, C.byref(kc), C.byref(phi)), h)
+    return kc.value, phi.value
+
+
+def rcp_state(h):
+    n = load().rcp_size(h)
+    x, m, v = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    s = rcp_scalars()
+    _check(load().rcp_state(h, x.ctypes.data, m.ctypes.data, v.ctypes.data, C.byref(s)), h)
+    return x, m, v, s
+
+
+def rcp_load_state(h, x, m, v, s: rcp_scalars):
+    x, m, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, m, v))
+    _check(load().rcp_load_state(h, x.ctypes.data, m.ctypes.data, v.ctypes.data, C.byref(s)), h)
+
+
+def rcp_neighbors(h):
+    n = load().rcp_size(h)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    P = C.c_longlong()
+    _check(load().rcp_neighbors(h, rowptr.ctypes.data, None, 0, C.byref(P)), h)
+    col = np.zeros(max(P.value, 1), dtype=np.int32)
+    _check(load().rcp_neighbors(h, rowptr.ctypes.data, col.ctypes.data, col.size, C.byref(P)), h)
+    return rowptr, col[: P.value]
+
+
+def rcp_cell_keys(h):
+    n = load().rcp_size(h)
+    k = np.zeros(n, dtype=np.uint64)
+    _check(load().rcp_cell_keys(h, k.ctypes.data), h)
+    return k
+
+
+def rcp_size(h) -> int:
+    return int(load().rcp_size(h))
+
+
+# ----------------------------------------------------------------- convenience
+@dataclass
+class RunSummary:
+    iters: int
+    rebuilds: int
+    pairs: int
+    stopped: bool
+    kappa: float
+    max_delta: float
+    energy: float
+    kappa_c: float
+    phi: float
+    seconds: float
+
+
+class Packing:
+    """One packing on the GPU (owns an rcp handle)."""
+
+    def __init__(self, diameters, box=1.0, seed: int = 0, precision: int = RCP_FP64, **cfg):
+        self.cfg = rcp_config_default(precision=precision, **cfg)
+        self.n = int(np.size(diameters))
+        self.h = rcp_create(diameters, box, seed, self.cfg)
+
+    def close(self):
+        if self.h:
+            rcp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def energy_grad(self, mu: float):
+        E, dk, md = np.zeros(1), np.zeros(1), np.zeros(1)
+        g = np.zeros((self.n, 3))
+        rcp_energy_grad(self.h, mu, E, g, dk, md)
+        return float(E[0]), g, float(dk[0]), float(md[0])
+
+    def run(self, max_iters=0, max_seconds=0.0, shrink=True) -> RunSummary:
+        r = rcp_run(self.h, max_iters, max_seconds, shrink)
+        return RunSummary(r.iters, r.rebuilds, r.pairs, bool(r.stopped), r.kappa, r.max_delta, r.energy,
+                          r.kappa_c, r.phi, r.seconds)
+
+    def state(self):
+        return rcp_state(self.h)
+
+    def positions(self):
+        return rcp_state(self.h)[0]
+
+    def neighbors(self):
+        return rcp_neighbors(self.h)
+
+    def cell_keys(self):
+        return rcp_cell_keys(self.h)
+
+    def set_positions(self, x, kappa=0.0):
+        rcp_set_positions(self.h, x, kappa)
+
+    def shrink(self):
+        return rcp_shrink(self.h)
+
+    def adam_step(self, g, dEdk, lr_x, lr_kappa):
+        rcp_adam_step(self.h, g, dEdk, lr_x, lr_kappa)

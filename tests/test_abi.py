@@ -1,0 +1,53 @@
+"""The C-ABI library loads and exports every entry point include/rcp.h declares
+(no compute call: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rcp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rcp_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_12235_b300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "rcp_create" in names and "rcp_run" in names and "rcp_energy_grad" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_2608_12235_b300 import rcp
+    assert sorted(rcp.EXPORTS) == _declared()
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2608_12235_b300 import rcp
+    rcp.load()
+    cfg = rcp.rcp_config_default()
+    assert cfg.tol == 5e-4 and (cfg.Y, cfg.X) == (2, 9) and cfg.beta1 == 0.9 and cfg.beta2 == 0.999
+    assert rcp.load().rcp_status_str(2).decode().startswith("periodic-image")
+
+
+def test_create_rejects_bad_input_before_touching_the_gpu(lib):
+    from paper_2608_12235_b300 import rcp
+    import numpy as np
+    with pytest.raises(rcp.RcpError) as e:
+        rcp.rcp_create(np.array([1.0, -1.0]), 1.0, 0)
+    assert e.value.status == 1
+    with pytest.raises(rcp.RcpError) as e:
+        rcp.rcp_create(np.ones(4), 1.0, 0, d=2)
+    assert e.value.status == 9
