@@ -211,6 +211,40 @@ rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys);
 /* Number of spheres. */
 long long rcp_size(rcp_handle h);
 
+/* Largest N accepted by rcp_energy_grad_noalloc. */
+#define RCP_NOALLOC_MAX_N (1LL << 21)
+
+/* Binary64 evaluation that allocates no memory (the paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory -- code
+ * running inside a memory pool another runtime has fully reserved, hosts that
+ * partition device memory once at start-up, or callers that must not enter
+ * the allocator while another library holds it).  No handle is involved and
+ * no cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * Computes, from caller-owned DEVICE buffers, exactly what rcp_energy_grad
+ * computes in RCP_FP64 mode: Eq. energy E, grad_x[N][3] = dE/dx_i, dE/dkappa
+ * and max(0, max delta_ij), over the CSR list rowptr[N+1] / col[P]
+ * (unsigned 32-bit, ascending columns per row; it must contain every
+ * overlapping pair, as rcp_neighbors' list does).
+ *   x: [N][3] positions inside the box; D0: [N] relative diameters;
+ *   box: HOST array of 3 box edges; kappa > 0; mu and eps as in Eq. energy;
+ *   E, dE_dkappa, max_delta: device pointers to one double each (may be NULL);
+ *   stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * Work is asynchronous on `stream`; outputs are valid once it completes.
+ *
+ * Scratch lives in a fixed static device array inside the library (about
+ * 192 KiB, held by every GPU that loads the library until the process exits)
+ * sized for N <= RCP_NOALLOC_MAX_N; larger N returns RCP_ERR_CAPACITY.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and caches it, so make that
+ * first call before any stream capture.  Every call shares the one array: two
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race and both results are undefined; serialize them. */
+rcp_status rcp_energy_grad_noalloc(const double* x, const double* D0, long long N, const double* box,
+                                   double kappa, double mu, double eps, const unsigned int* rowptr,
+                                   const unsigned int* col, double* E, double* grad_x,
+                                   double* dE_dkappa, double* max_delta, void* stream);
+
 /* Static text of a status code. */
 const char* rcp_status_str(rcp_status s);
 

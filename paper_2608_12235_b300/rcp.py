@@ -23,7 +23,8 @@ STATUS = {0: "RCP_OK", 1: "RCP_ERR_ARG", 2: "RCP_ERR_IMAGE", 3: "RCP_ERR_OOM", 4
 # every symbol include/rcp.h declares
 EXPORTS = ["rcp_config_default", "rcp_create", "rcp_destroy", "rcp_set_stream", "rcp_set_positions",
            "rcp_build_neighbors", "rcp_energy_grad", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
-           "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_status_str", "rcp_last_error"]
+           "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_status_str", "rcp_last_error",
+           "rcp_energy_grad_noalloc"]
 
 
 class rcp_config(C.Structure):
@@ -85,6 +86,8 @@ def load(path: str | None = None) -> C.CDLL:
     L.rcp_load_state.argtypes = [vp, vp, vp, vp, C.POINTER(rcp_scalars)]
     L.rcp_neighbors.argtypes = [vp, vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
     L.rcp_cell_keys.argtypes = [vp, vp]
+    L.rcp_energy_grad_noalloc.argtypes = [vp, vp, C.c_longlong, vp, C.c_double, C.c_double, C.c_double,
+                                          vp, vp, vp, vp, vp, vp, vp]
     L.rcp_size.argtypes = [vp]
     L.rcp_size.restype = C.c_longlong
     L.rcp_status_str.argtypes = [ip]
@@ -215,6 +218,17 @@ def rcp_cell_keys(h):
     k = np.zeros(n, dtype=np.uint64)
     _check(load().rcp_cell_keys(h, k.ctypes.data), h)
     return k
+
+
+def rcp_energy_grad_noalloc(x, D0, box, kappa: float, mu: float, rowptr, col, E, grad_x, dE_dkappa,
+                            max_delta, eps: float = 1.0, stream: int | None = None):
+    """Evaluation on caller-owned device buffers with no allocation (torch CUDA
+    tensors: x float64 [N,3], D0 float64 [N], rowptr/col int32, outputs
+    float64).  Asynchronous on `stream` (a cudaStream_t address)."""
+    b = np.full(3, float(box)) if np.isscalar(box) else np.ascontiguousarray(box, dtype=np.float64)
+    _check(load().rcp_energy_grad_noalloc(_ptr(x), _ptr(D0), int(D0.shape[0]), b.ctypes.data, kappa, mu, eps,
+                                          _ptr(rowptr), _ptr(col), _ptr(E), _ptr(grad_x), _ptr(dE_dkappa),
+                                          _ptr(max_delta), stream))
 
 
 def rcp_size(h) -> int:
