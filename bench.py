@@ -140,7 +140,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lognormal-n1e6-s5e5", choices=sorted(WORKLOADS))
     ap.add_argument("--iters-per-step", type=int, default=100)
-    ap.add_argument("--densify", type=int, default=2000)
+    ap.add_argument("--densify", type=int, default=6000)
+    ap.add_argument("--skin-abs", type=float, default=100.0)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -171,7 +172,7 @@ def main():
             dist.barrier()
 
     # ---- mixed precision: densify, warm up, time
-    p = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_MIXED)
+    p = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs)
     rcp.rcp_set_stream(p.h, stream.cuda_stream)
     p.run(max_iters=args.densify, shrink=False)
     for _ in range(args.warmup):
@@ -187,6 +188,7 @@ def main():
     for _ in range(args.steps):
         r = p.run(max_iters=ips, shrink=False)
         pairs_sum += r.pairs * ips
+        launches += r.launches
         if rebuild0 is None:
             rebuild0 = r.rebuilds
     ev1.record(stream)
@@ -217,7 +219,7 @@ def main():
     peak, peak_kind = peaks()
 
     # ---- binary64 at the same state
-    q = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_FP64)
+    q = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_FP64, skin_abs=args.skin_abs)
     rcp.rcp_set_stream(q.h, stream.cuda_stream)
     rcp.rcp_load_state(q.h, *snap)
     q.run(max_iters=ips, shrink=False)
@@ -259,6 +261,7 @@ def main():
             "vs_baseline": None, "dtype": "f32 pair math, f64 state and reductions", "data": "synthetic",
             "config": {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"],
                        "precision": "mixed", "iters_per_step": ips, "densify_iters": args.densify,
+                       "skin_abs": args.skin_abs,
                        "phi_at_timing": round(phi_now, 4), "l2": "working set larger than L2 (>250 MB)"},
             "pair_evals_per_s": pair_evals,
             "fp64": {"value": value64, "unit": "iters/s", "speedup_mixed_over_fp64": value / value64},
@@ -269,7 +272,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_rate, "unit": "iters/s", "h2d_bytes_per_step": 24 * w["N"],
                     "d2h_bytes_per_step": 24 * w["N"]},
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

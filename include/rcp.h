@@ -100,6 +100,8 @@ typedef struct {
     double    kappa_c;      /* shrink-to-contact kappa (0 until computed) */
     double    phi;          /* shrink-to-contact packing fraction (0 until computed) */
     double    seconds;      /* wall time of this call */
+    long long launches;     /* CUDA kernels launched by this call (each kernel of a
+                               replayed graph counts once per replay) */
 } rcp_result;
 
 /* Optimiser scalars, for checkpoint and resume (rcp_state / rcp_load_state). */

@@ -78,7 +78,7 @@ def lib():
         L.orc_levels.argtypes = [_dp, C.c_long, C.c_double, C.c_double, C.c_double,
                                  np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), _dp]
         L.orc_grid_n.restype = C.c_long
-        L.orc_grid_n.argtypes = [C.c_double, C.c_double]
+        L.orc_grid_n.argtypes = [C.c_double, C.c_double, C.c_long, C.c_double]
         L.orc_cell_keys.argtypes = [_dp, _dp, C.c_long, C.c_int, _dp, C.c_double, C.c_double,
                                     C.c_double, _up]
         for nm in ("orc_list_brute", "orc_list_grid"):
@@ -175,8 +175,8 @@ def levels(D0, kappa_b, s, sigma0):
     return lvl, rml[:nlev]
 
 
-def grid_n(L: float, rho_max_k: float) -> int:
-    return int(lib().orc_grid_n(L, rho_max_k))
+def grid_n(L: float, rho_max_k: float, count: int, V: float) -> int:
+    return int(lib().orc_grid_n(L, rho_max_k, count, V))
 
 
 def cell_keys(x, D0, L, kappa_b, s, sigma0, d=3):

@@ -200,11 +200,21 @@ int orc_levels(const double* D0, long n, double kappa_b, double s, double sigma0
 }
 
 /* Cells per axis at a level: the largest power of two n <= 2^19 whose cell
- * edge L/n is at least the level's largest interaction diameter 2 rho_max. */
-long orc_grid_n(double L, double rho_max_k)
+ * edge h = L/n is at least the level's largest interaction diameter
+ * 2 rho_max and whose cell volume h^3 holds at least ORC_OCC spheres of the
+ * level on average, h^3 count >= ORC_OCC V (cells smaller than either bound
+ * only add empty lookups).  V is the box volume, count the level's size. */
+#define ORC_OCC 2.0
+long orc_grid_n(double L, double rho_max_k, long count, double V)
 {
     long n = 1;
-    while (n < ORC_NMAX && L / (double)(2 * n) >= 2.0 * rho_max_k) n *= 2;
+    for (;;) {
+        if (n >= ORC_NMAX) break;
+        double h = L / (double)(2 * n);
+        if (!(h >= 2.0 * rho_max_k)) break;
+        if (!(((h * h) * h) * (double)count >= ORC_OCC * V)) break;
+        n *= 2;
+    }
     return n;
 }
 
@@ -228,10 +238,13 @@ void orc_cell_keys(const double* x, const double* D0, long n, int d, const doubl
     int* lvl = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     double rml[ORC_KMAX];
     orc_levels(D0, n, kappa_b, s, sigma0, lvl, rml);
+    long cnt[ORC_KMAX] = {0};
+    for (long i = 0; i < n; ++i) cnt[lvl[i]]++;
+    double V = box_volume(d, L);
     for (long i = 0; i < n; ++i) {
         int k = lvl[i];
         long c[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) c[a] = cell_of(x[d * i + a], L[a], orc_grid_n(L[a], rml[k]));
+        for (int a = 0; a < d; ++a) c[a] = cell_of(x[d * i + a], L[a], orc_grid_n(L[a], rml[k], cnt[k], V));
         key[i] = pack_key(k, c[2], c[1], c[0]);
     }
     free(lvl);
@@ -350,9 +363,12 @@ long orc_list_grid(const double* x, const double* D0, long n, int d, const doubl
     int* lvl = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     double rml[ORC_KMAX];
     int nlev = orc_levels(D0, n, kappa_b, s, sigma0, lvl, rml);
+    long cnt[ORC_KMAX] = {0};
+    for (long i = 0; i < n; ++i) cnt[lvl[i]]++;
+    double V = box_volume(d, L);
     long ng[ORC_KMAX][3];
     for (int k = 0; k < nlev; ++k)
-        for (int a = 0; a < 3; ++a) ng[k][a] = a < d ? orc_grid_n(L[a], rml[k]) : 1;
+        for (int a = 0; a < 3; ++a) ng[k][a] = a < d ? orc_grid_n(L[a], rml[k], cnt[k], V) : 1;
     keyidx* ki = (keyidx*)malloc(sizeof(keyidx) * (size_t)(n > 0 ? n : 1));
     for (long i = 0; i < n; ++i) {
         long c[3] = {0, 0, 0};

@@ -70,7 +70,7 @@ double orc_n_trig(long n, int d, int Y, int X);
 double orc_rho(double D0, double kappa_b, double s, double sigma0);
 int    orc_levels(const double* D0, long n, double kappa_b, double s, double sigma0,
                   int* lvl, double* rho_max_lvl /* [32] */);
-long   orc_grid_n(double L, double rho_max_k);
+long   orc_grid_n(double L, double rho_max_k, long count, double V);
 void   orc_cell_keys(const double* x, const double* D0, long n, int d, const double* L,
                      double kappa_b, double s, double sigma0, uint64_t* key);
 int    orc_listed(const double* xi, const double* xj, int d, const double* L,

@@ -65,6 +65,8 @@ struct rcp_ctx {
 
     // neighbour structure
     double* rho = nullptr;
+    float4* xf = nullptr;    // binary32 copy (x/L, rho) for the search prefilter
+    float4* xsf = nullptr;   // the same in cell order
     int* lvl = nullptr;
     unsigned long long* key = nullptr;
     unsigned long long* key1 = nullptr;
@@ -82,6 +84,7 @@ struct rcp_ctx {
     unsigned long long* pairs2 = nullptr;
     unsigned int* col = nullptr;
     unsigned int* rowptr = nullptr;  // [N+1]
+    unsigned int* long_rows = nullptr;  // [N] rows longer than RCP_LONG_ROW
     unsigned long long pcap = 0;
     unsigned int* hist = nullptr;
     unsigned long long hist_cap = 0;
@@ -97,6 +100,10 @@ struct rcp_ctx {
     double kappa_rung = 0.0;
     double SD = 0, SD3 = 0, SD4 = 0, Dref = 0, Neff = 0, kappa0 = 0, sigma0 = 0;
     double mu = 0, eta_x = 0, eta_k = 0;
+
+    // kernel launches issued (a replayed graph counts each of its kernels)
+    long long launches = 0;
+    long long g_kernels = 0;
 
     // graph
     cudaGraphExec_t gexec = nullptr;
@@ -160,11 +167,23 @@ rcp_status sync_ctl(rcp_ctx* h)
     return RCP_OK;
 }
 
+// Mixed precision keeps positions in the fixed-point records; write their
+// binary64 view into the current position buffer before a binary64 consumer.
+rcp_status materialize(rcp_ctx* h)
+{
+    if (h->cfg.precision != RCP_MIXED) return RCP_OK;
+    h->launches += 1;
+    k_from_fixed<<<rcp_ceil_div(h->N, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->D0, h->xA, h->xB);
+    CK(cudaPeekAtLastError());
+    return RCP_OK;
+}
+
 // Tree sum of f(D0) (power 1, 3 or 4) into *dst (device), canonical order.
 rcp_status tree_sum_D(rcp_ctx* h, int power, double* dst)
 {
     long long n = h->N;
     unsigned int nb = rcp_ceil_div(n, RCP_TREE);
+    h->launches += 1;
     k_tree_terms<<<nb, RCP_TREE, 0, h->stream>>>(h->D0, n, power, h->part_e);
     CKL();
     double* a = h->part_e;
@@ -172,6 +191,7 @@ rcp_status tree_sum_D(rcp_ctx* h, int power, double* dst)
     n = nb;
     while (n > 1) {
         nb = rcp_ceil_div(n, RCP_TREE);
+        h->launches += 1;
         k_tree_pass<<<nb, RCP_TREE, 0, h->stream>>>(a, n, b);
         CKL();
         std::swap(a, b);
@@ -205,14 +225,17 @@ rcp_status scan_u32(rcp_ctx* h, const unsigned int* in, unsigned long long n, un
     if (n == 0) return RCP_OK;
     unsigned int nb = rcp_ceil_div(n, 4096);
     if (nb == 1) {
+        h->launches += 1;
         k_scan_block<<<1, 1024, 0, h->stream>>>(in, (long long)n, out, nullptr);
         CKL();
         return RCP_OK;
     }
     unsigned int* totals = tmp;
+    h->launches += 1;
     k_scan_block<<<nb, 1024, 0, h->stream>>>(in, (long long)n, out, totals);
     CKL();
     CKS(scan_u32(h, totals, nb, totals, tmp + nb + 1));
+    h->launches += 1;
     k_scan_add<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(out, (long long)n, totals);
     CKL();
     return RCP_OK;
@@ -249,9 +272,11 @@ rcp_status radix_sort(rcp_ctx* h, const unsigned long long* in, const unsigned i
     }
     unsigned int nb = rcp_ceil_div(n, RCP_SORT_THREADS * RCP_SORT_ITEMS);
     for (size_t p = 0; p < shifts.size(); ++p) {
+        h->launches += 1;
         k_radix_hist<<<nb, RCP_SORT_THREADS, 0, h->stream>>>(src, (long long)n, shifts[p], h->hist, nb);
         CKL();
         CKS(scan_u32(h, h->hist, 256ull * nb, h->hist, h->scan_tmp));
+        h->launches += 1;
         k_radix_scatter<<<nb, RCP_SORT_THREADS, 0, h->stream>>>(src, vsrc, (long long)n, shifts[p], h->hist, nb,
                                                                dst, vsrc ? vdst : nullptr);
         CKL();
@@ -288,9 +313,14 @@ rcp_status build(rcp_ctx* h)
 {
     const long long N = h->N;
     const unsigned int nbN = rcp_ceil_div(N, 256);
+    CKS(materialize(h));
+    h->launches += 1;
     k_build_begin<<<1, 1, 0, h->stream>>>(h->ctl, h->sigma0);
-    k_rho<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho);
+    h->launches += 1;
+    k_rho<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->xf);
+    h->launches += 1;
     k_level<<<nbN, 256, 0, h->stream>>>(h->ctl, N, h->rho, h->lvl);
+    h->launches += 1;
     k_grid<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
     CKL();
     CKS(sync_ctl(h));
@@ -315,6 +345,7 @@ rcp_status build(rcp_ctx* h)
         while ((1 << b) < nlev) ++b;
         for (int s : field_shifts(57, b)) shifts.push_back(s);
     }
+    h->launches += 1;
     k_cell_key<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->lvl, h->key, h->idx0);
     CKL();
     const unsigned long long* skeys = nullptr;
@@ -322,33 +353,45 @@ rcp_status build(rcp_ctx* h)
     CKS(radix_sort(h, h->key, h->idx0, (unsigned long long)N, shifts, h->key1, h->idx1, h->key2, h->idx2, &skeys,
                    &sidx));
     h->idx_sorted = sidx;
+    h->launches += 1;
+    k_gather_sorted<<<nbN, 256, 0, h->stream>>>(N, h->idx_sorted, h->xf, h->xsf);
     CK(cudaMemsetAsync(h->hkeys, 0xFF, sizeof(unsigned long long) * h->hcap, h->stream));
+    h->launches += 1;
     k_hash_heads<<<nbN, 256, 0, h->stream>>>(skeys, N, h->hkeys, h->hvals, h->hcap - 1);
     CKL();
     const int nbits = bits_for((unsigned long long)N);
-    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->hkeys,
-                                         h->hvals, h->hcap - 1, nullptr, h->cnt, nullptr, 0, nbits);
-    CKL();
-    CK(cudaMemsetAsync(h->cnt + N, 0, sizeof(unsigned int), h->stream));
-    CKS(scan_u32(h, h->cnt, (unsigned long long)N + 1, h->offs, h->scan_tmp));
-    unsigned int P32 = 0;
-    CK(cudaMemcpyAsync(&P32, h->offs + N, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    unsigned long long P = P32;
-    CKS(ensure_pair_capacity(h, P));
-    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->hkeys,
-                                         h->hvals, h->hcap - 1, h->offs, nullptr, h->pairs1, 1, nbits);
-    CKL();
+    unsigned long long P = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
+        h->launches += 1;
+        k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xf,
+                                             h->xsf, h->hkeys, h->hvals, h->hcap - 1, h->pairs1, h->pcap, nbits);
+        CKL();
+        CK(cudaMemcpyAsync(&P, &h->ctl->pair_cursor, sizeof(P), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (P <= h->pcap) break;
+        CKS(ensure_pair_capacity(h, P));  // entries beyond the old capacity were dropped: search again
+    }
+    if (P >= (1ull << 32)) return fail(h, RCP_ERR_CAPACITY, "more than 2^32 listed pairs");
     std::vector<int> ps = field_shifts(0, nbits);
     for (int s : field_shifts(nbits, nbits)) ps.push_back(s);
     const unsigned long long* spairs = nullptr;
     CKS(radix_sort(h, h->pairs1, nullptr, P, ps, h->pairs2, nullptr, h->pairs1, nullptr, &spairs, nullptr));
+    h->launches += 1;
     k_csr<<<rcp_ceil_div((P > (unsigned long long)N ? P : (unsigned long long)N) + 1, 256), 256, 0, h->stream>>>(
         spairs, (long long)P, N, nbits, h->rowptr, h->col);
+    h->launches += 1;
+    k_long_flags<<<nbN, 256, 0, h->stream>>>(h->rowptr, N, h->cnt);
+    CKL();
+    CKS(scan_u32(h, h->cnt, (unsigned long long)N, h->offs, h->scan_tmp));
+    h->launches += 1;
+    k_long_compact<<<nbN, 256, 0, h->stream>>>(h->ctl, h->cnt, h->offs, N, h->long_rows);
+    h->launches += 1;
     k_build_end<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb, P);
     CKL();
     if (h->cfg.precision == RCP_MIXED) {
-        k_to_fixed<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, h->rb);
+        h->launches += 1;
+        k_snap_records<<<nbN, 256, 0, h->stream>>>(h->ctl, N, h->rA, h->rB, h->rb);
         CKL();
     }
     h->P = P;
@@ -359,13 +402,19 @@ rcp_status build(rcp_ctx* h)
 // ---------------------------------------------------------------- evaluation
 unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_THREADS); }
 
+// Blocks of one pair-kernel launch (the mixed kernel adds the long-row blocks).
+unsigned int launch_blocks(const rcp_ctx* h)
+{
+    return pair_blocks(h) + (h->cfg.precision == RCP_MIXED ? RCP_LONG_BLOCKS : 0);
+}
+
 // Reduce the pair kernel's block partials to <= 8192 entries; returns the
 // buffers and count to hand to k_kappa_step.
 void prereduce(rcp_ctx* h, const double** pe, const double** pk, long long* nb)
 {
     const double* a = h->part_e;
     const double* b = h->part_k;
-    long long n = pair_blocks(h);
+    long long n = launch_blocks(h);
     bool flip = false;
     while (n > 8192) {
         unsigned int g = rcp_ceil_div(n, RCP_TREE);
@@ -390,15 +439,16 @@ size_t kappa_smem(long long nb)
 }
 
 // One iteration (or one evaluation) on the stream; optional events bracket
-// the pair kernel (ev[0], ev[1]) and close the iteration (ev[2]).
-void launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
+// the pair kernel (ev[0], ev[1]) and close the iteration (ev[2]).  Returns the
+// number of kernels it launched.
+int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
 {
     const unsigned int nb = pair_blocks(h);
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->cfg.precision == RCP_MIXED) {
-        k_pair_mixed<<<nb, RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m32, h->v32, h->rA,
-                                                              h->rB, h->rowptr, h->col, h->rb, h->part_e, h->part_k,
-                                                              mode, h->g);
+        k_pair_mixed<<<nb + RCP_LONG_BLOCKS, RCP_PAIR_THREADS, 0, h->stream>>>(
+            h->ctl, h->c, h->m32, h->v32, h->rA, h->rB, h->rowptr, h->col, h->long_rows, h->rb, h->part_e, h->part_k,
+            mode, h->g);
     } else {
         k_pair64<<<nb, RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr,
                                                           h->col, h->xb, h->part_e, h->part_k, mode, h->g);
@@ -410,6 +460,9 @@ void launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
     prereduce(h, &pe, &pk, &n);
     k_kappa_step<<<1, 1024, kappa_smem(n), h->stream>>>(h->ctl, h->c, pe, pk, n, mode);
     if (ev) cudaEventRecord(ev[2], h->stream);
+    int passes = 0;
+    for (long long m = launch_blocks(h); m > 8192; m = (m + RCP_TREE - 1) / RCP_TREE) ++passes;
+    return 2 + passes;
 }
 
 struct ProfileAcc {
@@ -435,7 +488,8 @@ rcp_status capture_graph(rcp_ctx* h)
     }
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    for (int t = 0; t < h->cfg.chunk; ++t) launch_iteration(h, RCP_MODE_ADAM);
+    h->g_kernels = 0;
+    for (int t = 0; t < h->cfg.chunk; ++t) h->g_kernels += launch_iteration(h, RCP_MODE_ADAM);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&h->gexec, graph, 0);
@@ -546,8 +600,8 @@ rcp_status rcp_destroy(rcp_handle h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
-                    h->lvl, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->hkeys, h->hvals, h->cnt,
-                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->hist, h->scan_tmp};
+                    h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->hkeys, h->hvals, h->cnt,
+                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->hist, h->scan_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->ctl_h) cudaFreeHost(h->ctl_h);
@@ -588,6 +642,9 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         c.L[a] = box[a];
         c.halfL[a] = 0.5 * box[a];
         c.qscale[a] = (float)(box[a] * 0x1.0p-32);
+        c.qinv[a] = (float)(0x1.0p32 / box[a]);
+        c.invL[a] = 1.0 / box[a];
+        c.Lf[a] = (float)box[a];
         if (box[a] < c.Lmin) c.Lmin = box[a];
         if (box[a] > c.Lmax) c.Lmax = box[a];
     }
@@ -625,7 +682,8 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         }
         CKS(dalloc(h, &h->g, 3 * n));
         CKS(dalloc(h, &h->xtmp, 3 * n));
-        size_t nparts = (n + RCP_TREE - 1) / RCP_TREE + (n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS + 8;
+        size_t nparts = (n + RCP_TREE - 1) / RCP_TREE + (n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS +
+                        RCP_LONG_BLOCKS + 8;
         CKS(dalloc(h, &h->part_e, nparts));
         CKS(dalloc(h, &h->part_k, nparts));
         CKS(dalloc(h, &h->part_e2, nparts));
@@ -633,6 +691,8 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CKS(dalloc(h, &h->ctl, 1));
         CK(cudaMallocHost((void**)&h->ctl_h, sizeof(RcpCtl)));
         CKS(dalloc(h, &h->rho, n));
+        CKS(dalloc(h, &h->xf, n));
+        CKS(dalloc(h, &h->xsf, n));
         CKS(dalloc(h, &h->lvl, n));
         CKS(dalloc(h, &h->key, n));
         CKS(dalloc(h, &h->key1, n));
@@ -647,6 +707,7 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CKS(dalloc(h, &h->cnt, n + 1));
         CKS(dalloc(h, &h->offs, n + 1));
         CKS(dalloc(h, &h->rowptr, n + 1));
+        CKS(dalloc(h, &h->long_rows, n));
         CKS(ensure_pair_capacity(h, 16 * (unsigned long long)n));
         CK(cudaFuncSetAttribute(k_kappa_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8192 * 8));
         CKS(ensure_scan_tmp(h, n + 1));
@@ -663,11 +724,13 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CK(cudaMemcpyAsync(h->ctl, &init, sizeof(RcpCtl), cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemcpyAsync(h->D0, diameters, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
         const unsigned int nb = rcp_ceil_div(N, 256);
+        h->launches += 1;
         k_init_positions<<<nb, 256, 0, h->stream>>>(seed, N, c, h->D0, h->xA);
         CKL();
         CKS(tree_sum_D(h, 1, &h->ctl->SD));
         CKS(tree_sum_D(h, 3, &h->ctl->SD3));
         CKS(tree_sum_D(h, 4, &h->ctl->SD4));
+        h->launches += 1;
         k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.V);
         CKL();
         CKS(sync_ctl(h));
@@ -680,6 +743,7 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         h->sigma0 = h->cfg.skin_abs * ((h->cfg.lr_x * h->kappa0) * h->Dref);
         build_rungs(h);
         if (h->cfg.precision == RCP_MIXED) {
+            h->launches += 1;
             k_to_fixed<<<nb, 256, 0, h->stream>>>(h->ctl, c, h->xA, h->xB, h->rA, h->rB, nullptr);
             CKL();
         }
@@ -712,14 +776,17 @@ rcp_status rcp_set_positions(rcp_handle h, const double* x, double kappa, int on
     else CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
     CKS(sync_ctl(h));
     double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
+    h->launches += 1;
     k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur);
     CKL();
     if (kappa > 0.0) CK(cudaMemcpyAsync(&h->ctl->kappa, &kappa, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (h->cfg.precision == RCP_MIXED) {
+        h->launches += 1;
         k_to_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, nullptr);
         CKL();
     }
     if (h->built) {
+        h->launches += 1;
         k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
         CKL();
     }
@@ -741,9 +808,10 @@ rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x, d
     if (!h) return RCP_ERR_ARG;
     CKS(ensure_list(h));
     // evaluation mode: mu from the argument, no iteration limit involved
+    h->launches += 1;
     k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, mu, 0.0, 0.0, h->cfg.tol, 1LL << 62, 0);
     CKL();
-    launch_iteration(h, RCP_MODE_GRAD);
+    h->launches += launch_iteration(h, RCP_MODE_GRAD);
     CKL();
     const size_t n = (size_t)h->N;
     if (on_device) {
@@ -770,21 +838,17 @@ rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, d
     CK(cudaMemcpyAsync(h->g, grad_x, sizeof(double) * 3 * n,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     if (!h->built) CKS(build(h));
+    h->launches += 1;
     if (h->cfg.precision == RCP_MIXED)
-        k_adam_mixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m32, h->v32, h->g,
-                                                                  lr_x);
+        k_adam_mixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->m32, h->v32, h->g,
+                                                                  h->rb, lr_x);
     else
         k_adam64<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->g,
                                                                h->xb, lr_x);
     CKL();
+    h->launches += 1;
     k_adam_kappa<<<1, 1, 0, h->stream>>>(h->ctl, h->c, dE_dkappa, lr_kappa);
     CKL();
-    if (h->cfg.precision == RCP_MIXED) {
-        k_to_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, nullptr);
-        CKL();
-        k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
-        CKL();
-    }
     CK(cudaStreamSynchronize(h->stream));
     return RCP_OK;
 }
@@ -792,9 +856,12 @@ rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, d
 static rcp_status do_shrink(rcp_ctx* h)
 {
     CKS(ensure_list(h));
+    CKS(materialize(h));
     unsigned long long inf = 0x7FF0000000000000ull;
     CK(cudaMemcpyAsync(&h->ctl->shrink_bits, &inf, sizeof(inf), cudaMemcpyHostToDevice, h->stream));
+    h->launches += 1;
     k_shrink<<<pair_blocks(h), RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rowptr, h->col);
+    h->launches += 1;
     k_shrink_final<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
     CKL();
     return sync_ctl(h);
@@ -809,9 +876,10 @@ rcp_status rcp_shrink(rcp_handle h, double* kappa_c, double* phi)
     return RCP_OK;
 }
 
-static void fill_result(rcp_ctx* h, rcp_result* out, double secs)
+static void fill_result(rcp_ctx* h, rcp_result* out, double secs, long long launches)
 {
     if (!out) return;
+    out->launches = launches;
     const RcpCtl* c = h->ctl_h;
     out->iters = c->iter;
     out->rebuilds = c->rebuilds;
@@ -834,6 +902,7 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
     if (stop) st = *stop;
     CKS(sync_ctl(h));
     const long long call_start = h->ctl_h->iter;
+    const long long launches0 = h->launches;
     rcp_status result = RCP_OK;
     for (;;) {
         RcpCtl* hc = h->ctl_h;
@@ -871,10 +940,11 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
         rung_values(h, h->rung, h->kappa_rung);
         if (!h->built || hc->need_rebuild) CKS(build(h));
         if (!prof) CKS(capture_graph(h));
+        h->launches += 1;
         k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, h->mu, h->eta_x, h->eta_k, h->cfg.tol, limit, R.final_rung);
         CKL();
         if (prof) {
-            launch_iteration(h, RCP_MODE_ADAM, prof->ev);
+            h->launches += launch_iteration(h, RCP_MODE_ADAM, prof->ev);
             CKL();
             CK(cudaEventSynchronize(prof->ev[2]));
             float a = 0.f, b = 0.f;
@@ -885,6 +955,7 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
             prof->launches += 1;
         } else {
             CK(cudaGraphLaunch(h->gexec, h->stream));
+            h->launches += h->g_kernels;
         }
         CKS(sync_ctl(h));
         hc = h->ctl_h;
@@ -899,7 +970,7 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
         }
     }
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    fill_result(h, out, secs);
+    fill_result(h, out, secs, h->launches - launches0);
     return result;
 }
 
@@ -926,8 +997,11 @@ rcp_status rcp_profile(rcp_handle h, long long iters, double* ms_pair, double* m
 static rcp_status verify_stop_mixed(rcp_ctx* h, bool* stop)
 {
     // binary64 maximum overlap of the state that the binary32 pass flagged
+    CKS(materialize(h));
+    h->launches += 1;
     k_maxdelta64<<<pair_blocks(h), RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rowptr,
                                                                       h->col);
+    h->launches += 1;
     k_verify_final<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
     CKL();
     CKS(sync_ctl(h));
@@ -941,7 +1015,9 @@ rcp_status rcp_state(rcp_handle h, double* x, double* m, double* v, rcp_scalars*
     CKS(sync_ctl(h));
     const size_t n = (size_t)h->N;
     if (x) {
+        CKS(materialize(h));
         const double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
+        h->launches += 1;
         k_get_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, cur, h->xtmp);
         CKL();
         CK(cudaMemcpyAsync(x, h->xtmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));

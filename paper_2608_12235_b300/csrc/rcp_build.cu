@@ -31,51 +31,97 @@ __global__ void k_build_begin(RcpCtl* ctl, double sigma0)
     ctl->rho_max_bits = 0ull;
     for (int k = 0; k < RCP_KMAX; ++k) {
         ctl->rho_lvl_bits[k] = 0ull;
+        ctl->lvl_count[k] = 0ull;
         ctl->rho_lvl[k] = 0.0;
     }
     ctl->nlev = 0;
+    ctl->pair_cursor = 0ull;
 }
 
-__global__ void k_rho(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double* rho)
+// Interaction radii, their maximum, and a binary32 copy of every sphere for
+// the search's prefilter: (x/L_x, y/L_y, z/L_z, rho) rounded to binary32.
+__global__ void __launch_bounds__(256) k_rho(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                                             double* rho, float4* xf)
 {
+    __shared__ double sh[8];
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0.0;
     if (i < c.N) {
-        const double4_32a* x = ctl->parity ? xB : xA;
-        r = (ctl->kappa_b * x[i].w) * (0.5 + c.skin_s) + ctl->sigma0;
+        const double4_32a p = (ctl->parity ? xB : xA)[i];
+        r = (ctl->kappa_b * p.w) * (0.5 + c.skin_s) + ctl->sigma0;
         rho[i] = r;
+        xf[i] = make_float4((float)(p.x * c.invL[0]), (float)(p.y * c.invL[1]), (float)(p.z * c.invL[2]), (float)r);
     }
     for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
-    if ((threadIdx.x & 31) == 0 && r > 0.0) atomicMax(&ctl->rho_max_bits, dbits(r));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) r = fmax(r, sh[w]);
+        if (r > 0.0) atomicMax(&ctl->rho_max_bits, dbits(r));
+    }
+}
+
+// The binary32 copies in cell order, so the candidates of one cell are
+// contiguous.
+__global__ void k_gather_sorted(long long N, const unsigned int* idx_sorted, const float4* xf, float4* xsf)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) xsf[t] = xf[idx_sorted[t]];
 }
 
 // Class k_i = max{k in [0, 31] : rho_i 2^k <= rho_max} (exact power-of-two
-// scaling), and the largest rho of each class.
-__global__ void k_level(RcpCtl* ctl, long long N, const double* rho, int* lvl)
+// scaling), the largest rho and the size of each class (aggregated per block
+// in shared memory, then one atomic per class and block).
+__global__ void __launch_bounds__(256) k_level(RcpCtl* ctl, long long N, const double* rho, int* lvl)
 {
+    __shared__ unsigned long long smax[RCP_KMAX];
+    __shared__ unsigned int scnt[RCP_KMAX];
+    if (threadIdx.x < RCP_KMAX) {
+        smax[threadIdx.x] = 0ull;
+        scnt[threadIdx.x] = 0u;
+    }
+    __syncthreads();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double rmax = bitsd(ctl->rho_max_bits);
-    const double r = rho[i];
-    int k = 0;
-    while (k + 1 < RCP_KMAX && ldexp(r, k + 1) <= rmax) ++k;
-    lvl[i] = k;
-    atomicMax(&ctl->rho_lvl_bits[k], dbits(r));
+    if (i < N) {
+        const double rmax = bitsd(ctl->rho_max_bits);
+        const double r = rho[i];
+        int k = 0;
+        while (k + 1 < RCP_KMAX && ldexp(r, k + 1) <= rmax) ++k;
+        lvl[i] = k;
+        atomicMax(&smax[k], dbits(r));
+        atomicAdd(&scnt[k], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < RCP_KMAX && scnt[threadIdx.x]) {
+        atomicMax(&ctl->rho_lvl_bits[threadIdx.x], smax[threadIdx.x]);
+        atomicAdd(&ctl->lvl_count[threadIdx.x], (unsigned long long)scnt[threadIdx.x]);
+    }
 }
 
-// Cells per axis of each class: the largest power of two n <= 2^19 with
-// L/n >= 2 rho_max(k).  Also the periodic-image rule: every listed pair must
-// be closer than half a box edge, i.e. 4 rho_max < min L.
+// Cells per axis of each class: the largest power of two n <= 2^19 whose
+// cell edge h = L/n is at least the class's largest interaction diameter
+// 2 rho_max(k) and whose cell holds at least RCP_CELL_OCC spheres of the class
+// on average (h^3 count >= RCP_CELL_OCC V; finer cells would only add empty
+// lookups).  Also the periodic-image rule: every listed pair must be closer
+// than half a box edge, i.e. 4 rho_max < min L.
+#define RCP_CELL_OCC 2.0
 __global__ void k_grid(RcpCtl* ctl, RcpConst c)
 {
     int nlev = 0;
     for (int k = 0; k < RCP_KMAX; ++k) {
         double r = bitsd(ctl->rho_lvl_bits[k]);
+        const double cnt = (double)ctl->lvl_count[k];
         ctl->rho_lvl[k] = r;
         for (int a = 0; a < 3; ++a) {
             unsigned int n = 1;
             if (r > 0.0)
-                while (n < RCP_NMAX_AXIS && c.L[a] / (double)(2 * n) >= 2.0 * r) n *= 2;
+                for (;;) {
+                    if (n >= RCP_NMAX_AXIS) break;
+                    const double h = c.L[a] / (double)(2 * n);
+                    if (!(h >= 2.0 * r)) break;
+                    if (!(((h * h) * h) * cnt >= RCP_CELL_OCC * c.V)) break;
+                    n *= 2;
+                }
             ctl->ng[k][a] = (int)n;
         }
         if (r > 0.0) nlev = k + 1;
@@ -279,72 +325,134 @@ __device__ __forceinline__ bool hfind(const unsigned long long* hkeys, const uin
 }
 
 // ---------------------------------------------------------------------------
-// Pair search.  fill = 0: count the entries sphere i emits; fill = 1: write
-// them at offs[i].  The inclusion test is the exact binary64 predicate
-//   dx^2 + dy^2 + dz^2 < (rho_i + rho_j)^2   (minimum image).
+// Pair search, one pass.  Each thread keeps the entries it finds in a small
+// local buffer; a full buffer is flushed to the global array through one
+// atomic reservation, and the final flush is aggregated over the warp.  The
+// order of entries in the array is arbitrary (they are radix-sorted next);
+// entries beyond `cap` are counted but not written, and the host re-runs the
+// search with a larger array.  The inclusion test is the exact binary64
+// predicate  dx^2 + dy^2 + dz^2 < (rho_i + rho_j)^2  (minimum image).
+#define RCP_SEARCH_BUF 32
+
+__device__ __forceinline__ void flush_entries(unsigned long long* pairs, unsigned long long cap,
+                                              unsigned long long base, const unsigned long long* buf, int n)
+{
+    for (int q = 0; q < n; ++q)
+        if (base + q < cap) pairs[base + q] = buf[q];
+}
+
+// Minimum-image component in box units (u in [0, 1]): the wrap is exact.
+__device__ __forceinline__ float wrap_unit(float d)
+{
+    if (d > 0.5f) d = d - 1.0f;
+    else if (d < -0.5f) d = d + 1.0f;
+    return d;
+}
+
+// Binary32 prefilter with rigorous bounds.  With u = fl32(x/L) (error <=
+// 2^-25 per coordinate) the binary32 distance r_f of a pair satisfies
+// |r_f - r| <= 1e-6 r + 5e-7 Lmax (the rounding analysis gives 2.3e-7 r +
+// 1.6e-7 Lmax), and fl32(rho_i) + fl32(rho_j) is within 1.2e-7 of rho_i +
+// rho_j (relative).  The accept and reject thresholds carry 2e-6 relative
+// margins on top; pairs inside the band where those bounds cannot decide are
+// settled by the exact binary64 predicate, so the listed set is exactly the
+// binary64 one.
 __global__ void __launch_bounds__(256)
 k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
-         const unsigned int* idx_sorted, const unsigned long long* hkeys, const uint2* hvals,
-         unsigned long long hmask, const unsigned int* offs, unsigned int* cnt, unsigned long long* pairs,
-         int fill, int nbits)
+         const unsigned int* idx_sorted, const float4* xf, const float4* xsf, const unsigned long long* hkeys,
+         const uint2* hvals, unsigned long long hmask, unsigned long long* pairs, unsigned long long cap, int nbits)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.N) return;
-    const double4_32a* x = ctl->parity ? xB : xA;
-    const double4_32a xi = x[i];
-    const double ri = rho[i];
-    const int li = lvl[i];
-    const double pi3[3] = {xi.x, xi.y, xi.z};
-    unsigned int count = 0;
-    unsigned long long w = fill ? offs[i] : 0ull;
-    for (int k = 0; k <= li; ++k) {
-        const double rk = ctl->rho_lvl[k];
-        if (!(rk > 0.0)) continue;
-        const double R = (ri + rk) + 1e-9 * c.Lmax;
-        long long lo[3];
-        unsigned int nc[3], ng[3];
-        for (int a = 0; a < 3; ++a) {
-            ng[a] = (unsigned int)ctl->ng[k][a];
-            long long l = (long long)floor(((pi3[a] - R) / c.L[a]) * (double)ng[a]);
-            long long h = (long long)floor(((pi3[a] + R) / c.L[a]) * (double)ng[a]);
-            if (h - l + 1 >= (long long)ng[a]) {
-                lo[a] = 0;
-                nc[a] = ng[a];
-            } else {
-                lo[a] = l;
-                nc[a] = (unsigned int)(h - l + 1);
+    unsigned long long buf[RCP_SEARCH_BUF];
+    int nb = 0;
+    if (i < c.N) {
+        const double4_32a* x = ctl->parity ? xB : xA;
+        const float4 ui = xf[i];
+        const double ri = rho[i];
+        const int li = lvl[i];
+        const float L0 = c.Lf[0], L1 = c.Lf[1], L2 = c.Lf[2];
+        const float Eabs = (float)(5e-7 * c.Lmax);
+        const float up = 1.0f + 2e-6f, dn = 1.0f - 2e-6f;
+        const float u3[3] = {ui.x, ui.y, ui.z};
+        for (int k = 0; k <= li; ++k) {
+            const double rk = ctl->rho_lvl[k];
+            if (!(rk > 0.0)) continue;
+            int lo[3];
+            unsigned int nc[3], ng[3];
+            for (int a = 0; a < 3; ++a) {
+                ng[a] = (unsigned int)ctl->ng[k][a];
+                // search radius in box units with a margin far above the
+                // binary32 errors of u and of the product below
+                const float Ru = (float)(((ri + rk) * c.invL[a]) * (1.0 + 1e-6) + 2e-6);
+                const float fn = (float)ng[a];
+                const int l = (int)floorf((u3[a] - Ru) * fn);
+                const int h = (int)floorf((u3[a] + Ru) * fn);
+                if (h - l + 1 >= (int)ng[a]) {
+                    lo[a] = 0;
+                    nc[a] = ng[a];
+                } else {
+                    lo[a] = l;
+                    nc[a] = (unsigned int)(h - l + 1);
+                }
             }
-        }
-        for (unsigned int cz = 0; cz < nc[2]; ++cz) {
-            const unsigned int z = (unsigned int)((lo[2] + cz) & (long long)(ng[2] - 1));
-            for (unsigned int cy = 0; cy < nc[1]; ++cy) {
-                const unsigned int y = (unsigned int)((lo[1] + cy) & (long long)(ng[1] - 1));
-                for (unsigned int cx = 0; cx < nc[0]; ++cx) {
-                    const unsigned int xx = (unsigned int)((lo[0] + cx) & (long long)(ng[0] - 1));
-                    uint2 range;
-                    if (!hfind(hkeys, hvals, hmask, pack_key((unsigned int)k, z, y, xx), range)) continue;
-                    for (unsigned int t = range.x; t < range.y; ++t) {
-                        const unsigned int j = idx_sorted[t];
-                        if ((long long)j == i) continue;
-                        const double4_32a xj = x[j];
-                        double dx = min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
-                        double dy = min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
-                        double dz = min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
-                        double r2 = dx * dx + dy * dy + dz * dz;
-                        double cut = ri + rho[j];
-                        if (!(r2 < cut * cut)) continue;
-                        if (fill) {
-                            pairs[w++] = ((unsigned long long)i << nbits) | j;
-                            if (k < li) pairs[w++] = ((unsigned long long)j << nbits) | (unsigned long long)i;
-                        } else {
-                            count += (k < li) ? 2u : 1u;
+            for (unsigned int cz = 0; cz < nc[2]; ++cz) {
+                const unsigned int z = (unsigned int)(lo[2] + (int)cz) & (ng[2] - 1);
+                for (unsigned int cy = 0; cy < nc[1]; ++cy) {
+                    const unsigned int y = (unsigned int)(lo[1] + (int)cy) & (ng[1] - 1);
+                    for (unsigned int cx = 0; cx < nc[0]; ++cx) {
+                        const unsigned int xx = (unsigned int)(lo[0] + (int)cx) & (ng[0] - 1);
+                        uint2 range;
+                        if (!hfind(hkeys, hvals, hmask, pack_key((unsigned int)k, z, y, xx), range)) continue;
+                        for (unsigned int t = range.x; t < range.y; ++t) {
+                            const float4 uj = xsf[t];
+                            const float dx = wrap_unit(ui.x - uj.x) * L0;
+                            const float dy = wrap_unit(ui.y - uj.y) * L1;
+                            const float dz = wrap_unit(ui.z - uj.z) * L2;
+                            const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+                            const float cut = ui.w + uj.w;
+                            const float hi = (cut * up + Eabs) * up;
+                            if (r2 > hi * hi) continue;                    // certainly not listed
+                            const unsigned int j = idx_sorted[t];
+                            if ((long long)j == i) continue;
+                            const float lo_in = (cut * dn - Eabs) * dn;
+                            bool in = lo_in > 0.0f && r2 < lo_in * lo_in;   // certainly listed
+                            if (!in) {
+                                // the band: exact binary64 predicate
+                                const double4_32a xi = x[i], xj = x[j];
+                                double ex = min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
+                                double ey = min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
+                                double ez = min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
+                                double d2 = ex * ex + ey * ey + ez * ez;
+                                double cc = ri + rho[j];
+                                in = d2 < cc * cc;
+                            }
+                            if (!in) continue;
+                            const int need = (k < li) ? 2 : 1;
+                            if (nb + need > RCP_SEARCH_BUF) {
+                                const unsigned long long base = atomicAdd(&ctl->pair_cursor, (unsigned long long)nb);
+                                flush_entries(pairs, cap, base, buf, nb);
+                                nb = 0;
+                            }
+                            buf[nb++] = ((unsigned long long)i << nbits) | j;
+                            if (k < li) buf[nb++] = ((unsigned long long)j << nbits) | (unsigned long long)i;
                         }
                     }
                 }
             }
         }
     }
-    if (!fill) cnt[i] = count;
+    // warp-aggregated final flush
+    const int lane = threadIdx.x & 31;
+    unsigned int incl = (unsigned int)nb;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(&ctl->pair_cursor, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    flush_entries(pairs, cap, base + (incl - (unsigned int)nb), buf, nb);
 }
 
 // CSR from the sorted pair keys: columns are the low bits; rowptr[i] is the
@@ -365,6 +473,23 @@ __global__ void k_csr(const unsigned long long* pairs, long long P, long long N,
         }
         rowptr[t] = (unsigned int)lo;
     }
+}
+
+// Rows longer than RCP_LONG_ROW, compacted in ascending order (flags, an
+// exclusive scan, then this kernel); the mixed pair kernel gives each a warp.
+__global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int* flags)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) flags[i] = (rowptr[i + 1] - rowptr[i] > RCP_LONG_ROW) ? 1u : 0u;
+}
+
+__global__ void k_long_compact(RcpCtl* ctl, const unsigned int* flags, const unsigned int* offs, long long N,
+                               unsigned int* long_rows)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (flags[i]) long_rows[offs[i]] = (unsigned int)i;
+    if (i == N - 1) ctl->n_long = offs[i] + flags[i];
 }
 
 __global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double4_32a* xb,

@@ -18,6 +18,8 @@
 #define RCP_SORT_THREADS 256
 #define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
 #define RCP_HASH_EMPTY 0xFFFFFFFFFFFFFFFFull
+#define RCP_LONG_ROW 32        // rows longer than this get a warp in the mixed pair kernel
+#define RCP_LONG_BLOCKS 296    // blocks (8 warps each) that loop over the long rows
 
 // Device-resident control block of one packing.  Kernels read the optimiser
 // scalars and the current rung's values from here, so one captured graph
@@ -42,11 +44,14 @@ struct RcpCtl {
     double kappa_b, sigma0;
     unsigned long long rho_max_bits;
     unsigned long long rho_lvl_bits[RCP_KMAX];
+    unsigned long long lvl_count[RCP_KMAX];
+    unsigned long long pair_cursor;   // entries emitted by the pair search
     double rho_lvl[RCP_KMAX];
     int nlev;
     int ng[RCP_KMAX][3];
     long long rebuilds;
     unsigned long long pairs;
+    unsigned int n_long;      // rows longer than RCP_LONG_ROW
     // constants and one-off results
     double SD, SD3, SD4;
     unsigned long long shrink_bits;
@@ -65,6 +70,9 @@ struct RcpConst {
     double Lmin, Lmax;
     double stop_margin;     // 0: binary64 overlaps; > 0: relative band that triggers a binary64 check
     float qscale[3];        // L_a / 2^32: fixed-point unit of axis a
+    float qinv[3];          // 2^32 / L_a
+    double invL[3];         // 1 / L_a
+    float Lf[3];            // L_a in binary32
 };
 
 enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
@@ -110,18 +118,23 @@ struct __align__(32) MixRec {
 };
 __global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                            MixRec* rA, MixRec* rB, MixRec* rb);
-__global__ void k_pair_mixed(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, float* m, float* v,
-                             MixRec* rA, MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
+__global__ void k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB,
+                             const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
                              const MixRec* rb, double* part_e, double* part_k, int mode, double* g_out);
 __global__ void k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                              const unsigned int* rowptr, const unsigned int* col);
 __global__ void k_verify_final(RcpCtl* ctl, RcpConst c);
-__global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, float* m, float* v,
-                             const double* g, double eta_x);
+__global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, MixRec* rA, MixRec* rB, float* m, float* v, const double* g,
+                             const MixRec* rb, double eta_x);
+__global__ void k_from_fixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const double* D0,
+                             double4_32a* xA, double4_32a* xB);
+__global__ void k_snap_records(RcpCtl* ctl, long long N, const MixRec* rA, const MixRec* rB, MixRec* rb);
 
 // ---- neighbour structure (rcp_build.cu) ----
 __global__ void k_build_begin(RcpCtl* ctl, double sigma0);
-__global__ void k_rho(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double* rho);
+__global__ void k_rho(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double* rho,
+                      float4* xf);
+__global__ void k_gather_sorted(long long N, const unsigned int* idx_sorted, const float4* xf, float4* xsf);
 __global__ void k_level(RcpCtl* ctl, long long N, const double* rho, int* lvl);
 __global__ void k_grid(RcpCtl* ctl, RcpConst c);
 __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const int* lvl,
@@ -136,10 +149,13 @@ __global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* o
 __global__ void k_hash_heads(const unsigned long long* keys, long long n, unsigned long long* hkeys,
                              uint2* hvals, unsigned long long hmask);
 __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
-                         const int* lvl, const unsigned int* idx_sorted, const unsigned long long* hkeys,
-                         const uint2* hvals, unsigned long long hmask, const unsigned int* offs,
-                         unsigned int* cnt, unsigned long long* pairs, int fill, int nbits);
+                         const int* lvl, const unsigned int* idx_sorted, const float4* xf, const float4* xsf,
+                         const unsigned long long* hkeys, const uint2* hvals, unsigned long long hmask,
+                         unsigned long long* pairs, unsigned long long cap, int nbits);
 __global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits,
                       unsigned int* rowptr, unsigned int* col);
+__global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int* flags);
+__global__ void k_long_compact(RcpCtl* ctl, const unsigned int* flags, const unsigned int* offs, long long N,
+                               unsigned int* long_rows);
 __global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double4_32a* xb,
                             unsigned long long P);

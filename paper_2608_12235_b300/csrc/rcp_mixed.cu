@@ -1,17 +1,20 @@
-// rcp_mixed.cu -- the mixed-precision pair kernel.
+// rcp_mixed.cu -- the mixed-precision path.
 //
-// Positions stay binary64 (the optimiser's state) and each sphere also keeps a
-// 32-byte pair record: a 32-bit fixed-point position q_a = floor(x_a / L_a
-// 2^32) per axis, the binary32 remainder l_a = x_a / L_a 2^32 - q_a, and
-// D_i^0.  The displacement of a pair is (q_i - q_j) in 32-bit integer
-// arithmetic -- the wrap-around of the subtraction is exactly the periodic
-// minimum image -- plus (l_i - l_j), scaled to length by L_a 2^-32, so every
-// pair's separation is formed to binary32 relative precision at any scale
-// (from the largest spheres down to D_max / 5e5).  Distance, overlap and the
-// pair terms are binary32; each row sums them with a compensated (2Sum)
-// accumulation, the row sums are widened to binary64 for the global trees,
-// and the Adam moments are binary32 while the position update is binary64.
-// The stopping test of App. A is confirmed in binary64 (k_maxdelta64).
+// State of a sphere: a 32-byte record holding its position as a 56-bit fixed
+// point per axis -- a 32-bit integer q_a (units of L_a 2^-32) plus a binary32
+// remainder l_a in [0, 1) of those units -- and D_i^0.  That is finer than
+// binary64 over most of the box (2^-56 L everywhere), and the periodic wrap is
+// the wrap-around of 32-bit integer arithmetic: the minimum-image separation
+// of a pair is (q_i - q_j) as a signed 32-bit integer plus (l_i - l_j),
+// exactly formed to binary32 relative precision at any scale (from the largest
+// spheres down to D_max / 5e5).  Distance, overlap and the pair terms are
+// binary32; each row sums them with a compensated (2Sum) accumulation; block
+// and global sums are widened to binary64; the Adam moments are binary32 and
+// the position update adds the step to the fixed-point record, carrying the
+// integer part into q.  No binary64 operation runs per pair or per sphere in
+// an iteration (binary64 throughput on B300 is a small fraction of binary32).
+// Binary64 positions are derived from the records when a binary64 consumer
+// needs them (neighbour build, stopping-test confirmation, shrink, export).
 #include "rcp_internal.cuh"
 
 __device__ __forceinline__ void to_fixed(double x, double L, int& q, float& l)
@@ -33,6 +36,13 @@ __device__ __forceinline__ MixRec make_rec(double4_32a p, const RcpConst& c)
     return r;
 }
 
+__device__ __forceinline__ double from_fixed(int q, float l, double L)
+{
+    double v = ((double)(unsigned int)q + (double)l) * (L * 0x1.0p-32);
+    if (v >= L) v = v - L;
+    return v;
+}
+
 // Displacement a - b of two records along one axis, in length units.
 __device__ __forceinline__ float rec_dx(int qa, float la, int qb, float lb, float scale)
 {
@@ -40,9 +50,9 @@ __device__ __forceinline__ float rec_dx(int qa, float la, int qb, float lb, floa
     return ((float)dq + (la - lb)) * scale;
 }
 
-// Records of the current positions, and the build snapshot when rb != NULL.
-__global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, MixRec* rA, MixRec* rB,
-                           MixRec* rb)
+// Records from binary64 positions (positions set from outside).
+__global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, MixRec* rA,
+                           MixRec* rB, MixRec* rb)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
@@ -52,8 +62,30 @@ __global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const
     if (rb) rb[i] = r;
 }
 
-// 2Sum accumulation: s + c carries the exact sum of the added binary32 terms
-// to within one rounding of the final value (Knuth's TwoSum, no FMA).
+// Binary64 view of the current records, with D_i^0 from the diameter array.
+__global__ void k_from_fixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const double* D0,
+                             double4_32a* xA, double4_32a* xB)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
+    const int parity = ctl->parity;
+    const MixRec r = (parity ? rB : rA)[i];
+    double4_32a* x = parity ? xB : xA;
+    x[i] = make_double4_32a(from_fixed(r.q.x, r.l.x, c.L[0]), from_fixed(r.q.y, r.l.y, c.L[1]),
+                            from_fixed(r.q.z, r.l.z, c.L[2]), D0[i]);
+}
+
+// Snapshot of the current records at a neighbour build.
+__global__ void k_snap_records(RcpCtl* ctl, long long N, const MixRec* rA, const MixRec* rB, MixRec* rb)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    rb[i] = (ctl->parity ? rB : rA)[i];
+}
+
+// 2Sum accumulation: s + c carries the sum of the added binary32 terms to
+// within about one rounding of the result (Knuth's TwoSum; no FMA contraction
+// in this library, so the error term is exact).
 __device__ __forceinline__ void acc2(float& s, float& c, float x)
 {
     const float t = s + x;
@@ -62,133 +94,223 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x)
     s = t;
 }
 
-__device__ __forceinline__ double block_tree256(double v, double* sh)
+// Warp sum of compensated pairs; the full value lands in lane 0.
+__device__ __forceinline__ double warp_sum2(float s, float c)
 {
-    for (int o = 1; o < 32; o <<= 1) v = v + __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int s = 1; s < RCP_PAIR_THREADS / 32; s <<= 1)
-            for (int k = 0; k + s < RCP_PAIR_THREADS / 32; k += 2 * s) sh[k] = sh[k] + sh[k + s];
-        r = sh[0];
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_down_sync(0xffffffffu, s, o);
+        const float co = __shfl_down_sync(0xffffffffu, c, o);
+        acc2(s, c, so);
+        c = c + co;
     }
-    __syncthreads();
-    return r;
+    return (double)s + (double)c;
 }
 
-__device__ __forceinline__ float warp_maxf(float v)
+// Per-block scalars, derived once per block from the control block.
+struct MixScalars {
+    float kappa, eps, h1, h2, be1, be2, o1, o2, eta, aeps;
+    float limA, limB;  // skin budget: theta (s kappa_b D + sigma0) (1 - 1e-5) = limA D + limB
+};
+
+__device__ __forceinline__ void mix_scalars(const RcpCtl* ctl, const RcpConst& c, MixScalars& s)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
+    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+    s.kappa = (float)ctl->kappa;
+    s.eps = (float)c.eps;
+    s.h1 = (float)(1.0 - b1);
+    s.h2 = (float)(1.0 - b2);
+    s.be1 = (float)c.beta1;
+    s.be2 = (float)c.beta2;
+    s.o1 = (float)(1.0 - c.beta1);
+    s.o2 = (float)(1.0 - c.beta2);
+    s.eta = (float)ctl->eta_x;
+    s.aeps = (float)c.adam_eps;
+    const double m = c.skin_theta * (1.0 - 1e-5);
+    s.limA = (float)(m * c.skin_s * ctl->kappa_b);
+    s.limB = (float)(m * ctl->sigma0);
 }
 
-// One thread per sphere i (row of the full list).  Same terms as k_pair64,
-// in binary32 on fixed-point displacements.
+// Adam on one axis of a record: binary32 moments, step added to the
+// fixed-point position (integer part into q, fraction into l).
+__device__ __forceinline__ void adam_fixed(float g, float& m, float& v, int& q, float& l, float qinv,
+                                           const MixScalars& s)
+{
+    m = s.be1 * m + s.o1 * g;
+    v = s.be2 * v + s.o2 * (g * g);
+    const float step = (s.eta * (m / s.h1)) / (sqrtf(v / s.h2) + s.aeps);
+    float d = -step * qinv;                      // displacement in fixed-point units
+    d = fminf(fmaxf(d, -1073741824.0f), 1073741824.0f);
+    const float di = floorf(d);
+    const float df = d - di;                     // exact, in [0, 1)
+    float ln = l + df;                           // [0, 2)
+    const float carry = floorf(ln);
+    ln = ln - carry;
+    q = (int)((unsigned int)q + (unsigned int)(int)di + (unsigned int)(int)carry);
+    l = ln;
+}
+
+// Terms of one listed pair (i, j) in binary32: gradient into (g, cg), the
+// j > i share of e and k into (es, ec), (ks, kc), and the overlap maximum.
+struct PairAcc {
+    float g0, g1, g2, c0, c1, c2;
+};
+
+__device__ __forceinline__ void pair_term(const MixRec& ri, const MixRec& rj, long long i, unsigned int j,
+                                          const MixScalars& S, const float sx, const float sy, const float sz,
+                                          PairAcc& a, float& es, float& ec, float& ks, float& kc, float& md)
+{
+    const float dx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, sx);
+    const float dy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, sy);
+    const float dz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, sz);
+    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+    const float r = sqrtf(r2);
+    const float dd = S.kappa * (0.5f * (ri.l.w + rj.l.w));
+    const float delta = 1.0f - r / dd;
+    if (delta > 0.0f) {
+        if (r > 0.0f) {
+            const float coef = (S.eps * delta) / (dd * r);
+            acc2(a.g0, a.c0, -coef * dx);
+            acc2(a.g1, a.c1, -coef * dy);
+            acc2(a.g2, a.c2, -coef * dz);
+        }
+        if ((long long)j > i) {
+            acc2(es, ec, (0.5f * S.eps) * (delta * delta));
+            acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) / S.kappa);
+        }
+        md = fmaxf(md, delta);
+    }
+}
+
+// Close row i: the Adam step of its record (Adam mode) or its gradient out.
+__device__ __forceinline__ void row_epilogue(RcpCtl* ctl, const RcpConst& c, const MixScalars& S, long long i,
+                                             const MixRec& ri, float g0, float g1, float g2, float* m, float* v,
+                                             MixRec* rout, const MixRec* rb, int mode, double* g_out)
+{
+    if (mode == RCP_MODE_ADAM) {
+        MixRec rn = ri;
+        float m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
+        float v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
+        adam_fixed(g0, m0, v0, rn.q.x, rn.l.x, c.qinv[0], S);
+        adam_fixed(g1, m1, v1, rn.q.y, rn.l.y, c.qinv[1], S);
+        adam_fixed(g2, m2, v2, rn.q.z, rn.l.z, c.qinv[2], S);
+        m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
+        v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
+        rout[i] = rn;
+        // skin check against the build snapshot, binary32 with a margin
+        const MixRec b = rb[i];
+        const float ex = rec_dx(rn.q.x, rn.l.x, b.q.x, b.l.x, c.qscale[0]);
+        const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, c.qscale[1]);
+        const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, c.qscale[2]);
+        const float lim = __fmaf_rn(S.limA, ri.l.w, S.limB);
+        if (ex * ex + ey * ey + ez * ez > lim * lim) atomicOr(&ctl->disp_flag, 1u);
+    } else {
+        g_out[3 * i] = (double)g0;
+        g_out[3 * i + 1] = (double)g1;
+        g_out[3 * i + 2] = (double)g2;
+    }
+}
+
+__device__ __forceinline__ float warp_sum2f(float s, float c)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float co = __shfl_xor_sync(0xffffffffu, c, o);
+        acc2(s, c, so);
+        c = c + co;
+    }
+    return s + c;
+}
+
+// The pair kernel of the mixed path.  Blocks [0, RCP_LONG_BLOCKS) give one
+// warp to each row longer than RCP_LONG_ROW (the rows of the largest spheres,
+// which hold hundreds of small neighbours): lanes stride over the row and the
+// gradient is reduced with compensated shuffles.  The other blocks give one
+// thread to each remaining row, loading partners four at a time.  Both end
+// with the row's Adam step; block partials of e and k go to part_e/part_k.
 __global__ void __launch_bounds__(RCP_PAIR_THREADS)
-k_pair_mixed(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, float* m, float* v, MixRec* rA, MixRec* rB,
-             const unsigned int* rowptr, const unsigned int* col, const MixRec* rb, double* part_e, double* part_k,
-             int mode, double* g_out)
+k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB, const unsigned int* rowptr,
+             const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
+             double* part_k, int mode, double* g_out)
 {
-    __shared__ double sh[RCP_PAIR_THREADS / 32];
+    __shared__ double she[RCP_PAIR_THREADS / 32], shk[RCP_PAIR_THREADS / 32];
     __shared__ float shm[RCP_PAIR_THREADS / 32];
+    __shared__ MixScalars S;
     if (ctl->halted) return;
+    if (threadIdx.x == 0) mix_scalars(ctl, c, S);
+    __syncthreads();
     const int parity = ctl->parity;
     const MixRec* __restrict__ rin = parity ? rB : rA;
     MixRec* __restrict__ rout = parity ? rA : rB;
-    const double kappa = ctl->kappa;
-    const float kf = (float)kappa;
-    const float epsf = (float)c.eps;
     const float sx = c.qscale[0], sy = c.qscale[1], sz = c.qscale[2];
-    const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
-    if (i < c.N) {
-        const MixRec ri = rin[i];
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-        const unsigned int t1 = rowptr[i + 1];
-        for (unsigned int t = rowptr[i]; t < t1; ++t) {
-            const unsigned int j = col[t];
-            const MixRec rj = rin[j];
-            const float dx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, sx);
-            const float dy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, sy);
-            const float dz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, sz);
-            const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
-            const float r = sqrtf(r2);
-            const float dd = kf * (0.5f * (ri.l.w + rj.l.w));
-            const float delta = 1.0f - r / dd;
-            if (delta > 0.0f) {
-                if (r > 0.0f) {
-                    const float coef = (epsf * delta) / (dd * r);
-                    acc2(g0, c0, -coef * dx);
-                    acc2(g1, c1, -coef * dy);
-                    acc2(g2, c2, -coef * dz);
-                }
-                if ((long long)j > i) {
-                    acc2(es, ec, (0.5f * epsf) * (delta * delta));
-                    acc2(ks, kc, ((epsf * delta) * (1.0f - delta)) / kf);
-                }
-                md = fmaxf(md, delta);
+    if (blockIdx.x < RCP_LONG_BLOCKS) {
+        const unsigned int nlong = ctl->n_long;
+        const unsigned int nw = RCP_LONG_BLOCKS * (RCP_PAIR_THREADS / 32);
+        for (unsigned int r = blockIdx.x * (RCP_PAIR_THREADS / 32) + warp; r < nlong; r += nw) {
+            const long long i = long_rows[r];
+            const MixRec ri = rin[i];
+            PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const unsigned int t1 = rowptr[i + 1];
+            for (unsigned int t = rowptr[i] + lane; t < t1; t += 32) {
+                const unsigned int j = col[t];
+                pair_term(ri, rin[j], i, j, S, sx, sy, sz, a, es, ec, ks, kc, md);
             }
+            const float g0 = warp_sum2f(a.g0, a.c0);
+            const float g1 = warp_sum2f(a.g1, a.c1);
+            const float g2 = warp_sum2f(a.g2, a.c2);
+            if (lane == 0) row_epilogue(ctl, c, S, i, ri, g0, g1, g2, m, v, rout, rb, mode, g_out);
         }
-        g0 = g0 + c0;
-        g1 = g1 + c1;
-        g2 = g2 + c2;
-        if (mode == RCP_MODE_ADAM) {
-            const double4_32a* xin = parity ? xB : xA;
-            double4_32a* xout = parity ? xA : xB;
-            const double4_32a xi = xin[i];
-            const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
-            const float h1 = (float)(1.0 - b1), h2 = (float)(1.0 - b2);
-            const float be1 = (float)c.beta1, be2 = (float)c.beta2;
-            const float o1 = (float)(1.0 - c.beta1), o2 = (float)(1.0 - c.beta2);
-            const float etaf = (float)ctl->eta_x, aeps = (float)c.adam_eps;
-            float gg[3] = {g0, g1, g2};
-            double p[3] = {xi.x, xi.y, xi.z};
-            for (int a = 0; a < 3; ++a) {
-                float mm = be1 * m[3 * i + a] + o1 * gg[a];
-                float vv = be2 * v[3 * i + a] + o2 * (gg[a] * gg[a]);
-                m[3 * i + a] = mm;
-                v[3 * i + a] = vv;
-                const float step = (etaf * (mm / h1)) / (sqrtf(vv / h2) + aeps);
-                double q = p[a] - (double)step;
-                if (q < 0.0) q = q + c.L[a];
-                if (q >= c.L[a]) q = q - c.L[a];
-                p[a] = q;
+    } else {
+        const long long i = (long long)(blockIdx.x - RCP_LONG_BLOCKS) * RCP_PAIR_THREADS + threadIdx.x;
+        if (i < c.N) {
+            const unsigned int t0 = rowptr[i], t1 = rowptr[i + 1];
+            if (t1 - t0 <= RCP_LONG_ROW) {
+                const MixRec ri = rin[i];
+                PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                unsigned int t = t0;
+                for (; t + 4 <= t1; t += 4) {
+                    const unsigned int j0 = col[t], j1 = col[t + 1], j2 = col[t + 2], j3 = col[t + 3];
+                    const MixRec r0 = rin[j0], r1 = rin[j1], r2 = rin[j2], r3 = rin[j3];
+                    pair_term(ri, r0, i, j0, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                    pair_term(ri, r1, i, j1, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                    pair_term(ri, r2, i, j2, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                    pair_term(ri, r3, i, j3, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                }
+                for (; t < t1; ++t) {
+                    const unsigned int j = col[t];
+                    pair_term(ri, rin[j], i, j, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                }
+                row_epilogue(ctl, c, S, i, ri, a.g0 + a.c0, a.g1 + a.c1, a.g2 + a.c2, m, v, rout, rb, mode, g_out);
             }
-            const double4_32a xn = make_double4_32a(p[0], p[1], p[2], xi.w);
-            xout[i] = xn;
-            const MixRec rn = make_rec(xn, c);
-            rout[i] = rn;
-            // skin check against the build snapshot, binary32 with a margin
-            const MixRec b = rb[i];
-            const float ex = rec_dx(rn.q.x, rn.l.x, b.q.x, b.l.x, sx);
-            const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, sy);
-            const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, sz);
-            const float lim = (float)(c.skin_theta * (c.skin_s * ctl->kappa_b * xi.w + ctl->sigma0) * (1.0 - 1e-5));
-            if (ex * ex + ey * ey + ez * ez > lim * lim) atomicOr(&ctl->disp_flag, 1u);
-        } else {
-            g_out[3 * i] = (double)g0;
-            g_out[3 * i + 1] = (double)g1;
-            g_out[3 * i + 2] = (double)g2;
         }
     }
-    const double se = block_tree256((double)es + (double)ec, sh);
-    const double sk = block_tree256((double)ks + (double)kc, sh);
-    const float wm = warp_maxf(md);
-    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = wm;
+    const double we = warp_sum2(es, ec);
+    const double wk = warp_sum2(ks, kc);
+    float wm = md;
+    for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_down_sync(0xffffffffu, wm, o));
+    if (lane == 0) {
+        she[warp] = we;
+        shk[warp] = wk;
+        shm[warp] = wm;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float bm = shm[0];
-        for (int w = 1; w < RCP_PAIR_THREADS / 32; ++w) bm = fmaxf(bm, shm[w]);
+        double se = 0.0, sk = 0.0;
+        float bm = 0.f;
+        for (int w = 0; w < RCP_PAIR_THREADS / 32; ++w) {
+            se = se + she[w];
+            sk = sk + shk[w];
+            bm = fmaxf(bm, shm[w]);
+        }
         part_e[blockIdx.x] = se;
         part_k[blockIdx.x] = sk;
         if (bm > 0.f) atomicMax(&ctl->maxdelta_bits, dbits((double)bm));
     }
 }
 
-// Binary64 maximum overlap over the listed pairs of the current state, same
-// arithmetic as k_pair64 (confirms a binary32 stop candidate).
+// Binary64 maximum overlap over the listed pairs of the current binary64
+// positions, same arithmetic as k_pair64 (confirms a binary32 stop candidate).
 __global__ void __launch_bounds__(RCP_PAIR_THREADS)
 k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const unsigned int* rowptr,
              const unsigned int* col)
@@ -217,32 +339,34 @@ k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* 
     if ((threadIdx.x & 31) == 0 && md > 0.0) atomicMax(&ctl->md64_bits, dbits(md));
 }
 
-// Standalone Adam step in mixed precision (rcp_adam_step): binary32 moments,
-// binary64 position update, in place on the current buffer.
-__global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, float* m, float* v, const double* g,
-                             double eta_x)
+// Standalone Adam step in mixed precision (rcp_adam_step): binary32 moments
+// on the fixed-point records, in place, with the skin check.
+__global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, MixRec* rA, MixRec* rB, float* m, float* v, const double* g,
+                             const MixRec* rb, double eta_x)
 {
+    __shared__ MixScalars S;
+    if (threadIdx.x == 0) {
+        mix_scalars(ctl, c, S);
+        S.eta = (float)eta_x;
+    }
+    __syncthreads();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
-    double4_32a* x = ctl->parity ? xB : xA;
-    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
-    const float h1 = (float)(1.0 - b1), h2 = (float)(1.0 - b2);
-    const float be1 = (float)c.beta1, be2 = (float)c.beta2;
-    const float o1 = (float)(1.0 - c.beta1), o2 = (float)(1.0 - c.beta2);
-    const float etaf = (float)eta_x, aeps = (float)c.adam_eps;
-    double4_32a xi = x[i];
-    double p[3] = {xi.x, xi.y, xi.z};
+    MixRec* r = ctl->parity ? rB : rA;
+    MixRec rn = r[i];
     for (int a = 0; a < 3; ++a) {
-        const float gg = (float)g[3 * i + a];
-        float mm = be1 * m[3 * i + a] + o1 * gg;
-        float vv = be2 * v[3 * i + a] + o2 * (gg * gg);
+        float mm = m[3 * i + a], vv = v[3 * i + a];
+        int* q = a == 0 ? &rn.q.x : (a == 1 ? &rn.q.y : &rn.q.z);
+        float* l = a == 0 ? &rn.l.x : (a == 1 ? &rn.l.y : &rn.l.z);
+        adam_fixed((float)g[3 * i + a], mm, vv, *q, *l, c.qinv[a], S);
         m[3 * i + a] = mm;
         v[3 * i + a] = vv;
-        const float step = (etaf * (mm / h1)) / (sqrtf(vv / h2) + aeps);
-        double q = p[a] - (double)step;
-        if (q < 0.0) q = q + c.L[a];
-        if (q >= c.L[a]) q = q - c.L[a];
-        p[a] = q;
     }
-    x[i] = make_double4_32a(p[0], p[1], p[2], xi.w);
+    r[i] = rn;
+    const MixRec b = rb[i];
+    const float ex = rec_dx(rn.q.x, rn.l.x, b.q.x, b.l.x, c.qscale[0]);
+    const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, c.qscale[1]);
+    const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, c.qscale[2]);
+    const float lim = __fmaf_rn(S.limA, rn.l.w, S.limB);
+    if (ex * ex + ey * ey + ez * ez > lim * lim) atomicOr(&ctl->disp_flag, 1u);
 }

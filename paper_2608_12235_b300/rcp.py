@@ -43,7 +43,8 @@ class rcp_stop(C.Structure):
 class rcp_result(C.Structure):
     _fields_ = [("iters", C.c_longlong), ("rebuilds", C.c_longlong), ("pairs", C.c_longlong),
                 ("stopped", C.c_int), ("kappa", C.c_double), ("max_delta", C.c_double),
-                ("energy", C.c_double), ("kappa_c", C.c_double), ("phi", C.c_double), ("seconds", C.c_double)]
+                ("energy", C.c_double), ("kappa_c", C.c_double), ("phi", C.c_double), ("seconds", C.c_double),
+                ("launches", C.c_longlong)]
 
 
 class rcp_scalars(C.Structure):
@@ -248,6 +249,7 @@ class RunSummary:
     kappa_c: float
     phi: float
     seconds: float
+    launches: int
 
 
 class Packing:
@@ -278,7 +280,7 @@ class Packing:
     def run(self, max_iters=0, max_seconds=0.0, shrink=True) -> RunSummary:
         r = rcp_run(self.h, max_iters, max_seconds, shrink)
         return RunSummary(r.iters, r.rebuilds, r.pairs, bool(r.stopped), r.kappa, r.max_delta, r.energy,
-                          r.kappa_c, r.phi, r.seconds)
+                          r.kappa_c, r.phi, r.seconds, r.launches)
 
     def state(self):
         return rcp_state(self.h)

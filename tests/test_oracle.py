@@ -294,16 +294,21 @@ def test_levels_and_cells_follow_definition(orc):
     for i in range(0, 3000, 7):
         k = int(lvl[i])
         assert math.ldexp(rho[i], k) <= rmax and (k == 31 or math.ldexp(rho[i], k + 1) > rmax)
+    cnt = np.bincount(lvl)
     for k in range(len(rml)):
         assert rml[k] == rho[lvl == k].max()
-        nk = orc.grid_n(1.0, rml[k])
-        assert nk & (nk - 1) == 0 and (nk == 1 or 1.0 / nk >= 2 * rml[k])
-        assert nk == 2 ** 19 or 1.0 / (2 * nk) < 2 * rml[k]
+        nk = orc.grid_n(1.0, rml[k], int(cnt[k]), 1.0)
+        # power of two; cells no smaller than the largest interaction diameter
+        # and holding >= 2 spheres of the class on average; the next finer grid
+        # would break one of the two bounds
+        h = 1.0 / nk
+        assert nk & (nk - 1) == 0 and (nk == 1 or (h >= 2 * rml[k] and h ** 3 * cnt[k] >= 2.0))
+        assert nk == 2 ** 19 or (h / 2 < 2 * rml[k] or (h / 2) ** 3 * cnt[k] < 2.0)
     x = orc.init_positions(4, 3000)
     key = orc.cell_keys(x, D0, 1.0, kb, s, sg)
     assert np.array_equal((key >> np.uint64(57)).astype(int), lvl)
     for i in range(0, 3000, 11):
-        nk = orc.grid_n(1.0, rml[int(lvl[i])])
+        nk = orc.grid_n(1.0, rml[int(lvl[i])], int(cnt[int(lvl[i])]), 1.0)
         c = [int((int(key[i]) >> sh) & (2 ** 19 - 1)) for sh in (0, 19, 38)]
         assert c == [min(int(math.floor(x[i, a] * nk)), nk - 1) for a in range(3)]
 
