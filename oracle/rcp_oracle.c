@@ -200,18 +200,18 @@ int orc_levels(const double* D0, long n, double kappa_b, double s, double sigma0
 }
 
 /* Cells per axis at a level: the largest power of two n <= 2^19 whose cell
- * edge h = L/n is at least the level's largest interaction diameter
- * 2 rho_max and whose cell volume h^3 holds at least ORC_OCC spheres of the
- * level on average, h^3 count >= ORC_OCC V (cells smaller than either bound
- * only add empty lookups).  V is the box volume, count the level's size. */
+ * volume holds at least ORC_OCC spheres of the level on average,
+ * h^3 count >= ORC_OCC V with h = L/n (V the box volume, count the level's
+ * size).  The search scans every cell within the search radius, so any cell
+ * size is correct; this one balances cell lookups against candidates. */
 #define ORC_OCC 2.0
 long orc_grid_n(double L, double rho_max_k, long count, double V)
 {
+    (void)rho_max_k;
     long n = 1;
     for (;;) {
         if (n >= ORC_NMAX) break;
         double h = L / (double)(2 * n);
-        if (!(h >= 2.0 * rho_max_k)) break;
         if (!(((h * h) * h) * (double)count >= ORC_OCC * V)) break;
         n *= 2;
     }

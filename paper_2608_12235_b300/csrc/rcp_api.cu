@@ -644,6 +644,11 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         c.qscale[a] = (float)(box[a] * 0x1.0p-32);
         c.qinv[a] = (float)(0x1.0p32 / box[a]);
         c.invL[a] = 1.0 / box[a];
+        {
+            const double sc = box[a] * 0x1.0p-32;
+            c.qs_hi[a] = (float)sc;
+            c.qs_lo[a] = (float)(sc - (double)c.qs_hi[a]);
+        }
         c.Lf[a] = (float)box[a];
         if (box[a] < c.Lmin) c.Lmin = box[a];
         if (box[a] > c.Lmax) c.Lmax = box[a];

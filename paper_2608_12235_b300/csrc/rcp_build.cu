@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(256) k_level(RcpCtl* ctl, long long N, const d
 }
 
 // Cells per axis of each class: the largest power of two n <= 2^19 whose
-// cell edge h = L/n is at least the class's largest interaction diameter
-// 2 rho_max(k) and whose cell holds at least RCP_CELL_OCC spheres of the class
-// on average (h^3 count >= RCP_CELL_OCC V; finer cells would only add empty
-// lookups).  Also the periodic-image rule: every listed pair must be closer
-// than half a box edge, i.e. 4 rho_max < min L.
+// cell holds at least RCP_CELL_OCC spheres of the class on average
+// (h^3 count >= RCP_CELL_OCC V, h = L/n).  The search scans every cell within
+// its radius, so any cell size is correct; this one balances hash lookups
+// against candidates.  Also the periodic-image rule: every listed pair must
+// be closer than half a box edge, i.e. 4 rho_max < min L.
 #define RCP_CELL_OCC 2.0
 __global__ void k_grid(RcpCtl* ctl, RcpConst c)
 {
@@ -118,7 +118,6 @@ __global__ void k_grid(RcpCtl* ctl, RcpConst c)
                 for (;;) {
                     if (n >= RCP_NMAX_AXIS) break;
                     const double h = c.L[a] / (double)(2 * n);
-                    if (!(h >= 2.0 * r)) break;
                     if (!(((h * h) * h) * cnt >= RCP_CELL_OCC * c.V)) break;
                     n *= 2;
                 }

@@ -19,7 +19,7 @@
 #define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
 #define RCP_HASH_EMPTY 0xFFFFFFFFFFFFFFFFull
 #define RCP_LONG_ROW 32        // rows longer than this get a warp in the mixed pair kernel
-#define RCP_LONG_BLOCKS 296    // blocks (8 warps each) that loop over the long rows
+#define RCP_LONG_BLOCKS 592    // blocks (8 warps each) that loop over the long rows
 
 // Device-resident control block of one packing.  Kernels read the optimiser
 // scalars and the current rung's values from here, so one captured graph
@@ -73,6 +73,7 @@ struct RcpConst {
     float qinv[3];          // 2^32 / L_a
     double invL[3];         // 1 / L_a
     float Lf[3];            // L_a in binary32
+    float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
 };
 
 enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
@@ -113,8 +114,8 @@ __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c);
 // binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0.  One
 // 32-byte sector per gather.
 struct __align__(32) MixRec {
-    int4 q;    // qx, qy, qz, unused
-    float4 l;  // lx, ly, lz, D0
+    int4 q;    // qx, qy, qz, and the bits of the binary32 D_i^0 - fl32(D_i^0)
+    float4 l;  // lx, ly, lz, fl32(D_i^0)
 };
 __global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                            MixRec* rA, MixRec* rB, MixRec* rb);

@@ -31,8 +31,8 @@ __device__ __forceinline__ MixRec make_rec(double4_32a p, const RcpConst& c)
     to_fixed(p.x, c.L[0], r.q.x, r.l.x);
     to_fixed(p.y, c.L[1], r.q.y, r.l.y);
     to_fixed(p.z, c.L[2], r.q.z, r.l.z);
-    r.q.w = 0;
     r.l.w = (float)p.w;
+    r.q.w = __float_as_int((float)(p.w - (double)r.l.w));
     return r;
 }
 
@@ -94,8 +94,8 @@ __device__ __forceinline__ void acc2(float& s, float& c, float x)
     s = t;
 }
 
-// Warp sum of compensated pairs; the full value lands in lane 0.
-__device__ __forceinline__ double warp_sum2(float s, float c)
+// Warp sum of compensated pairs; the full (s, c) lands in lane 0.
+__device__ __forceinline__ void warp_sum2(float& s, float& c)
 {
     for (int o = 16; o > 0; o >>= 1) {
         const float so = __shfl_down_sync(0xffffffffu, s, o);
@@ -103,12 +103,11 @@ __device__ __forceinline__ double warp_sum2(float s, float c)
         acc2(s, c, so);
         c = c + co;
     }
-    return (double)s + (double)c;
 }
 
 // Per-block scalars, derived once per block from the control block.
 struct MixScalars {
-    float kappa, eps, h1, h2, be1, be2, o1, o2, eta, aeps;
+    float kappa, kappa_lo, eps, h1, h2, be1, be2, o1, o2, eta, aeps;
     float limA, limB;  // skin budget: theta (s kappa_b D + sigma0) (1 - 1e-5) = limA D + limB
 };
 
@@ -116,6 +115,7 @@ __device__ __forceinline__ void mix_scalars(const RcpCtl* ctl, const RcpConst& c
 {
     const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
     s.kappa = (float)ctl->kappa;
+    s.kappa_lo = (float)(ctl->kappa - (double)s.kappa);
     s.eps = (float)c.eps;
     s.h1 = (float)(1.0 - b1);
     s.h2 = (float)(1.0 - b2);
@@ -149,36 +149,118 @@ __device__ __forceinline__ void adam_fixed(float g, float& m, float& v, int& q, 
     l = ln;
 }
 
-// Terms of one listed pair (i, j) in binary32: gradient into (g, cg), the
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProd).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = a * b;
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Displacement a - b along one axis as an unevaluated binary32 sum hi + lo in
+// length units, exact up to ~2^-40 relative: the integer part is split so
+// that no digit of the remainder difference is lost.
+__device__ __forceinline__ void rec_dx2(int qa, float la, int qb, float lb, float shi, float slo, float& hi,
+                                        float& lo)
+{
+    const int dq = (int)((unsigned int)qa - (unsigned int)qb);
+    const float hq = (float)dq;
+    const float eq = (float)((long long)dq - __float2ll_rn(hq));   // |eq| <= 64, exact
+    float s1, e1, x_hi, t;
+    two_sum(eq, la - lb, s1, e1);
+    two_sum(hq, s1, x_hi, t);
+    const float x_lo = t + e1;
+    float p, pe;
+    two_prod(x_hi, shi, p, pe);
+    hi = p;
+    lo = pe + (x_hi * slo + x_lo * shi);
+}
+
+// Overlap of a pair that the binary32 pretest could not reject, with the
+// cancellation in d - r removed: N = d^2 - r^2 is formed in binary32 pairs
+// (d = kappa (D_i + D_j)/2 and r^2 from the split displacements), then
+// u = N / d^2 and delta = 1 - sqrt(1 - u) = u / (1 + sqrt(1 - u)).  Returns
+// delta (<= 0 for no overlap), r, and the displacement (binary32).
+__device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& rj, const MixScalars& S,
+                                               const RcpConst& c, float& dx, float& dy, float& dz, float& r)
+{
+    float xh, xl, yh, yl, zh, zl;
+    rec_dx2(ri.q.x, ri.l.x, rj.q.x, rj.l.x, c.qs_hi[0], c.qs_lo[0], xh, xl);
+    rec_dx2(ri.q.y, ri.l.y, rj.q.y, rj.l.y, c.qs_hi[1], c.qs_lo[1], yh, yl);
+    rec_dx2(ri.q.z, ri.l.z, rj.q.z, rj.l.z, c.qs_hi[2], c.qs_lo[2], zh, zl);
+    // r^2
+    float px, ex, py, ey, pz, ez;
+    two_prod(xh, xh, px, ex);
+    two_prod(yh, yh, py, ey);
+    two_prod(zh, zh, pz, ez);
+    float s1, t1, s2, t2;
+    two_sum(px, py, s1, t1);
+    two_sum(s1, pz, s2, t2);
+    const float r2l = ((t1 + t2) + (ex + ey + ez)) + 2.0f * ((xh * xl + yh * yl) + zh * zl);
+    // d = kappa (D_i + D_j) / 2
+    float sh, se;
+    two_sum(ri.l.w, rj.l.w, sh, se);
+    const float sl = se + (__int_as_float(ri.q.w) + __int_as_float(rj.q.w));
+    float dh, de;
+    two_prod(S.kappa, 0.5f * sh, dh, de);
+    const float dl = de + (S.kappa * (0.5f * sl) + S.kappa_lo * (0.5f * sh));
+    // d^2 - r^2
+    float d2h, d2e;
+    two_prod(dh, dh, d2h, d2e);
+    const float d2l = d2e + 2.0f * dh * dl;
+    float nh, ne;
+    two_sum(d2h, -s2, nh, ne);
+    const float n = nh + (ne + (d2l - r2l));
+    dx = xh;
+    dy = yh;
+    dz = zh;
+    r = sqrtf(s2);
+    if (!(n > 0.0f)) return n;
+    const float u = n / d2h;
+    return u / (1.0f + sqrtf(1.0f - u));
+}
+
+// Terms of one listed pair (i, j): gradient into the compensated (g, c), the
 // j > i share of e and k into (es, ec), (ks, kc), and the overlap maximum.
+// Pairs are first tested in plain binary32 (r^2 > d^2 (1 + 1e-5) cannot
+// overlap); the rest go through precise_delta.
 struct PairAcc {
     float g0, g1, g2, c0, c1, c2;
 };
 
 __device__ __forceinline__ void pair_term(const MixRec& ri, const MixRec& rj, long long i, unsigned int j,
-                                          const MixScalars& S, const float sx, const float sy, const float sz,
-                                          PairAcc& a, float& es, float& ec, float& ks, float& kc, float& md)
+                                          const MixScalars& S, const RcpConst& c, PairAcc& a, float& es, float& ec,
+                                          float& ks, float& kc, float& md)
 {
-    const float dx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, sx);
-    const float dy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, sy);
-    const float dz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, sz);
-    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
-    const float r = sqrtf(r2);
-    const float dd = S.kappa * (0.5f * (ri.l.w + rj.l.w));
-    const float delta = 1.0f - r / dd;
-    if (delta > 0.0f) {
-        if (r > 0.0f) {
-            const float coef = (S.eps * delta) / (dd * r);
-            acc2(a.g0, a.c0, -coef * dx);
-            acc2(a.g1, a.c1, -coef * dy);
-            acc2(a.g2, a.c2, -coef * dz);
-        }
-        if ((long long)j > i) {
-            acc2(es, ec, (0.5f * S.eps) * (delta * delta));
-            acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) / S.kappa);
-        }
-        md = fmaxf(md, delta);
+    {
+        const float fx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, c.qscale[0]);
+        const float fy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, c.qscale[1]);
+        const float fz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, c.qscale[2]);
+        const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
+        const float d = S.kappa * (0.5f * (ri.l.w + rj.l.w));
+        if (r2 > (d * d) * 1.00001f) return;
     }
+    float dx, dy, dz, r;
+    const float delta = precise_delta(ri, rj, S, c, dx, dy, dz, r);
+    if (!(delta > 0.0f)) return;
+    const float dd = S.kappa * (0.5f * (ri.l.w + rj.l.w));
+    if (r > 0.0f) {
+        const float coef = (S.eps * delta) / (dd * r);
+        acc2(a.g0, a.c0, -coef * dx);
+        acc2(a.g1, a.c1, -coef * dy);
+        acc2(a.g2, a.c2, -coef * dz);
+    }
+    if ((long long)j > i) {
+        acc2(es, ec, (0.5f * S.eps) * (delta * delta));
+        acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) / S.kappa);
+    }
+    md = fmaxf(md, delta);
 }
 
 // Close row i: the Adam step of its record (Adam mode) or its gradient out.
@@ -227,7 +309,10 @@ __device__ __forceinline__ float warp_sum2f(float s, float c)
 // gradient is reduced with compensated shuffles.  The other blocks give one
 // thread to each remaining row, loading partners four at a time.  Both end
 // with the row's Adam step; block partials of e and k go to part_e/part_k.
-__global__ void __launch_bounds__(RCP_PAIR_THREADS)
+#ifndef RCP_MIX_MINB
+#define RCP_MIX_MINB 4   // resident blocks per SM the register budget is sized for
+#endif
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
 k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB, const unsigned int* rowptr,
              const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
              double* part_k, int mode, double* g_out)
@@ -241,7 +326,6 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
     const int parity = ctl->parity;
     const MixRec* __restrict__ rin = parity ? rB : rA;
     MixRec* __restrict__ rout = parity ? rA : rB;
-    const float sx = c.qscale[0], sy = c.qscale[1], sz = c.qscale[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
     if (blockIdx.x < RCP_LONG_BLOCKS) {
@@ -252,9 +336,19 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
             const MixRec ri = rin[i];
             PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const unsigned int t1 = rowptr[i + 1];
-            for (unsigned int t = rowptr[i] + lane; t < t1; t += 32) {
+            unsigned int t = rowptr[i] + lane;
+            // four strides of the warp per round trip to memory
+            for (; t + 96 < t1; t += 128) {
+                const unsigned int j0 = col[t], j1 = col[t + 32], j2 = col[t + 64], j3 = col[t + 96];
+                const MixRec r0 = rin[j0], r1 = rin[j1], r2 = rin[j2], r3 = rin[j3];
+                pair_term(ri, r0, i, j0, S, c, a, es, ec, ks, kc, md);
+                pair_term(ri, r1, i, j1, S, c, a, es, ec, ks, kc, md);
+                pair_term(ri, r2, i, j2, S, c, a, es, ec, ks, kc, md);
+                pair_term(ri, r3, i, j3, S, c, a, es, ec, ks, kc, md);
+            }
+            for (; t < t1; t += 32) {
                 const unsigned int j = col[t];
-                pair_term(ri, rin[j], i, j, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                pair_term(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
             }
             const float g0 = warp_sum2f(a.g0, a.c0);
             const float g1 = warp_sum2f(a.g1, a.c1);
@@ -269,29 +363,27 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
                 const MixRec ri = rin[i];
                 PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 unsigned int t = t0;
-                for (; t + 4 <= t1; t += 4) {
-                    const unsigned int j0 = col[t], j1 = col[t + 1], j2 = col[t + 2], j3 = col[t + 3];
-                    const MixRec r0 = rin[j0], r1 = rin[j1], r2 = rin[j2], r3 = rin[j3];
-                    pair_term(ri, r0, i, j0, S, sx, sy, sz, a, es, ec, ks, kc, md);
-                    pair_term(ri, r1, i, j1, S, sx, sy, sz, a, es, ec, ks, kc, md);
-                    pair_term(ri, r2, i, j2, S, sx, sy, sz, a, es, ec, ks, kc, md);
-                    pair_term(ri, r3, i, j3, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                for (; t + 2 <= t1; t += 2) {
+                    const unsigned int j0 = col[t], j1 = col[t + 1];
+                    const MixRec r0 = rin[j0], r1 = rin[j1];
+                    pair_term(ri, r0, i, j0, S, c, a, es, ec, ks, kc, md);
+                    pair_term(ri, r1, i, j1, S, c, a, es, ec, ks, kc, md);
                 }
                 for (; t < t1; ++t) {
                     const unsigned int j = col[t];
-                    pair_term(ri, rin[j], i, j, S, sx, sy, sz, a, es, ec, ks, kc, md);
+                    pair_term(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
                 }
                 row_epilogue(ctl, c, S, i, ri, a.g0 + a.c0, a.g1 + a.c1, a.g2 + a.c2, m, v, rout, rb, mode, g_out);
             }
         }
     }
-    const double we = warp_sum2(es, ec);
-    const double wk = warp_sum2(ks, kc);
+    warp_sum2(es, ec);
+    warp_sum2(ks, kc);
     float wm = md;
     for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_down_sync(0xffffffffu, wm, o));
     if (lane == 0) {
-        she[warp] = we;
-        shk[warp] = wk;
+        she[warp] = (double)es + (double)ec;
+        shk[warp] = (double)ks + (double)kc;
         shm[warp] = wm;
     }
     __syncthreads();

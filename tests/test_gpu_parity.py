@@ -204,6 +204,28 @@ def test_energy_grad_mixed_within_tolerance(rcp, orc):
         p.close()
 
 
+def test_energy_grad_mixed_near_contact(rcp, orc):
+    """Small overlaps (delta ~ 1e-3, a relaxed packing inflated by 0.2 %): the
+    regime where a plain binary32 d - r would cancel."""
+    D0 = inputs.lognormal(400, 0.5, 10.0)
+    ref = orc.run(D0, seed=2)
+    k = ref.kappa_c * 1.002
+    x = ref.x
+    p = _mk(rcp, D0, precision=rcp.RCP_MIXED)
+    p.set_positions(x, k)
+    for mu in (0.0, 0.01):
+        E, g, dk, md = p.energy_grad(mu)
+        oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, mu)
+        assert 5e-4 < omd < 5e-3
+        print(f"mu={mu} relE={abs(E - oE) / abs(oE):.2e} reldk={abs(dk - odk) / abs(odk):.2e} "
+              f"relg={np.linalg.norm(g - og) / np.linalg.norm(og):.2e} relmd={abs(md - omd) / omd:.2e}")
+        assert abs(E - oE) <= 1e-5 * abs(oE)
+        assert abs(dk - odk) <= 1e-5 * abs(odk)
+        assert np.linalg.norm(g - og) <= 1e-5 * np.linalg.norm(og)
+        assert abs(md - omd) <= 1e-5 * omd
+    p.close()
+
+
 def test_mixed_run_reaches_the_criterion(rcp, orc):
     D0 = inputs.lognormal(1000, 0.5, 10.0)
     p = _mk(rcp, D0, seed=0, precision=rcp.RCP_MIXED)

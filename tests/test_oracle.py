@@ -298,12 +298,11 @@ def test_levels_and_cells_follow_definition(orc):
     for k in range(len(rml)):
         assert rml[k] == rho[lvl == k].max()
         nk = orc.grid_n(1.0, rml[k], int(cnt[k]), 1.0)
-        # power of two; cells no smaller than the largest interaction diameter
-        # and holding >= 2 spheres of the class on average; the next finer grid
-        # would break one of the two bounds
+        # power of two whose cells hold >= 2 spheres of the class on average;
+        # the next finer grid would not
         h = 1.0 / nk
-        assert nk & (nk - 1) == 0 and (nk == 1 or (h >= 2 * rml[k] and h ** 3 * cnt[k] >= 2.0))
-        assert nk == 2 ** 19 or (h / 2 < 2 * rml[k] or (h / 2) ** 3 * cnt[k] < 2.0)
+        assert nk & (nk - 1) == 0 and (nk == 1 or h ** 3 * cnt[k] >= 2.0)
+        assert nk == 2 ** 19 or (h / 2) ** 3 * cnt[k] < 2.0
     x = orc.init_positions(4, 3000)
     key = orc.cell_keys(x, D0, 1.0, kb, s, sg)
     assert np.array_equal((key >> np.uint64(57)).astype(int), lvl)
