@@ -182,6 +182,9 @@ def main():
     clk = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     it0 = snap[3].t
+    prof_region = os.environ.get("RCP_PROFILE_REGION") == "1"  # bracket the timed region for ncu
+    if prof_region:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     pairs_sum, rebuild0 = 0, None
     launches = 0
@@ -193,6 +196,8 @@ def main():
             rebuild0 = r.rebuilds
     ev1.record(stream)
     barrier_sync()
+    if prof_region:
+        torch.cuda.profiler.stop()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
     x_end, _, _, s_end = p.state()
@@ -210,11 +215,16 @@ def main():
     pair_evals = pairs_sum / 2.0 / (ms / 1e3) * world  # unordered pairs
     phi_now = (np.pi / 6.0) * s_end.kappa ** 3 * float(np.sum(D0.astype(np.float64) ** 3))
 
-    # ---- roofline of the dominant kernel (pair kernel), events per launch
+    # ---- roofline of the dominant kernel (pair kernel), events per launch.
+    # Algorithmic bytes of one mixed pair-kernel launch: per sphere the row
+    # pointer (4), its record (32 read, 32 written), the binary32 Adam moments
+    # (24 read, 24 written) and the build snapshot for the skin test (32); per
+    # listed entry its column index (4).  Partner records are gathers that the
+    # method reuses from cache, not extra algorithmic traffic.
     ms_pair, ms_iter, nl = rcp.rcp_profile(p.h, 50)
     info = p.run(max_iters=1, shrink=False)
     Pn = info.pairs
-    bytes_per_launch = 212.0 * w["N"] + 4.0 * Pn
+    bytes_per_launch = 148.0 * w["N"] + 4.0 * Pn
     gbs = bytes_per_launch / (ms_pair / nl / 1e3) / 1e9
     peak, peak_kind = peaks()
 

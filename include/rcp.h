@@ -66,7 +66,10 @@ typedef struct {
     double    beta2;        /* Adam second-moment decay (0.999) */
     double    adam_eps;     /* Adam denominator guard (1e-8) */
     double    skin_s;       /* size-proportional Verlet skin fraction s (0.1) */
-    double    skin_theta;   /* rebuild when a sphere moved theta of its skin (0.5) */
+    double    skin_theta;   /* rebuild when a sphere's displacement plus its share
+                               (kappa - kappa_b) D_i/2 of the growth exceeds theta of
+                               its skin sigma_i; theta <= 1 keeps every overlapping
+                               pair listed (1) */
     double    skin_abs;     /* absolute skin sigma0 in units of the first rung's
                                position learning rate (20) */
     double    lr_x;         /* position learning rate in units of kappa D_ref,
@@ -80,6 +83,9 @@ typedef struct {
     int       n_cycles;     /* mu cycles after the descent (2) */
     long long max_iters;    /* cap on Adam steps (2000000) */
     int       chunk;        /* iterations per CUDA-graph replay (32) */
+    double    cell_occupancy; /* spheres per cell each size class's grid aims at:
+                                 cells are the smallest power-of-two grid with at
+                                 least this many per cell on average (1) */
 } rcp_config;
 
 /* When rcp_run returns early. */
@@ -187,8 +193,9 @@ rcp_status rcp_profile(rcp_handle h, long long iters, double* ms_pair, double* m
                        long long* launches);
 
 /* Shrink to contact at the current state (Sec. II, App. A): kappa_c is the
- * smaller of kappa and min_{i<j} r_ij / d_ij^0; phi is the solid-volume
- * fraction at kappa_c.  Positions and kappa are not changed. */
+ * smaller of kappa and min_{i<j} r_ij / d_ij^0, lowered by the factor
+ * (1 - 2^-50) so that a binary64 re-evaluation finds no overlap; phi is the
+ * solid-volume fraction at kappa_c.  Positions and kappa are not changed. */
 rcp_status rcp_shrink(rcp_handle h, double* kappa_c, double* phi);
 
 /* Copy the state to host arrays (any pointer may be NULL): x and the Adam

@@ -78,9 +78,9 @@ def lib():
         L.orc_levels.argtypes = [_dp, C.c_long, C.c_double, C.c_double, C.c_double,
                                  np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"), _dp]
         L.orc_grid_n.restype = C.c_long
-        L.orc_grid_n.argtypes = [C.c_double, C.c_double, C.c_long, C.c_double]
+        L.orc_grid_n.argtypes = [C.c_double, C.c_long, C.c_double, C.c_double]
         L.orc_cell_keys.argtypes = [_dp, _dp, C.c_long, C.c_int, _dp, C.c_double, C.c_double,
-                                    C.c_double, _up]
+                                    C.c_double, C.c_double, _up]
         for nm in ("orc_list_brute", "orc_list_grid"):
             f = getattr(L, nm)
             f.restype = C.c_long
@@ -175,15 +175,15 @@ def levels(D0, kappa_b, s, sigma0):
     return lvl, rml[:nlev]
 
 
-def grid_n(L: float, rho_max_k: float, count: int, V: float) -> int:
-    return int(lib().orc_grid_n(L, rho_max_k, count, V))
+def grid_n(L: float, count: int, V: float, occ: float = 1.0) -> int:
+    return int(lib().orc_grid_n(L, count, V, occ))
 
 
-def cell_keys(x, D0, L, kappa_b, s, sigma0, d=3):
+def cell_keys(x, D0, L, kappa_b, s, sigma0, d=3, occ=1.0):
     x = f64(x).ravel()
     D0 = f64(D0)
     key = np.zeros(D0.size, dtype=np.uint64)
-    lib().orc_cell_keys(x, D0, D0.size, d, _box(L, d), kappa_b, s, sigma0, key)
+    lib().orc_cell_keys(x, D0, D0.size, d, _box(L, d), kappa_b, s, sigma0, occ, key)
     return key
 
 

@@ -200,19 +200,17 @@ int orc_levels(const double* D0, long n, double kappa_b, double s, double sigma0
 }
 
 /* Cells per axis at a level: the largest power of two n <= 2^19 whose cell
- * volume holds at least ORC_OCC spheres of the level on average,
- * h^3 count >= ORC_OCC V with h = L/n (V the box volume, count the level's
- * size).  The search scans every cell within the search radius, so any cell
- * size is correct; this one balances cell lookups against candidates. */
-#define ORC_OCC 2.0
-long orc_grid_n(double L, double rho_max_k, long count, double V)
+ * volume holds at least `occ` spheres of the level on average,
+ * h^3 count >= occ V with h = L/n (V the box volume, count the level's size).
+ * The search scans every cell within the search radius, so any cell size is
+ * correct; this one balances cell lookups against candidates. */
+long orc_grid_n(double L, long count, double V, double occ)
 {
-    (void)rho_max_k;
     long n = 1;
     for (;;) {
         if (n >= ORC_NMAX) break;
         double h = L / (double)(2 * n);
-        if (!(((h * h) * h) * (double)count >= ORC_OCC * V)) break;
+        if (!(((h * h) * h) * (double)count >= occ * V)) break;
         n *= 2;
     }
     return n;
@@ -233,7 +231,7 @@ static uint64_t pack_key(int k, long cz, long cy, long cx)
 }
 
 void orc_cell_keys(const double* x, const double* D0, long n, int d, const double* L,
-                   double kappa_b, double s, double sigma0, uint64_t* key)
+                   double kappa_b, double s, double sigma0, double occ, uint64_t* key)
 {
     int* lvl = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     double rml[ORC_KMAX];
@@ -244,7 +242,7 @@ void orc_cell_keys(const double* x, const double* D0, long n, int d, const doubl
     for (long i = 0; i < n; ++i) {
         int k = lvl[i];
         long c[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) c[a] = cell_of(x[d * i + a], L[a], orc_grid_n(L[a], rml[k], cnt[k], V));
+        for (int a = 0; a < d; ++a) c[a] = cell_of(x[d * i + a], L[a], orc_grid_n(L[a], cnt[k], V, occ));
         key[i] = pack_key(k, c[2], c[1], c[0]);
     }
     free(lvl);
@@ -360,6 +358,13 @@ long orc_list_grid(const double* x, const double* D0, long n, int d, const doubl
                    double kappa_b, double s, double sigma0,
                    long* rowptr, int* col, long cap)
 {
+    return orc_list_grid_occ(x, D0, n, d, L, kappa_b, s, sigma0, 1.0, rowptr, col, cap);
+}
+
+long orc_list_grid_occ(const double* x, const double* D0, long n, int d, const double* L,
+                       double kappa_b, double s, double sigma0, double occ,
+                       long* rowptr, int* col, long cap)
+{
     int* lvl = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     double rml[ORC_KMAX];
     int nlev = orc_levels(D0, n, kappa_b, s, sigma0, lvl, rml);
@@ -368,7 +373,7 @@ long orc_list_grid(const double* x, const double* D0, long n, int d, const doubl
     double V = box_volume(d, L);
     long ng[ORC_KMAX][3];
     for (int k = 0; k < nlev; ++k)
-        for (int a = 0; a < 3; ++a) ng[k][a] = a < d ? orc_grid_n(L[a], rml[k], cnt[k], V) : 1;
+        for (int a = 0; a < 3; ++a) ng[k][a] = a < d ? orc_grid_n(L[a], cnt[k], V, occ) : 1;
     keyidx* ki = (keyidx*)malloc(sizeof(keyidx) * (size_t)(n > 0 ? n : 1));
     for (long i = 0; i < n; ++i) {
         long c[3] = {0, 0, 0};
@@ -553,7 +558,10 @@ void orc_adam_update(double* p, double* m, double* v, const double* g, long n,
 /* ------------------------------------------------------------------------ */
 /* Shrink to contact (Sec. II, App. A): with positions and D^0 fixed, the
  * largest kappa' <= kappa at which no pair overlaps is the smaller of kappa
- * and min_{i<j} r_ij / d_ij^0 (a pair touching exactly does not overlap). */
+ * and min_{i<j} r_ij / d_ij^0 (a pair touching exactly does not overlap).
+ * Reading: that quotient is rounded, so the result is lowered by the factor
+ * (1 - 2^-50) -- a few units in the last place -- which guarantees that a
+ * binary64 re-evaluation at kappa_c finds no overlap at all. */
 double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const double* L,
                         double kappa, const long* rowptr, const int* col)
 {
@@ -567,7 +575,7 @@ double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const 
             double q = r / (0.5 * (D0[i] + D0[j]));
             if (q < kc) kc = q;
         }
-    return kc;
+    return kc * (1.0 - 0x1.0p-50);
 }
 
 /* Solid-volume fraction of spheres (disks for d = 2) of diameters kappa D^0. */
@@ -598,7 +606,7 @@ void orc_params_default(orc_params* p)
     p->beta2 = 0.999;
     p->adam_eps = 1e-8;
     p->skin_s = 0.1;
-    p->skin_theta = 0.5;
+    p->skin_theta = 1.0;
     p->skin_abs = 20.0;
     p->lr_x = 1e-3;
     p->lr_kappa = 1e-3;
@@ -610,6 +618,22 @@ void orc_params_default(orc_params* p)
     p->n_down = 3;
     p->n_cycles = 2;
     p->max_iters = 2000000;
+}
+
+/* Rebuild test (the list criterion above): a pair listed at kappa_b with
+ * margin sigma_i + sigma_j stays non-overlapping while every sphere keeps
+ * |x_i - x_i^b| + (kappa - kappa_b) D_i^0 / 2 <= theta sigma_i, theta <= 1.
+ * Returns 1 if some sphere broke it (1e-9 margins cover rounding). */
+static int skin_spent(const double* x, const double* xb, const double* D0, long n, int d, const double* L,
+                      double kappa, double kb, double s, double th, double sigma0)
+{
+    for (long i = 0; i < n; ++i) {
+        double dx[3];
+        double disp = sqrt(min_image(&x[d * i], &xb[d * i], d, L, dx)) * (1.0 + 1e-9);
+        double sig = th * (s * kb * D0[i] + sigma0) * (1.0 - 1e-9);
+        if (disp + (kappa - kb) * D0[i] * 0.5 * (1.0 + 1e-9) > sig) return 1;
+    }
+    return 0;
 }
 
 /* Rung table (reading of App. A: a short descent of mu in discrete rungs,
@@ -727,16 +751,7 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
                 for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
             orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);
             ++it;
-            /* rebuild when some particle has moved more than theta of its skin
-             * or kappa has grown past kappa_b (1 + 2 s (1 - theta)); the
-             * thresholds carry a 1e-9 safety factor against rounding */
-            if (kappa > kb * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) need = 1;
-            for (long i = 0; i < n && !need; ++i) {
-                double dx[3];
-                double r2 = min_image(&x[d * i], &xb[d * i], d, L, dx);
-                double lim = th * (s * kb * D0[i] + sigma0) * (1.0 - 1e-9);
-                if (r2 > lim * lim) need = 1;
-            }
+            need = need || skin_spent(x, xb, D0, n, d, L, kappa, kb, s, th, sigma0);
         }
     }
     {
@@ -803,13 +818,7 @@ long orc_sample_iterations(const orc_params* p, const double* D0, long n, double
         for (long i = 0; i < n; ++i)
             for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
         orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);
-        if (kappa > kb * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) need = 1;
-        for (long i = 0; i < n && !need; ++i) {
-            double dx[3];
-            double r2 = min_image(&x[d * i], &xb[d * i], d, L, dx);
-            double lim = th * (s * kb * D0[i] + sigma0) * (1.0 - 1e-9);
-            if (r2 > lim * lim) need = 1;
-        }
+        need = need || skin_spent(x, xb, D0, n, d, L, kappa, kb, s, th, sigma0);
     }
     free(m); free(v); free(g); free(xb); free(rowptr); free(col);
     return builds;

@@ -70,9 +70,9 @@ double orc_n_trig(long n, int d, int Y, int X);
 double orc_rho(double D0, double kappa_b, double s, double sigma0);
 int    orc_levels(const double* D0, long n, double kappa_b, double s, double sigma0,
                   int* lvl, double* rho_max_lvl /* [32] */);
-long   orc_grid_n(double L, double rho_max_k, long count, double V);
+long   orc_grid_n(double L, long count, double V, double occ);
 void   orc_cell_keys(const double* x, const double* D0, long n, int d, const double* L,
-                     double kappa_b, double s, double sigma0, uint64_t* key);
+                     double kappa_b, double s, double sigma0, double occ, uint64_t* key);
 int    orc_listed(const double* xi, const double* xj, int d, const double* L,
                   double rho_i, double rho_j);
 long   orc_list_brute(const double* x, const double* D0, long n, int d, const double* L,
@@ -81,6 +81,9 @@ long   orc_list_brute(const double* x, const double* D0, long n, int d, const do
 long   orc_list_grid(const double* x, const double* D0, long n, int d, const double* L,
                      double kappa_b, double s, double sigma0,
                      long* rowptr, int* col, long cap);
+long   orc_list_grid_occ(const double* x, const double* D0, long n, int d, const double* L,
+                         double kappa_b, double s, double sigma0, double occ,
+                         long* rowptr, int* col, long cap);
 long   orc_row_brute(const double* x, const double* D0, long n, int d, const double* L,
                      double kappa_b, double s, double sigma0, long i, int* col, long cap);
 

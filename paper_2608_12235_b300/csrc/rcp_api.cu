@@ -402,10 +402,13 @@ rcp_status build(rcp_ctx* h)
 // ---------------------------------------------------------------- evaluation
 unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_THREADS); }
 
-// Blocks of one pair-kernel launch (the mixed kernel adds the long-row blocks).
+// Partial sums one pair-kernel launch writes: one per block in binary64 mode
+// (canonical trees), one per warp in mixed mode (which also adds the
+// long-row blocks).
 unsigned int launch_blocks(const rcp_ctx* h)
 {
-    return pair_blocks(h) + (h->cfg.precision == RCP_MIXED ? RCP_LONG_BLOCKS : 0);
+    if (h->cfg.precision == RCP_MIXED) return (pair_blocks(h) + RCP_LONG_BLOCKS) * (RCP_PAIR_THREADS / 32);
+    return pair_blocks(h);
 }
 
 // Reduce the pair kernel's block partials to <= 8192 entries; returns the
@@ -557,7 +560,7 @@ rcp_status rcp_config_default(rcp_config* cfg)
     cfg->beta2 = 0.999;
     cfg->adam_eps = 1e-8;
     cfg->skin_s = 0.1;
-    cfg->skin_theta = 0.5;
+    cfg->skin_theta = 1.0;
     cfg->skin_abs = 20.0;
     cfg->lr_x = 1e-3;
     cfg->lr_kappa = 1e-3;
@@ -570,6 +573,7 @@ rcp_status rcp_config_default(rcp_config* cfg)
     cfg->n_cycles = 2;
     cfg->max_iters = 2000000;
     cfg->chunk = 32;
+    cfg->cell_occupancy = 1.0;
     return RCP_OK;
 }
 
@@ -627,7 +631,7 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
     else rcp_config_default(&h->cfg);
     if (h->cfg.chunk < 1) h->cfg.chunk = 1;
     if ((h->cfg.precision != RCP_FP64 && h->cfg.precision != RCP_MIXED) || !(h->cfg.phi0 > 0.0) ||
-        !(h->cfg.skin_theta > 0.0 && h->cfg.skin_theta < 1.0) || !(h->cfg.skin_s >= 0.0) || !(h->cfg.tol > 0.0)) {
+        !(h->cfg.skin_theta > 0.0 && h->cfg.skin_theta <= 1.0) || !(h->cfg.skin_s >= 0.0) || !(h->cfg.tol > 0.0)) {
         delete h;
         return RCP_ERR_ARG;
     }
@@ -661,6 +665,7 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
     c.skin_s = h->cfg.skin_s;
     c.skin_theta = h->cfg.skin_theta;
     c.stop_margin = h->cfg.precision == RCP_MIXED ? 1e-2 : 0.0;
+    c.cell_occ = h->cfg.cell_occupancy > 0.0 ? h->cfg.cell_occupancy : 1.0;
 
     rcp_status st = [&]() -> rcp_status {
         CK(cudaGetDevice(&h->device));
@@ -687,8 +692,8 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         }
         CKS(dalloc(h, &h->g, 3 * n));
         CKS(dalloc(h, &h->xtmp, 3 * n));
-        size_t nparts = (n + RCP_TREE - 1) / RCP_TREE + (n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS +
-                        RCP_LONG_BLOCKS + 8;
+        size_t nparts = (n + RCP_TREE - 1) / RCP_TREE +
+                        ((n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS + RCP_LONG_BLOCKS) * (RCP_PAIR_THREADS / 32) + 8;
         CKS(dalloc(h, &h->part_e, nparts));
         CKS(dalloc(h, &h->part_k, nparts));
         CKS(dalloc(h, &h->part_e2, nparts));

@@ -99,12 +99,11 @@ __global__ void __launch_bounds__(256) k_level(RcpCtl* ctl, long long N, const d
 }
 
 // Cells per axis of each class: the largest power of two n <= 2^19 whose
-// cell holds at least RCP_CELL_OCC spheres of the class on average
-// (h^3 count >= RCP_CELL_OCC V, h = L/n).  The search scans every cell within
+// cell holds at least c.cell_occ spheres of the class on average
+// (h^3 count >= cell_occ V, h = L/n).  The search scans every cell within
 // its radius, so any cell size is correct; this one balances hash lookups
 // against candidates.  Also the periodic-image rule: every listed pair must
 // be closer than half a box edge, i.e. 4 rho_max < min L.
-#define RCP_CELL_OCC 2.0
 __global__ void k_grid(RcpCtl* ctl, RcpConst c)
 {
     int nlev = 0;
@@ -118,7 +117,7 @@ __global__ void k_grid(RcpCtl* ctl, RcpConst c)
                 for (;;) {
                     if (n >= RCP_NMAX_AXIS) break;
                     const double h = c.L[a] / (double)(2 * n);
-                    if (!(((h * h) * h) * cnt >= RCP_CELL_OCC * c.V)) break;
+                    if (!(((h * h) * h) * cnt >= c.cell_occ * c.V)) break;
                     n *= 2;
                 }
             ctl->ng[k][a] = (int)n;
@@ -499,6 +498,7 @@ __global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, cons
     if (i == 0) {
         ctl->need_rebuild = 0;
         ctl->disp_flag = 0u;
+        ctl->kbud_bits = RCP_KBUD_INF;
         ctl->rebuilds += 1;
         ctl->pairs = P;
     }

@@ -36,7 +36,8 @@ struct RcpCtl {
     int parity;             // 0: buffer A holds the current positions
     // flags
     int halted, stopped, need_rebuild, status;
-    unsigned int disp_flag;
+    unsigned int disp_flag;   // some sphere used up its skin budget
+    unsigned int kbud_bits;   // binary32 bits of min_i 2 (theta sigma_i - |x_i - x_i^b|) / D_i
     // last evaluation
     double E, dEdk, maxdelta;
     unsigned long long maxdelta_bits;
@@ -69,6 +70,7 @@ struct RcpConst {
     double skin_s, skin_theta;
     double Lmin, Lmax;
     double stop_margin;     // 0: binary64 overlaps; > 0: relative band that triggers a binary64 check
+    double cell_occ;        // target spheres per cell of a class grid
     float qscale[3];        // L_a / 2^32: fixed-point unit of axis a
     float qinv[3];          // 2^32 / L_a
     double invL[3];         // 1 / L_a
@@ -79,6 +81,7 @@ struct RcpConst {
 enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
 
 // ---- small helpers ----
+#define RCP_KBUD_INF 0x7F800000u
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 

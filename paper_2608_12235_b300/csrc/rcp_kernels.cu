@@ -202,17 +202,46 @@ __device__ __forceinline__ double adam_coord(double p, double g, double& m, doub
     return p - (eta * mh) / (sqrt(vh) + c.adam_eps);
 }
 
-// Has sphere i moved farther than theta of its skin since the last build?
-// (A 1e-9 safety factor keeps rounding on the safe side.)
-__device__ __forceinline__ bool moved_too_far(const RcpCtl* ctl, const RcpConst& c, double px, double py,
-                                              double pz, double D0, double4_32a b)
+// Skin budget of sphere i (exact Verlet criterion).  A pair is listed iff its
+// distance at the build was below kappa_b d0 + sigma_i + sigma_j; it stays
+// non-overlapping while |dx_i| + |dx_j| + (kappa - kappa_b) d0 <= sigma_i +
+// sigma_j, which holds if every sphere keeps
+//   |x_i - x_i^b| + (kappa - kappa_b) D_i / 2 <= theta sigma_i   (theta <= 1).
+// The displacement part is known here; what it leaves for kappa growth,
+// b_i = 2 (theta sigma_i - |x_i - x_i^b|) / D_i, is reduced to its minimum
+// (the kappa step compares kappa - kappa_b with it).  A negative b_i flags
+// the rebuild directly.  Margins of 1e-9 cover rounding.
+__device__ __forceinline__ void skin_budget64(RcpCtl* ctl, const RcpConst& c, double px, double py, double pz,
+                                              double D0, double4_32a b, float& bud)
 {
     double dx = min_image(px - b.x, c.L[0], c.halfL[0]);
     double dy = min_image(py - b.y, c.L[1], c.halfL[1]);
     double dz = min_image(pz - b.z, c.L[2], c.halfL[2]);
-    double r2 = dx * dx + dy * dy + dz * dz;
-    double lim = c.skin_theta * (c.skin_s * ctl->kappa_b * D0 + ctl->sigma0) * (1.0 - 1e-9);
-    return r2 > lim * lim;
+    const double disp = sqrt(dx * dx + dy * dy + dz * dz) * (1.0 + 1e-9);
+    const double sig = c.skin_theta * (c.skin_s * ctl->kappa_b * D0 + ctl->sigma0) * (1.0 - 1e-9);
+    const double bi = 2.0 * (sig - disp) / D0;
+    if (!(bi >= 0.0)) atomicOr(&ctl->disp_flag, 1u);
+    else bud = fminf(bud, __double2float_rd(bi * (1.0 - 1e-9)));
+}
+
+// Warp minimum of the budgets, one atomic per warp (non-negative binary32
+// values order like their bit patterns).
+__device__ __forceinline__ void push_budget(RcpCtl* ctl, float bud)
+{
+    for (int o = 16; o > 0; o >>= 1) bud = fminf(bud, __shfl_down_sync(0xffffffffu, bud, o));
+    if ((threadIdx.x & 31) == 0 && bud < INFINITY) {
+        const unsigned int bits = __float_as_uint(bud);
+        if (bits < *(volatile unsigned int*)&ctl->kbud_bits) atomicMin(&ctl->kbud_bits, bits);
+    }
+}
+
+// Does kappa_new still fit the minimum budget (the rebuild test closing an
+// iteration or a standalone Adam step)?  Resets the budget for the next one.
+__device__ __forceinline__ bool skin_exhausted(RcpCtl* ctl, double kappa_new)
+{
+    const float bud = __uint_as_float(ctl->kbud_bits);
+    ctl->kbud_bits = RCP_KBUD_INF;
+    return ctl->disp_flag || (kappa_new - ctl->kappa_b) * (1.0 + 1e-9) > (double)bud;
 }
 
 // ---------------------------------------------------------------------------
@@ -239,6 +268,7 @@ k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, d
     const double kappa = ctl->kappa;
     const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
     double e = 0.0, k = 0.0, md = 0.0;
+    float bud = INFINITY;
     if (i < c.N) {
         const double4_32a xi = xin[i];
         double g0 = 0.0, g1 = 0.0, g2 = 0.0;
@@ -279,13 +309,14 @@ k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, d
             m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
             v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
             xout[i] = make_double4_32a(p0, p1, p2, xi.w);
-            if (moved_too_far(ctl, c, p0, p1, p2, xi.w, xb[i])) atomicOr(&ctl->disp_flag, 1u);
+            skin_budget64(ctl, c, p0, p1, p2, xi.w, xb[i], bud);
         } else {
             g_out[3 * i] = g0;
             g_out[3 * i + 1] = g1;
             g_out[3 * i + 2] = g2;
         }
     }
+    if (mode == RCP_MODE_ADAM) push_budget(ctl, bud);
     double se = block_tree<RCP_PAIR_THREADS>(e, sh);
     double sk = block_tree<RCP_PAIR_THREADS>(k, sh);
     double bm = block_max(md, sh);
@@ -313,8 +344,7 @@ __device__ void kappa_adam_tail(RcpCtl* ctl, const RcpConst& c)
     ctl->parity ^= 1;
     ctl->iter += 1;
     if (ctl->iter >= ctl->iter_limit) ctl->halted = 1;
-    const double s = c.skin_s, th = c.skin_theta;
-    if (ctl->disp_flag || kn > ctl->kappa_b * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) {
+    if (skin_exhausted(ctl, kn)) {
         ctl->need_rebuild = 1;
         ctl->halted = 1;
     }
@@ -404,21 +434,24 @@ __global__ void k_verify_final(RcpCtl* ctl, RcpConst c)
 __global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const double* g, const double4_32a* xb, double eta_x)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.N) return;
-    double4_32a* x = ctl->parity ? xB : xA;
-    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
-    const double h1 = 1.0 - b1, h2 = 1.0 - b2;
-    double4_32a p = x[i];
-    double m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
-    double v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
-    double p0 = wrap_step(adam_coord(p.x, g[3 * i], m0, v0, eta_x, c, h1, h2), c.L[0]);
-    double p1 = wrap_step(adam_coord(p.y, g[3 * i + 1], m1, v1, eta_x, c, h1, h2), c.L[1]);
-    double p2 = wrap_step(adam_coord(p.z, g[3 * i + 2], m2, v2, eta_x, c, h1, h2), c.L[2]);
-    m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
-    v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
-    x[i] = make_double4_32a(p0, p1, p2, p.w);
-    if (moved_too_far(ctl, c, p0, p1, p2, p.w, xb[i])) atomicOr(&ctl->disp_flag, 1u);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float bud = INFINITY;
+    if (i < c.N) {
+        double4_32a* x = ctl->parity ? xB : xA;
+        const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+        const double h1 = 1.0 - b1, h2 = 1.0 - b2;
+        double4_32a p = x[i];
+        double m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
+        double v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
+        double p0 = wrap_step(adam_coord(p.x, g[3 * i], m0, v0, eta_x, c, h1, h2), c.L[0]);
+        double p1 = wrap_step(adam_coord(p.y, g[3 * i + 1], m1, v1, eta_x, c, h1, h2), c.L[1]);
+        double p2 = wrap_step(adam_coord(p.z, g[3 * i + 2], m2, v2, eta_x, c, h1, h2), c.L[2]);
+        m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
+        v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
+        x[i] = make_double4_32a(p0, p1, p2, p.w);
+        skin_budget64(ctl, c, p0, p1, p2, p.w, xb[i], bud);
+    }
+    push_budget(ctl, bud);
 }
 
 // kappa's share of the standalone Adam step; also advances t and the bias
@@ -434,23 +467,25 @@ __global__ void k_adam_kappa(RcpCtl* ctl, RcpConst c, double dEdk, double eta_k)
     ctl->b1 = b1;
     ctl->b2 = b2;
     ctl->iter += 1;
-    const double s = c.skin_s, th = c.skin_theta;
-    if (ctl->disp_flag || kn > ctl->kappa_b * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) ctl->need_rebuild = 1;
+    if (skin_exhausted(ctl, kn)) ctl->need_rebuild = 1;
 }
 
 // Skin check of the current state against the last build (after positions or
-// kappa were replaced from outside).
-__global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double4_32a* xb)
+// kappa were replaced from outside): a sphere's displacement plus its share of
+// kappa - kappa_b must stay within theta of its skin.
+__global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                             const double4_32a* xb)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        const double s = c.skin_s, th = c.skin_theta;
-        if (ctl->kappa > ctl->kappa_b * (1.0 + 2.0 * s * (1.0 - th)) * (1.0 - 1e-9)) ctl->need_rebuild = 1;
-    }
     if (i >= c.N) return;
     const double4_32a* x = ctl->parity ? xB : xA;
-    double4_32a p = x[i];
-    if (moved_too_far(ctl, c, p.x, p.y, p.z, p.w, xb[i])) ctl->need_rebuild = 1;
+    const double4_32a p = x[i], b = xb[i];
+    double dx = min_image(p.x - b.x, c.L[0], c.halfL[0]);
+    double dy = min_image(p.y - b.y, c.L[1], c.halfL[1]);
+    double dz = min_image(p.z - b.z, c.L[2], c.halfL[2]);
+    const double disp = sqrt(dx * dx + dy * dy + dz * dz) * (1.0 + 1e-9);
+    const double sig = c.skin_theta * (c.skin_s * ctl->kappa_b * p.w + ctl->sigma0) * (1.0 - 1e-9);
+    if (disp + (ctl->kappa - ctl->kappa_b) * p.w * 0.5 * (1.0 + 1e-9) > sig) ctl->need_rebuild = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -483,12 +518,15 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
     if (threadIdx.x == 0 && bm < INFINITY) atomicMin(&ctl->shrink_bits, dbits(bm));
 }
 
-// kappa_c = min(kappa, q_min); phi = (pi/6) kappa_c^3 sum D^3 / V.
+// kappa_c = min(kappa, q_min) (1 - 2^-50): lowered by a few units in the
+// last place so that no pair overlaps when re-evaluated in binary64;
+// phi = (pi/6) kappa_c^3 sum D^3 / V.
 __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c)
 {
     double q = bitsd(ctl->shrink_bits);
     double kc = ctl->kappa;
     if (q < kc) kc = q;
+    kc = kc * (1.0 - 0x1.0p-50);
     ctl->kappa_c = kc;
     ctl->phi = (((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) / c.V;
 }

@@ -107,8 +107,8 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c)
 
 // Per-block scalars, derived once per block from the control block.
 struct MixScalars {
-    float kappa, kappa_lo, eps, h1, h2, be1, be2, o1, o2, eta, aeps;
-    float limA, limB;  // skin budget: theta (s kappa_b D + sigma0) (1 - 1e-5) = limA D + limB
+    float kappa, kappa_lo, rkappa, eps, rh1, rh2, be1, be2, o1, o2, eta, aeps;
+    float limA, limB;  // theta sigma_i (1 - 1e-5) = limA D_i + limB
 };
 
 __device__ __forceinline__ void mix_scalars(const RcpCtl* ctl, const RcpConst& c, MixScalars& s)
@@ -116,18 +116,19 @@ __device__ __forceinline__ void mix_scalars(const RcpCtl* ctl, const RcpConst& c
     const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
     s.kappa = (float)ctl->kappa;
     s.kappa_lo = (float)(ctl->kappa - (double)s.kappa);
+    s.rkappa = (float)(1.0 / ctl->kappa);
     s.eps = (float)c.eps;
-    s.h1 = (float)(1.0 - b1);
-    s.h2 = (float)(1.0 - b2);
+    s.rh1 = (float)(1.0 / (1.0 - b1));
+    s.rh2 = (float)(1.0 / (1.0 - b2));
     s.be1 = (float)c.beta1;
     s.be2 = (float)c.beta2;
     s.o1 = (float)(1.0 - c.beta1);
     s.o2 = (float)(1.0 - c.beta2);
     s.eta = (float)ctl->eta_x;
     s.aeps = (float)c.adam_eps;
-    const double m = c.skin_theta * (1.0 - 1e-5);
-    s.limA = (float)(m * c.skin_s * ctl->kappa_b);
-    s.limB = (float)(m * ctl->sigma0);
+    const double mth = c.skin_theta * (1.0 - 1e-5);
+    s.limA = (float)(mth * c.skin_s * ctl->kappa_b);
+    s.limB = (float)(mth * ctl->sigma0);
 }
 
 // Adam on one axis of a record: binary32 moments, step added to the
@@ -137,7 +138,7 @@ __device__ __forceinline__ void adam_fixed(float g, float& m, float& v, int& q, 
 {
     m = s.be1 * m + s.o1 * g;
     v = s.be2 * v + s.o2 * (g * g);
-    const float step = (s.eta * (m / s.h1)) / (sqrtf(v / s.h2) + s.aeps);
+    const float step = __fdividef(s.eta * (m * s.rh1), sqrtf(v * s.rh2) + s.aeps);
     float d = -step * qinv;                      // displacement in fixed-point units
     d = fminf(fmaxf(d, -1073741824.0f), 1073741824.0f);
     const float di = floorf(d);
@@ -222,8 +223,8 @@ __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& r
     dz = zh;
     r = sqrtf(s2);
     if (!(n > 0.0f)) return n;
-    const float u = n / d2h;
-    return u / (1.0f + sqrtf(1.0f - u));
+    const float u = __fdividef(n, d2h);
+    return __fdividef(u, 1.0f + sqrtf(1.0f - u));
 }
 
 // Terms of one listed pair (i, j): gradient into the compensated (g, c), the
@@ -251,22 +252,51 @@ __device__ __forceinline__ void pair_term(const MixRec& ri, const MixRec& rj, lo
     if (!(delta > 0.0f)) return;
     const float dd = S.kappa * (0.5f * (ri.l.w + rj.l.w));
     if (r > 0.0f) {
-        const float coef = (S.eps * delta) / (dd * r);
+        const float coef = __fdividef(S.eps * delta, dd * r);
         acc2(a.g0, a.c0, -coef * dx);
         acc2(a.g1, a.c1, -coef * dy);
         acc2(a.g2, a.c2, -coef * dz);
     }
     if ((long long)j > i) {
         acc2(es, ec, (0.5f * S.eps) * (delta * delta));
-        acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) / S.kappa);
+        acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) * S.rkappa);
     }
     md = fmaxf(md, delta);
 }
 
+// Skin budget of a record against its build snapshot (binary32 with 1e-5
+// margins): what its displacement leaves for kappa growth,
+// b_i = 2 (theta sigma_i - |x_i - x_i^b|) / D_i; negative flags the rebuild.
+__device__ __forceinline__ float skin_budget32(RcpCtl* ctl, const RcpConst& c, const MixScalars& S, const MixRec& rn,
+                                               const MixRec& b)
+{
+    const float ex = rec_dx(rn.q.x, rn.l.x, b.q.x, b.l.x, c.qscale[0]);
+    const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, c.qscale[1]);
+    const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, c.qscale[2]);
+    const float disp = sqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, ez * ez))) * 1.00001f;
+    const float sig = __fmaf_rn(S.limA, rn.l.w, S.limB);
+    const float bi = 2.0f * (sig - disp) / rn.l.w * 0.99999f;
+    if (!(bi >= 0.0f)) {
+        atomicOr(&ctl->disp_flag, 1u);
+        return INFINITY;
+    }
+    return bi;
+}
+
+__device__ __forceinline__ void push_budget32(RcpCtl* ctl, float bud)
+{
+    for (int o = 16; o > 0; o >>= 1) bud = fminf(bud, __shfl_down_sync(0xffffffffu, bud, o));
+    if ((threadIdx.x & 31) == 0 && bud < INFINITY) {
+        const unsigned int bits = __float_as_uint(bud);
+        if (bits < *(volatile unsigned int*)&ctl->kbud_bits) atomicMin(&ctl->kbud_bits, bits);
+    }
+}
+
 // Close row i: the Adam step of its record (Adam mode) or its gradient out.
-__device__ __forceinline__ void row_epilogue(RcpCtl* ctl, const RcpConst& c, const MixScalars& S, long long i,
-                                             const MixRec& ri, float g0, float g1, float g2, float* m, float* v,
-                                             MixRec* rout, const MixRec* rb, int mode, double* g_out)
+// Returns the row's skin budget (infinity in gradient mode).
+__device__ __forceinline__ float row_epilogue(RcpCtl* ctl, const RcpConst& c, const MixScalars& S, long long i,
+                                              const MixRec& ri, float g0, float g1, float g2, float* m, float* v,
+                                              MixRec* rout, const MixRec* rb, int mode, double* g_out)
 {
     if (mode == RCP_MODE_ADAM) {
         MixRec rn = ri;
@@ -278,18 +308,12 @@ __device__ __forceinline__ void row_epilogue(RcpCtl* ctl, const RcpConst& c, con
         m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
         v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
         rout[i] = rn;
-        // skin check against the build snapshot, binary32 with a margin
-        const MixRec b = rb[i];
-        const float ex = rec_dx(rn.q.x, rn.l.x, b.q.x, b.l.x, c.qscale[0]);
-        const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, c.qscale[1]);
-        const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, c.qscale[2]);
-        const float lim = __fmaf_rn(S.limA, ri.l.w, S.limB);
-        if (ex * ex + ey * ey + ez * ez > lim * lim) atomicOr(&ctl->disp_flag, 1u);
-    } else {
-        g_out[3 * i] = (double)g0;
-        g_out[3 * i + 1] = (double)g1;
-        g_out[3 * i + 2] = (double)g2;
+        return skin_budget32(ctl, c, S, rn, rb[i]);
     }
+    g_out[3 * i] = (double)g0;
+    g_out[3 * i + 1] = (double)g1;
+    g_out[3 * i + 2] = (double)g2;
+    return INFINITY;
 }
 
 __device__ __forceinline__ float warp_sum2f(float s, float c)
@@ -317,8 +341,6 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
              const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
              double* part_k, int mode, double* g_out)
 {
-    __shared__ double she[RCP_PAIR_THREADS / 32], shk[RCP_PAIR_THREADS / 32];
-    __shared__ float shm[RCP_PAIR_THREADS / 32];
     __shared__ MixScalars S;
     if (ctl->halted) return;
     if (threadIdx.x == 0) mix_scalars(ctl, c, S);
@@ -328,6 +350,7 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
     MixRec* __restrict__ rout = parity ? rA : rB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
+    float bud = INFINITY;
     if (blockIdx.x < RCP_LONG_BLOCKS) {
         const unsigned int nlong = ctl->n_long;
         const unsigned int nw = RCP_LONG_BLOCKS * (RCP_PAIR_THREADS / 32);
@@ -353,7 +376,7 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
             const float g0 = warp_sum2f(a.g0, a.c0);
             const float g1 = warp_sum2f(a.g1, a.c1);
             const float g2 = warp_sum2f(a.g2, a.c2);
-            if (lane == 0) row_epilogue(ctl, c, S, i, ri, g0, g1, g2, m, v, rout, rb, mode, g_out);
+            if (lane == 0) bud = fminf(bud, row_epilogue(ctl, c, S, i, ri, g0, g1, g2, m, v, rout, rb, mode, g_out));
         }
     } else {
         const long long i = (long long)(blockIdx.x - RCP_LONG_BLOCKS) * RCP_PAIR_THREADS + threadIdx.x;
@@ -373,31 +396,25 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
                     const unsigned int j = col[t];
                     pair_term(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
                 }
-                row_epilogue(ctl, c, S, i, ri, a.g0 + a.c0, a.g1 + a.c1, a.g2 + a.c2, m, v, rout, rb, mode, g_out);
+                bud = row_epilogue(ctl, c, S, i, ri, a.g0 + a.c0, a.g1 + a.c1, a.g2 + a.c2, m, v, rout, rb, mode,
+                                   g_out);
             }
         }
     }
+    // per-warp partials (no block barrier: warps finish independently)
+    push_budget32(ctl, bud);
     warp_sum2(es, ec);
     warp_sum2(ks, kc);
     float wm = md;
     for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_down_sync(0xffffffffu, wm, o));
     if (lane == 0) {
-        she[warp] = (double)es + (double)ec;
-        shk[warp] = (double)ks + (double)kc;
-        shm[warp] = wm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double se = 0.0, sk = 0.0;
-        float bm = 0.f;
-        for (int w = 0; w < RCP_PAIR_THREADS / 32; ++w) {
-            se = se + she[w];
-            sk = sk + shk[w];
-            bm = fmaxf(bm, shm[w]);
+        const unsigned long long w = (unsigned long long)blockIdx.x * (RCP_PAIR_THREADS / 32) + warp;
+        part_e[w] = (double)es + (double)ec;
+        part_k[w] = (double)ks + (double)kc;
+        if (wm > 0.f) {
+            const unsigned long long b = dbits((double)wm);
+            if (b > *(volatile unsigned long long*)&ctl->maxdelta_bits) atomicMax(&ctl->maxdelta_bits, b);
         }
-        part_e[blockIdx.x] = se;
-        part_k[blockIdx.x] = sk;
-        if (bm > 0.f) atomicMax(&ctl->maxdelta_bits, dbits((double)bm));
     }
 }
 
@@ -442,23 +459,21 @@ __global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, MixRec* rA, MixRec* rB, fl
         S.eta = (float)eta_x;
     }
     __syncthreads();
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.N) return;
-    MixRec* r = ctl->parity ? rB : rA;
-    MixRec rn = r[i];
-    for (int a = 0; a < 3; ++a) {
-        float mm = m[3 * i + a], vv = v[3 * i + a];
-        int* q = a == 0 ? &rn.q.x : (a == 1 ? &rn.q.y : &rn.q.z);
-        float* l = a == 0 ? &rn.l.x : (a == 1 ? &rn.l.y : &rn.l.z);
-        adam_fixed((float)g[3 * i + a], mm, vv, *q, *l, c.qinv[a], S);
-        m[3 * i + a] = mm;
-        v[3 * i + a] = vv;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float bud = INFINITY;
+    if (i < c.N) {
+        MixRec* r = ctl->parity ? rB : rA;
+        MixRec rn = r[i];
+        for (int a = 0; a < 3; ++a) {
+            float mm = m[3 * i + a], vv = v[3 * i + a];
+            int* q = a == 0 ? &rn.q.x : (a == 1 ? &rn.q.y : &rn.q.z);
+            float* l = a == 0 ? &rn.l.x : (a == 1 ? &rn.l.y : &rn.l.z);
+            adam_fixed((float)g[3 * i + a], mm, vv, *q, *l, c.qinv[a], S);
+            m[3 * i + a] = mm;
+            v[3 * i + a] = vv;
+        }
+        r[i] = rn;
+        bud = skin_budget32(ctl, c, S, rn, rb[i]);
     }
-    r[i] = rn;
-    const MixRec b = rb[i];
-    const float ex = rec_dx(rn.q.x, rn.l.x, b.q.x, b.l.x, c.qscale[0]);
-    const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, c.qscale[1]);
-    const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, c.qscale[2]);
-    const float lim = __fmaf_rn(S.limA, rn.l.w, S.limB);
-    if (ex * ex + ey * ey + ez * ez > lim * lim) atomicOr(&ctl->disp_flag, 1u);
+    push_budget32(ctl, bud);
 }

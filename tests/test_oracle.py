@@ -297,17 +297,17 @@ def test_levels_and_cells_follow_definition(orc):
     cnt = np.bincount(lvl)
     for k in range(len(rml)):
         assert rml[k] == rho[lvl == k].max()
-        nk = orc.grid_n(1.0, rml[k], int(cnt[k]), 1.0)
+        nk = orc.grid_n(1.0, int(cnt[k]), 1.0, 2.0)
         # power of two whose cells hold >= 2 spheres of the class on average;
         # the next finer grid would not
         h = 1.0 / nk
         assert nk & (nk - 1) == 0 and (nk == 1 or h ** 3 * cnt[k] >= 2.0)
         assert nk == 2 ** 19 or (h / 2) ** 3 * cnt[k] < 2.0
     x = orc.init_positions(4, 3000)
-    key = orc.cell_keys(x, D0, 1.0, kb, s, sg)
+    key = orc.cell_keys(x, D0, 1.0, kb, s, sg, occ=2.0)
     assert np.array_equal((key >> np.uint64(57)).astype(int), lvl)
     for i in range(0, 3000, 11):
-        nk = orc.grid_n(1.0, rml[int(lvl[i])], int(cnt[int(lvl[i])]), 1.0)
+        nk = orc.grid_n(1.0, int(cnt[int(lvl[i])]), 1.0, 2.0)
         c = [int((int(key[i]) >> sh) & (2 ** 19 - 1)) for sh in (0, 19, 38)]
         assert c == [min(int(math.floor(x[i, a] * nk)), nk - 1) for a in range(3)]
 
@@ -333,11 +333,11 @@ def test_shrink_to_contact(orc):
     assert kc < k
     _, _, _, md = orc.energy_grad(x, D0, 1.0, kc, 0.0)
     assert md == 0.0
-    # one pair is exactly in contact: a hair larger kappa overlaps
+    # one pair is in contact: a hair larger kappa overlaps
     _, _, _, md2 = orc.energy_grad(x, D0, 1.0, kc * (1 + 1e-12), 0.0)
     assert 0 < md2 < 1e-11
-    # without overlaps kappa is kept
-    assert orc.shrink_kappa(x, D0, 1.0, kc * 0.5, rp, col) == kc * 0.5
+    # without overlaps kappa is kept (up to the few-ulp margin)
+    assert orc.shrink_kappa(x, D0, 1.0, kc * 0.5, rp, col) == (kc * 0.5) * (1.0 - 2.0 ** -50)
 
 
 def test_phi_closed_form(orc):
@@ -368,3 +368,32 @@ def test_table1_small_rows(orc, alpha, S, phi_paper):
     r = orc.run(D0, seed=1)
     assert r.stopped
     assert abs(r.phi - phi_paper) < 0.012
+
+
+def test_rebuild_criterion_keeps_every_overlap_listed(orc):
+    """Move every sphere as far as the rebuild test allows (|dx_i| + (kappa -
+    kappa_b) D_i/2 = sigma_i, in random directions) and grow kappa: every pair
+    that now overlaps was listed at the build."""
+    rng = np.random.default_rng(4)
+    n, s, sigma0 = 400, 0.1, 0.004
+    D0 = inputs.lognormal(n, 0.7, 30.0)
+    kb = orc.kappa0(D0, 1.0, 0.45)
+    x = orc.init_positions(3, n)
+    rp, col = orc.list_grid(x, D0, 1.0, kb, s, sigma0)
+    listed = set(zip(np.repeat(np.arange(n), np.diff(rp)).tolist(), col.tolist()))
+    for grow in (0.0, 0.05, 0.15):
+        k = kb * (1 + grow)
+        sig = s * kb * D0 + sigma0
+        room = sig - (k - kb) * D0 / 2
+        if (room < 0).any():
+            continue
+        u = rng.standard_normal((n, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        xm = np.mod(x + u * room[:, None] * (1 - 1e-12), 1.0)
+        d = xm[:, None, :] - xm[None, :, :]
+        d -= np.rint(d)
+        r = np.sqrt((d ** 2).sum(-1))
+        over = r < k * 0.5 * (D0[:, None] + D0[None, :])
+        np.fill_diagonal(over, False)
+        for i, j in zip(*np.nonzero(over)):
+            assert (int(i), int(j)) in listed
