@@ -143,8 +143,11 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
 rcp_status rcp_destroy(rcp_handle h);
 
 /* Issue the handle's work on `stream` (a cudaStream_t of the handle's
- * device; NULL selects the handle's own stream).  Captured graphs are
- * re-captured on the next call that needs them. */
+ * device; NULL selects the handle's own stream; cudaStreamLegacy selects the
+ * legacy default stream, on which graphs cannot be captured: rcp_run then
+ * replays its graph on the handle's own stream, ordered before and after
+ * with events).  Captured graphs are re-captured on the next call that needs
+ * them. */
 rcp_status rcp_set_stream(rcp_handle h, void* stream);
 
 /* Replace the positions (N x 3, wrapped into the box) and optionally kappa
@@ -167,6 +170,16 @@ rcp_status rcp_build_neighbors(rcp_handle h);
  * on_device = 1 all non-NULL outputs are device pointers. */
 rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x,
                            double* dE_dkappa, double* max_delta, int on_device);
+
+/* Evaluate at a state given on the device: positions x_dev [N][3] (inside
+ * or outside the box; wrapped) and kappa_dev (one double) become the
+ * handle's state, the neighbour structure is rebuilt if the skin test asks
+ * for it, and E, grad_x[N][3], dE/dkappa and max delta are written to the
+ * given device pointers (any of them may be NULL).  This is the forward of
+ * the torch.autograd binding: one fused pass gives the energy and both
+ * gradients.  Reads one flag back to the host (the rebuild decision). */
+rcp_status rcp_energy_grad_at(rcp_handle h, const double* x_dev, const double* kappa_dev, double mu,
+                              double* E, double* grad_x, double* dE_dkappa, double* max_delta);
 
 /* One Adam step (Kingma & Ba, Algorithm 1) on every coordinate and on kappa
  * with the given gradient (grad_x[N][3], host or device per on_device) and

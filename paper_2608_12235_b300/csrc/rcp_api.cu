@@ -105,10 +105,13 @@ struct rcp_ctx {
     long long launches = 0;
     long long g_kernels = 0;
 
-    // graph
+    // graph (captured on cap_stream: the user stream, or the handle's own
+    // stream when the user stream is the legacy default stream, which cannot
+    // be captured -- replays are then ordered with events)
     cudaGraphExec_t gexec = nullptr;
     int gT = 0;
     cudaStream_t g_stream = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     unsigned long long g_pcap = 0;
 };
 
@@ -482,6 +485,10 @@ rcp_status ensure_list(rcp_ctx* h)
     return RCP_OK;
 }
 
+bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy; }
+
+cudaStream_t capture_stream(const rcp_ctx* h) { return capturable(h->stream) ? h->stream : h->own_stream; }
+
 rcp_status capture_graph(rcp_ctx* h)
 {
     if (h->gexec && h->gT == h->cfg.chunk && h->g_stream == h->stream && h->g_pcap == h->pcap) return RCP_OK;
@@ -490,10 +497,17 @@ rcp_status capture_graph(rcp_ctx* h)
         h->gexec = nullptr;
     }
     cudaGraph_t graph;
-    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t user = h->stream;
+    h->stream = capture_stream(h);  // launch_iteration issues on h->stream
+    cudaError_t e0 = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e0 != cudaSuccess) {
+        h->stream = user;
+        return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e0));
+    }
     h->g_kernels = 0;
     for (int t = 0; t < h->cfg.chunk; ++t) h->g_kernels += launch_iteration(h, RCP_MODE_ADAM);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->stream = user;
     if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&h->gexec, graph, 0);
     cudaGraphDestroy(graph);
@@ -609,6 +623,8 @@ rcp_status rcp_destroy(rcp_handle h)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->ctl_h) cudaFreeHost(h->ctl_h);
+    if (h->ev_a) cudaEventDestroy(h->ev_a);
+    if (h->ev_b) cudaEventDestroy(h->ev_b);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
     return RCP_OK;
@@ -671,6 +687,8 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CK(cudaGetDevice(&h->device));
         CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
         h->stream = h->own_stream;
+        CK(cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming));
         const size_t n = (size_t)N;
         CKS(dalloc(h, &h->D0, n));
         CKS(dalloc(h, &h->xA, n));
@@ -840,6 +858,31 @@ rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x, d
     return RCP_OK;
 }
 
+rcp_status rcp_energy_grad_at(rcp_handle h, const double* x_dev, const double* kappa_dev, double mu, double* E,
+                              double* grad_x, double* dE_dkappa, double* max_delta)
+{
+    if (!h || !x_dev || !kappa_dev) return RCP_ERR_ARG;
+    const size_t n = (size_t)h->N;
+    CK(cudaMemcpyAsync(h->xtmp, x_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(&h->ctl->kappa, kappa_dev, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKS(sync_ctl(h));  // parity and build state
+    double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
+    h->launches += 1;
+    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur);
+    CKL();
+    if (h->cfg.precision == RCP_MIXED) {
+        h->launches += 1;
+        k_to_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rA, h->rB, nullptr);
+        CKL();
+    }
+    if (h->built) {
+        h->launches += 1;
+        k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
+        CKL();
+    }
+    return rcp_energy_grad(h, mu, E, grad_x, dE_dkappa, max_delta, 1);
+}
+
 rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, double lr_x, double lr_kappa,
                          int on_device)
 {
@@ -964,7 +1007,16 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
             prof->ms_iter += b;
             prof->launches += 1;
         } else {
-            CK(cudaGraphLaunch(h->gexec, h->stream));
+            const cudaStream_t cs = capture_stream(h);
+            if (cs != h->stream) {
+                CK(cudaEventRecord(h->ev_a, h->stream));
+                CK(cudaStreamWaitEvent(cs, h->ev_a, 0));
+            }
+            CK(cudaGraphLaunch(h->gexec, cs));
+            if (cs != h->stream) {
+                CK(cudaEventRecord(h->ev_b, cs));
+                CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
+            }
             h->launches += h->g_kernels;
         }
         CKS(sync_ctl(h));

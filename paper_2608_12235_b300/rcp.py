@@ -22,7 +22,7 @@ STATUS = {0: "RCP_OK", 1: "RCP_ERR_ARG", 2: "RCP_ERR_IMAGE", 3: "RCP_ERR_OOM", 4
 
 # every symbol include/rcp.h declares
 EXPORTS = ["rcp_config_default", "rcp_create", "rcp_destroy", "rcp_set_stream", "rcp_set_positions",
-           "rcp_build_neighbors", "rcp_energy_grad", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
+           "rcp_build_neighbors", "rcp_energy_grad", "rcp_energy_grad_at", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
            "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_status_str", "rcp_last_error",
            "rcp_energy_grad_noalloc"]
 
@@ -80,6 +80,7 @@ def load(path: str | None = None) -> C.CDLL:
     L.rcp_build_neighbors.argtypes = [vp]
     L.rcp_energy_grad.argtypes = [vp, C.c_double, vp, vp, vp, vp, ip]
     L.rcp_adam_step.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, ip]
+    L.rcp_energy_grad_at.argtypes = [vp, vp, vp, C.c_double, vp, vp, vp, vp]
     L.rcp_run.argtypes = [vp, C.POINTER(rcp_stop), C.POINTER(rcp_result)]
     L.rcp_profile.argtypes = [vp, C.c_longlong, dp, dp, C.POINTER(C.c_longlong)]
     L.rcp_shrink.argtypes = [vp, dp, dp]
@@ -140,8 +141,21 @@ def rcp_destroy(h):
     _check(load().rcp_destroy(h))
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
 def rcp_set_stream(h, stream: int | None):
+    """stream: a cudaStream_t address, None for the handle's own stream, or
+    CUDA_STREAM_LEGACY for the legacy default stream (torch's default)."""
     _check(load().rcp_set_stream(h, stream), h)
+
+
+def torch_stream(device=None) -> int:
+    """The cudaStream_t of torch's current stream, mapping torch's default
+    stream (handle 0) to cudaStreamLegacy so that work stays ordered with it."""
+    import torch
+    s = torch.cuda.current_stream(device).cuda_stream
+    return s if s else CUDA_STREAM_LEGACY
 
 
 def rcp_set_positions(h, x, kappa: float = 0.0, on_device: bool = False):
@@ -159,6 +173,12 @@ def rcp_energy_grad(h, mu: float, E=None, grad_x=None, dE_dkappa=None, max_delta
     float64 CUDA tensors with on_device=True)."""
     _check(load().rcp_energy_grad(h, mu, _ptr(E), _ptr(grad_x), _ptr(dE_dkappa), _ptr(max_delta),
                                   int(on_device)), h)
+
+
+def rcp_energy_grad_at(h, x_dev, kappa_dev, mu: float, E=None, grad_x=None, dE_dkappa=None, max_delta=None):
+    """Device-pointer evaluation (torch CUDA float64 tensors) on the handle's stream."""
+    _check(load().rcp_energy_grad_at(h, _ptr(x_dev), _ptr(kappa_dev), mu, _ptr(E), _ptr(grad_x), _ptr(dE_dkappa),
+                                     _ptr(max_delta)), h)
 
 
 def rcp_adam_step(h, grad_x, dE_dkappa: float, lr_x: float, lr_kappa: float, on_device=False):
