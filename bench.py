@@ -113,6 +113,19 @@ def cpu_baseline(D0, iters, phi=0.5, seed=0):
     return iters / dt, dt, builds
 
 
+def aggregate(ms: float, iters: float, world: int, dist=None, device="cuda"):
+    """Whole-job throughput: iterations of all ranks over the slowest rank's
+    timed region.  Returns (iterations/s, max ms)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        n = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms, iters = float(t[0]), float(n[0])
+    return iters / (ms / 1e3), ms
+
+
 def run_reference(args, w):
     """--impl reference: the CPU oracle on the same workload and metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -203,15 +216,7 @@ def main():
     x_end, _, _, s_end = p.state()
     iters_done = s_end.t - it0
     rebuilds = r.rebuilds
-    if world > 1:
-        t = torch.tensor([ms, float(iters_done)], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, total_iters = float(tmax[0]), float(t[1])
-    else:
-        total_iters = float(iters_done)
-    value = total_iters / (ms / 1e3)
+    value, ms = aggregate(ms, iters_done, world, dist)
     pair_evals = pairs_sum / 2.0 / (ms / 1e3) * world  # unordered pairs
     phi_now = (np.pi / 6.0) * s_end.kappa ** 3 * float(np.sum(D0.astype(np.float64) ** 3))
 
