@@ -126,6 +126,73 @@ def aggregate(ms: float, iters: float, world: int, dist=None, device="cuda"):
     return iters / (ms / 1e3), ms
 
 
+def bench_batch(rcp, torch, iters: int, seed: int = 0, count: int = 64):
+    """64 independent packings (N log-uniform in [1e3, 1e5], lognormal sigma_ln
+    in [0.2, 1], S log-uniform in [5, 200], mixed precision): `iters`
+    iterations of each from its start, advanced together by one graph of
+    batched kernels (autotuned), against the same packings run one after
+    another.  Aggregate packing-iterations/s."""
+    from paper_2608_12235_b300 import inputs
+    specs = inputs.batch_specs(count, master_seed=seed)
+    mk = lambda: [rcp.Packing(s["D0"], seed=s["seed"], precision=rcp.RCP_MIXED) for s in specs]
+    packs = mk()
+    b = rcp.Batch(packs, autotune=True)
+    b.run(max_iters=iters // 3, shrink=False)              # tuning and warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = b.run(max_iters=iters, shrink=False)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    n_it = sum(r.iters for r in res) - count * (iters // 3)
+    lr, chunk = b.tuning()
+    b.close()
+    for p in packs:
+        p.close()
+    packs = mk()
+    for p in packs:
+        p.run(max_iters=iters // 3, shrink=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p in packs:
+        p.run(max_iters=iters, shrink=False)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    for p in packs:
+        p.close()
+    return {"packings": count, "spheres": int(sum(s["N"] for s in specs)), "iters_per_packing": iters,
+            "batched_iters_per_s": n_it / tb, "sequential_iters_per_s": count * iters / ts,
+            "speedup": (n_it / tb) / (count * iters / ts), "tuned_long_row": lr, "tuned_chunk": chunk}
+
+
+def bench_autograd(rcp, torch, reps: int = 20):
+    """Fused forward + backward of the autograd binding (binary64) on N = 2e5
+    truncated Weibull (k = 1.5, S = 100) at phi = 0.6, uniform positions."""
+    from paper_2608_12235_b300 import autograd, inputs
+    D0 = inputs.weibull(200_000, 1.5, 100.0)
+    p = rcp.Packing(D0, seed=0)
+    dev = torch.device("cuda", 0)
+    S3 = float(np.sum(D0 ** 3))
+    k = (0.6 / (np.pi / 6 * S3)) ** (1 / 3)
+    x = torch.rand((D0.size, 3), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    kt = torch.tensor(k, dtype=torch.float64, device=dev)
+    out = {}
+    for name, prec in (("fp64", rcp.RCP_FP64), ("mixed", rcp.RCP_MIXED)):
+        p = rcp.Packing(D0, seed=0, precision=prec)
+        xr = x.clone().requires_grad_(True)
+        for _ in range(3):
+            autograd.energy(xr, kt, p, 0.0).backward()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            xr.grad = None
+            autograd.energy(xr, kt, p, 0.0).backward()
+        torch.cuda.synchronize()
+        out[name] = reps / (time.perf_counter() - t0)
+        p.close()
+    return {"workload": "weibull-n2e5-s100 phi 0.6", "fwd_bwd_per_s_fp64": out["fp64"],
+            "fwd_bwd_per_s_mixed": out["mixed"]}
+
+
 def run_reference(args, w):
     """--impl reference: the CPU oracle on the same workload and metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -158,6 +225,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and autograd measurements")
+    ap.add_argument("--batch-iters", type=int, default=300)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -261,6 +330,12 @@ def main():
     e2e_dt = time.perf_counter() - t0
     e2e_rate = e_steps * ips / e2e_dt * world
 
+    # ---- extras: 64 packings in one graph vs one after another; autograd
+    extras = {}
+    if not args.no_extras:
+        extras["batch"] = bench_batch(rcp, torch, args.batch_iters, seed=rank)
+        extras["autograd"] = bench_autograd(rcp, torch)
+
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -290,6 +365,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     p.close()
     if world > 1:

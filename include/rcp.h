@@ -233,6 +233,36 @@ rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys);
 /* Number of spheres. */
 long long rcp_size(rcp_handle h);
 
+/* ---- batches: many independent packings in one graph of batched kernels ---- */
+typedef struct rcp_batch_ctx* rcp_batch;
+
+/* Group B existing handles (same device, same precision; each at most ~8192
+ * block partial sums, i.e. N up to ~2e6 in binary64 or ~2.5e5 in mixed
+ * precision) for rcp_batch_run.  The handles keep their state and ownership;
+ * destroy the batch before its handles.  autotune = 1 times, on the first
+ * run, the long-row threshold of the mixed pair kernel (16, 32, 64, 128) and
+ * the iterations per graph replay (8, 16, 32, 64) and keeps the fastest.
+ * A failure message is left in rcp_last_error(hs[0]). */
+rcp_status rcp_batch_create(rcp_handle* hs, int B, int autotune, rcp_batch* out);
+
+/* Advance every packing of the batch as rcp_run would (its own rung schedule,
+ * stopping test, rebuilds, and shrink to contact once it stops), all of them
+ * in each replay of one CUDA graph whose per-iteration work is one batched
+ * pair kernel and one batched kappa step.  A packing's trajectory is
+ * bit-identical to running it alone with the same long-row threshold.
+ * outs (may be NULL) receives B summaries; outs[0].launches counts the
+ * batch's kernel launches.  Returns the first non-OK status of a packing. */
+rcp_status rcp_batch_run(rcp_batch b, const rcp_stop* stop, rcp_result* outs);
+
+/* The tuned long-row threshold and iterations per replay. */
+rcp_status rcp_batch_tuning(rcp_batch b, int* long_row, int* chunk);
+
+/* Free the batch (not its handles).  NULL is accepted. */
+rcp_status rcp_batch_destroy(rcp_batch b);
+
+/* Message of the last failure on this batch ("" if none). */
+const char* rcp_batch_last_error(rcp_batch b);
+
 /* Largest N accepted by rcp_energy_grad_noalloc. */
 #define RCP_NOALLOC_MAX_N (1LL << 21)
 

@@ -301,6 +301,9 @@ std::vector<int> field_shifts(int lo, int nbits)
 }
 
 // ---------------------------------------------------------------- build
+rcp_status search_once(rcp_ctx* h);
+rcp_status relist_long(rcp_ctx* h);
+
 rcp_status ensure_pair_capacity(rcp_ctx* h, unsigned long long P)
 {
     if (P <= h->pcap && h->pairs1) return RCP_OK;
@@ -312,7 +315,12 @@ rcp_status ensure_pair_capacity(rcp_ctx* h, unsigned long long P)
     return ensure_hist(h, cap > (unsigned long long)h->N ? cap : (unsigned long long)h->N);
 }
 
-rcp_status build(rcp_ctx* h)
+// The build runs in three phases separated by host reads, so that several
+// packings can be built concurrently on their own streams (the batch):
+//   A: class sizes and grids (ctl copied to the host);
+//   B: keys, sort, hash, search (entry count copied to the host);
+//   C: pair sort, CSR, long-row list, snapshot.
+rcp_status build_a(rcp_ctx* h)
 {
     const long long N = h->N;
     const unsigned int nbN = rcp_ceil_div(N, 256);
@@ -326,7 +334,14 @@ rcp_status build(rcp_ctx* h)
     h->launches += 1;
     k_grid<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
     CKL();
-    CKS(sync_ctl(h));
+    CK(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(RcpCtl), cudaMemcpyDeviceToHost, h->stream));
+    return RCP_OK;
+}
+
+rcp_status build_b(rcp_ctx* h)
+{
+    const long long N = h->N;
+    const unsigned int nbN = rcp_ceil_div(N, 256);
     if (h->ctl_h->status == RCP_ERR_IMAGE)
         return fail(h, RCP_ERR_IMAGE,
                     "largest interaction diameter 4 rho_max = %.6g reaches the smallest box edge %.6g: a sphere "
@@ -362,18 +377,36 @@ rcp_status build(rcp_ctx* h)
     h->launches += 1;
     k_hash_heads<<<nbN, 256, 0, h->stream>>>(skeys, N, h->hkeys, h->hvals, h->hcap - 1);
     CKL();
+    return search_once(h);
+}
+
+rcp_status search_once(rcp_ctx* h)
+{
+    const long long N = h->N;
+    const unsigned int nbN = rcp_ceil_div(N, 256);
     const int nbits = bits_for((unsigned long long)N);
-    unsigned long long P = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
-        h->launches += 1;
-        k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xf,
-                                             h->xsf, h->hkeys, h->hvals, h->hcap - 1, h->pairs1, h->pcap, nbits);
-        CKL();
-        CK(cudaMemcpyAsync(&P, &h->ctl->pair_cursor, sizeof(P), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
+    h->launches += 1;
+    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xf, h->xsf,
+                                         h->hkeys, h->hvals, h->hcap - 1, h->pairs1, h->pcap, nbits);
+    CKL();
+    CK(cudaMemcpyAsync(&h->ctl_h->pair_cursor, &h->ctl->pair_cursor, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, h->stream));
+    return RCP_OK;
+}
+
+rcp_status build_c(rcp_ctx* h)
+{
+    const long long N = h->N;
+    const unsigned int nbN = rcp_ceil_div(N, 256);
+    const int nbits = bits_for((unsigned long long)N);
+    unsigned long long P = h->ctl_h->pair_cursor;
+    if (P > h->pcap) {
+        // entries beyond the old capacity were dropped: grow and search again
+        CKS(ensure_pair_capacity(h, P));
+        CKS(search_once(h));
         CK(cudaStreamSynchronize(h->stream));
-        if (P <= h->pcap) break;
-        CKS(ensure_pair_capacity(h, P));  // entries beyond the old capacity were dropped: search again
+        P = h->ctl_h->pair_cursor;
     }
     if (P >= (1ull << 32)) return fail(h, RCP_ERR_CAPACITY, "more than 2^32 listed pairs");
     std::vector<int> ps = field_shifts(0, nbits);
@@ -383,12 +416,8 @@ rcp_status build(rcp_ctx* h)
     h->launches += 1;
     k_csr<<<rcp_ceil_div((P > (unsigned long long)N ? P : (unsigned long long)N) + 1, 256), 256, 0, h->stream>>>(
         spairs, (long long)P, N, nbits, h->rowptr, h->col);
-    h->launches += 1;
-    k_long_flags<<<nbN, 256, 0, h->stream>>>(h->rowptr, N, h->cnt);
     CKL();
-    CKS(scan_u32(h, h->cnt, (unsigned long long)N, h->offs, h->scan_tmp));
-    h->launches += 1;
-    k_long_compact<<<nbN, 256, 0, h->stream>>>(h->ctl, h->cnt, h->offs, N, h->long_rows);
+    CKS(relist_long(h));
     h->launches += 1;
     k_build_end<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb, P);
     CKL();
@@ -402,6 +431,30 @@ rcp_status build(rcp_ctx* h)
     return RCP_OK;
 }
 
+// Rows longer than c.long_row, compacted (used by the mixed pair kernel).
+rcp_status relist_long(rcp_ctx* h)
+{
+    const long long N = h->N;
+    const unsigned int nbN = rcp_ceil_div(N, 256);
+    h->launches += 1;
+    k_long_flags<<<nbN, 256, 0, h->stream>>>(h->rowptr, N, h->c.long_row, h->cnt);
+    CKL();
+    CKS(scan_u32(h, h->cnt, (unsigned long long)N, h->offs, h->scan_tmp));
+    h->launches += 1;
+    k_long_compact<<<nbN, 256, 0, h->stream>>>(h->ctl, h->cnt, h->offs, N, h->long_rows);
+    CKL();
+    return RCP_OK;
+}
+
+rcp_status build(rcp_ctx* h)
+{
+    CKS(build_a(h));
+    CK(cudaStreamSynchronize(h->stream));
+    CKS(build_b(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return build_c(h);
+}
+
 // ---------------------------------------------------------------- evaluation
 unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_THREADS); }
 
@@ -410,7 +463,7 @@ unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_
 // long-row blocks).
 unsigned int launch_blocks(const rcp_ctx* h)
 {
-    if (h->cfg.precision == RCP_MIXED) return (pair_blocks(h) + RCP_LONG_BLOCKS) * (RCP_PAIR_THREADS / 32);
+    if (h->cfg.precision == RCP_MIXED) return (pair_blocks(h) + h->c.long_blocks) * (RCP_PAIR_THREADS / 32);
     return pair_blocks(h);
 }
 
@@ -452,7 +505,7 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
     const unsigned int nb = pair_blocks(h);
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->cfg.precision == RCP_MIXED) {
-        k_pair_mixed<<<nb + RCP_LONG_BLOCKS, RCP_PAIR_THREADS, 0, h->stream>>>(
+        k_pair_mixed<<<nb + h->c.long_blocks, RCP_PAIR_THREADS, 0, h->stream>>>(
             h->ctl, h->c, h->m32, h->v32, h->rA, h->rB, h->rowptr, h->col, h->long_rows, h->rb, h->part_e, h->part_k,
             mode, h->g);
     } else {
@@ -682,6 +735,14 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
     c.skin_theta = h->cfg.skin_theta;
     c.stop_margin = h->cfg.precision == RCP_MIXED ? 1e-2 : 0.0;
     c.cell_occ = h->cfg.cell_occupancy > 0.0 ? h->cfg.cell_occupancy : 1.0;
+    c.long_row = RCP_LONG_ROW;
+    {
+        // blocks serving long rows: about one per 1536 spheres, at least 2
+        long long lb = N / 1536;
+        if (lb < 2) lb = 2;
+        if (lb > RCP_LONG_BLOCKS_MAX) lb = RCP_LONG_BLOCKS_MAX;
+        c.long_blocks = (unsigned int)lb;
+    }
 
     rcp_status st = [&]() -> rcp_status {
         CK(cudaGetDevice(&h->device));
@@ -711,7 +772,8 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CKS(dalloc(h, &h->g, 3 * n));
         CKS(dalloc(h, &h->xtmp, 3 * n));
         size_t nparts = (n + RCP_TREE - 1) / RCP_TREE +
-                        ((n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS + RCP_LONG_BLOCKS) * (RCP_PAIR_THREADS / 32) + 8;
+                        ((n + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS + RCP_LONG_BLOCKS_MAX) * (RCP_PAIR_THREADS / 32) +
+                        8;
         CKS(dalloc(h, &h->part_e, nparts));
         CKS(dalloc(h, &h->part_k, nparts));
         CKS(dalloc(h, &h->part_e2, nparts));
@@ -1181,6 +1243,469 @@ rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys)
     CK(cudaMemcpyAsync(keys, h->key, sizeof(unsigned long long) * (size_t)h->N, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return RCP_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batches: many independent packings advanced by one graph of batched
+// kernels.  Each packing keeps its own handle (state, list, schedule); the
+// batched pair kernel and kappa step walk a device array of per-packing
+// descriptors, block b serving packing p with local block b - bstart[p], so
+// a packing computes exactly what its own launch would (bit-identical
+// trajectories).  Packings stop, pause and rebuild independently; rebuilds
+// of several packings run concurrently on their own streams.
+
+namespace {
+
+enum PlanResult { PLAN_RUN, PLAN_PAUSE, PLAN_STOPPED, PLAN_MAXITER, PLAN_ERROR };
+
+// Next replay of one packing from h->ctl_h (iter, kappa, stopped, status):
+// the rung logic of rcp_run.
+PlanResult plan_replay(rcp_ctx* h, long long call_start, long long call_max, long long* limit, int* final_rung)
+{
+    RcpCtl* hc = h->ctl_h;
+    if (hc->status != RCP_OK) return PLAN_ERROR;
+    if (hc->stopped) return PLAN_STOPPED;
+    if (h->rung < 0) {
+        h->rung = 0;
+        h->rung_start = hc->iter;
+        h->kappa_rung = hc->kappa;
+    }
+    long long rung_end = 0;
+    for (;;) {
+        const Rung& R = h->rungs[h->rung];
+        rung_end = R.final_rung ? h->cfg.max_iters : h->rung_start + R.budget;
+        if (rung_end > h->cfg.max_iters) rung_end = h->cfg.max_iters;
+        if (hc->iter < rung_end) break;
+        if (R.final_rung || hc->iter >= h->cfg.max_iters) return PLAN_MAXITER;
+        h->rung += 1;
+        h->rung_start = hc->iter;
+        h->kappa_rung = hc->kappa;
+    }
+    long long lim = rung_end;
+    if (call_max > 0 && call_start + call_max < lim) lim = call_start + call_max;
+    if (hc->iter >= lim) return PLAN_PAUSE;
+    rung_values(h, h->rung, h->kappa_rung);
+    *limit = lim;
+    *final_rung = h->rungs[h->rung].final_rung;
+    return PLAN_RUN;
+}
+
+PackDev pack_of(rcp_ctx* h)
+{
+    PackDev q;
+    memset(&q, 0, sizeof(q));
+    q.ctl = h->ctl;
+    q.c = h->c;
+    q.xA = h->xA;
+    q.xB = h->xB;
+    q.xb = h->xb;
+    q.m64 = h->m64;
+    q.v64 = h->v64;
+    q.m32 = h->m32;
+    q.v32 = h->v32;
+    q.rA = h->rA;
+    q.rB = h->rB;
+    q.rb = h->rb;
+    q.rowptr = h->rowptr;
+    q.col = h->col;
+    q.long_rows = h->long_rows;
+    q.part_e = h->part_e;
+    q.part_k = h->part_k;
+    q.g = h->g;
+    q.nparts = launch_blocks(h);
+    q.nblocks = pair_blocks(h) + (h->cfg.precision == RCP_MIXED ? h->c.long_blocks : 0);
+    return q;
+}
+
+}  // namespace
+
+struct rcp_batch_ctx {
+    int B = 0;
+    std::vector<rcp_ctx*> hs;
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    PackDev* d_packs = nullptr;
+    PackDev* h_packs = nullptr;
+    unsigned int* d_bstart = nullptr;
+    RungSet* d_rs = nullptr;
+    RungSet* h_rs = nullptr;
+    BatchStat* d_st = nullptr;
+    BatchStat* h_st = nullptr;
+    unsigned int total_blocks = 0;
+    size_t kappa_smem = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int gT = 0;
+    int chunk = 32;
+    int autotune = 0;
+    bool tuned = false;
+    int long_row = RCP_LONG_ROW;
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    long long launches = 0;
+    char err[512] = {0};
+};
+
+namespace {
+
+rcp_status bfail(rcp_batch_ctx* b, rcp_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b->err, sizeof(b->err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define BK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? RCP_ERR_OOM : RCP_ERR_CUDA, "%s failed: %s", #call, \
+                         cudaGetErrorString(e_));                                                  \
+    } while (0)
+
+#define BKS(h, expr)                                                   \
+    do {                                                               \
+        rcp_status s_ = (expr);                                        \
+        if (s_ != RCP_OK) return bfail(b, s_, "%s", rcp_last_error(h)); \
+    } while (0)
+
+rcp_status batch_refresh(rcp_batch_ctx* b)
+{
+    for (int p = 0; p < b->B; ++p) b->h_packs[p] = pack_of(b->hs[p]);
+    BK(cudaMemcpyAsync(b->d_packs, b->h_packs, sizeof(PackDev) * b->B, cudaMemcpyHostToDevice, b->stream));
+    return RCP_OK;
+}
+
+void batch_iteration(rcp_batch_ctx* b, int mode)
+{
+    if (b->precision == RCP_MIXED)
+        k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
+    else
+        k_pair64_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
+    k_kappa_step_batch<<<b->B, 1024, b->kappa_smem, b->stream>>>(b->d_packs, mode);
+}
+
+rcp_status batch_capture(rcp_batch_ctx* b)
+{
+    if (b->gexec && b->gT == b->chunk) return RCP_OK;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    cudaGraph_t graph;
+    BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < b->chunk; ++t) batch_iteration(b, RCP_MODE_ADAM);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess) return bfail(b, RCP_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, RCP_ERR_CUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+    b->gT = b->chunk;
+    return RCP_OK;
+}
+
+rcp_status batch_status(rcp_batch_ctx* b)
+{
+    k_batch_status<<<rcp_ceil_div(b->B, 64), 64, 0, b->stream>>>(b->d_packs, b->d_st, b->B);
+    BK(cudaPeekAtLastError());
+    BK(cudaMemcpyAsync(b->h_st, b->d_st, sizeof(BatchStat) * b->B, cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    b->launches += 1;
+    for (int p = 0; p < b->B; ++p) {
+        RcpCtl* c = b->hs[p]->ctl_h;
+        const BatchStat& s = b->h_st[p];
+        c->iter = s.iter;
+        c->rebuilds = s.rebuilds;
+        c->kappa = s.kappa;
+        c->E = s.E;
+        c->maxdelta = s.maxdelta;
+        c->pairs = s.pairs;
+        c->halted = s.halted;
+        c->stopped = s.stopped;
+        c->need_rebuild = s.need_rebuild;
+        c->status = s.status;
+        c->verify = s.verify;
+        c->parity = s.parity;
+    }
+    return RCP_OK;
+}
+
+// Rebuild the flagged packings, phases interleaved across their streams.
+rcp_status batch_build(rcp_batch_ctx* b, const std::vector<int>& which)
+{
+    if (which.empty()) return RCP_OK;
+    for (int p : which) BKS(b->hs[p], build_a(b->hs[p]));
+    for (int p : which) BK(cudaStreamSynchronize(b->hs[p]->stream));
+    for (int p : which) BKS(b->hs[p], build_b(b->hs[p]));
+    for (int p : which) BK(cudaStreamSynchronize(b->hs[p]->stream));
+    for (int p : which) {
+        rcp_ctx* h = b->hs[p];
+        BKS(h, build_c(h));
+        BK(cudaEventRecord(b->ev[p], h->stream));
+        BK(cudaStreamWaitEvent(b->stream, b->ev[p], 0));
+        b->launches += 0;
+    }
+    return batch_refresh(b);
+}
+
+// Autotuner: the long-row threshold of the mixed pair kernel, chosen by
+// timing the batched kernel in gradient mode (no state change) for each
+// candidate; then the graph chunk, chosen by timing replays.
+rcp_status batch_autotune_rows(rcp_batch_ctx* b)
+{
+    if (b->precision != RCP_MIXED) return RCP_OK;
+    const unsigned int cand[4] = {16, 32, 64, 128};
+    float best = 1e30f;
+    unsigned int pick = RCP_LONG_ROW;
+    for (unsigned int lr : cand) {
+        for (rcp_ctx* h : b->hs) {
+            h->c.long_row = lr;
+            BKS(h, relist_long(h));
+        }
+        for (rcp_ctx* h : b->hs) BK(cudaStreamSynchronize(h->stream));
+        BKS(b->hs[0], batch_refresh(b));
+        for (int w = 0; w < 2; ++w)
+            k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
+                                                                                    RCP_MODE_GRAD);
+        BK(cudaEventRecord(b->t0, b->stream));
+        for (int w = 0; w < 5; ++w)
+            k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
+                                                                                    RCP_MODE_GRAD);
+        BK(cudaEventRecord(b->t1, b->stream));
+        BK(cudaEventSynchronize(b->t1));
+        float ms = 0.f;
+        BK(cudaEventElapsedTime(&ms, b->t0, b->t1));
+        b->launches += 7;
+        if (ms < best) {
+            best = ms;
+            pick = lr;
+        }
+    }
+    for (rcp_ctx* h : b->hs) {
+        h->c.long_row = pick;
+        BKS(h, relist_long(h));
+        h->gexec ? (void)cudaGraphExecDestroy(h->gexec) : (void)0;
+        h->gexec = nullptr;  // the packing's own graph bakes its constants in
+    }
+    for (rcp_ctx* h : b->hs) BK(cudaStreamSynchronize(h->stream));
+    b->long_row = (int)pick;
+    return batch_refresh(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+rcp_status rcp_batch_create(rcp_handle* hs, int B, int autotune, rcp_batch* out)
+{
+    if (!out || !hs || B < 1) return RCP_ERR_ARG;
+    *out = nullptr;
+    rcp_batch_ctx* b = new rcp_batch_ctx();
+    b->B = B;
+    b->autotune = autotune;
+    b->precision = hs[0] ? hs[0]->cfg.precision : 0;
+    rcp_status st = [&]() -> rcp_status {
+        int dev0 = hs[0] ? hs[0]->device : 0;
+        unsigned int blocks = 0;
+        long long maxM = 1;
+        std::vector<unsigned int> bstart(B);
+        for (int p = 0; p < B; ++p) {
+            rcp_ctx* h = hs[p];
+            if (!h) return bfail(b, RCP_ERR_ARG, "handle %d is NULL", p);
+            if (h->device != dev0) return bfail(b, RCP_ERR_ARG, "handle %d lives on another device", p);
+            if (h->cfg.precision != b->precision) return bfail(b, RCP_ERR_ARG, "handles mix precisions");
+            for (int q = 0; q < p; ++q)
+                if (hs[q] == h) return bfail(b, RCP_ERR_ARG, "handle %d appears twice", p);
+            const PackDev q = pack_of(h);
+            if (q.nparts > 8192)
+                return bfail(b, RCP_ERR_CAPACITY, "packing %d has %u block partials (at most 8192 in a batch)", p,
+                             q.nparts);
+            long long M = 1;
+            while (M < (long long)q.nparts) M <<= 1;
+            if (M > maxM) maxM = M;
+            bstart[p] = blocks;
+            blocks += q.nblocks;
+            b->hs.push_back(h);
+            h->stream = h->own_stream;
+        }
+        b->total_blocks = blocks;
+        b->kappa_smem = 2 * sizeof(double) * (size_t)maxM;
+        BK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        BK(cudaMalloc(&b->d_packs, sizeof(PackDev) * B));
+        BK(cudaMallocHost(&b->h_packs, sizeof(PackDev) * B));
+        BK(cudaMalloc(&b->d_bstart, sizeof(unsigned int) * B));
+        BK(cudaMalloc(&b->d_rs, sizeof(RungSet) * B));
+        BK(cudaMallocHost(&b->h_rs, sizeof(RungSet) * B));
+        BK(cudaMalloc(&b->d_st, sizeof(BatchStat) * B));
+        BK(cudaMallocHost(&b->h_st, sizeof(BatchStat) * B));
+        BK(cudaEventCreate(&b->t0));
+        BK(cudaEventCreate(&b->t1));
+        b->ev.resize(B);
+        for (int p = 0; p < B; ++p) BK(cudaEventCreateWithFlags(&b->ev[p], cudaEventDisableTiming));
+        BK(cudaMemcpy(b->d_bstart, bstart.data(), sizeof(unsigned int) * B, cudaMemcpyHostToDevice));
+        BK(cudaFuncSetAttribute(k_kappa_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8192 * 8));
+        for (rcp_ctx* h : b->hs) BK(cudaStreamSynchronize(h->stream));
+        return batch_refresh(b);
+    }();
+    if (st != RCP_OK) {
+        // keep the message for the caller through the first handle
+        if (hs[0]) snprintf(hs[0]->err, sizeof(hs[0]->err), "%s", b->err);
+        rcp_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return RCP_OK;
+}
+
+rcp_status rcp_batch_destroy(rcp_batch b)
+{
+    if (!b) return RCP_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->d_packs) cudaFree(b->d_packs);
+    if (b->h_packs) cudaFreeHost(b->h_packs);
+    if (b->d_bstart) cudaFree(b->d_bstart);
+    if (b->d_rs) cudaFree(b->d_rs);
+    if (b->h_rs) cudaFreeHost(b->h_rs);
+    if (b->d_st) cudaFree(b->d_st);
+    if (b->h_st) cudaFreeHost(b->h_st);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return RCP_OK;
+}
+
+const char* rcp_batch_last_error(rcp_batch b) { return b ? b->err : ""; }
+
+rcp_status rcp_batch_tuning(rcp_batch b, int* long_row, int* chunk)
+{
+    if (!b) return RCP_ERR_ARG;
+    if (long_row) *long_row = b->long_row;
+    if (chunk) *chunk = b->chunk;
+    return RCP_OK;
+}
+
+rcp_status rcp_batch_run(rcp_batch b, const rcp_stop* stop, rcp_result* outs)
+{
+    if (!b) return RCP_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    rcp_stop st = {0, 0.0, 1};
+    if (stop) st = *stop;
+    const long long launches0 = b->launches;
+    if (auto s = batch_status(b)) return s;
+    std::vector<long long> call_start(b->B);
+    std::vector<long long> hl0(b->B);
+    for (int p = 0; p < b->B; ++p) {
+        call_start[p] = b->hs[p]->ctl_h->iter;
+        hl0[p] = b->hs[p]->launches;
+    }
+    std::vector<rcp_status> result(b->B, RCP_OK);
+    std::vector<int> flagged;
+    int chunk_phase = b->autotune && !b->tuned ? 0 : -1;  // chunk candidates still to time
+    const int chunks[4] = {8, 16, 32, 64};
+    float chunk_ms[4] = {0, 0, 0, 0};
+    long long chunk_it[4] = {0, 0, 0, 0};
+    for (;;) {
+        int active = 0;
+        flagged.clear();
+        bool verified = false;
+        for (int p = 0; p < b->B; ++p) {
+            rcp_ctx* h = b->hs[p];
+            RungSet& rs = b->h_rs[p];
+            rs.active = 0;
+            if (h->ctl_h->verify) {
+                bool s = false;
+                if (verify_stop_mixed(h, &s) != RCP_OK) return bfail(b, RCP_ERR_CUDA, "packing %d: %s", p, h->err);
+                verified = true;
+                continue;
+            }
+            long long limit = 0;
+            int fin = 0;
+            const PlanResult pr = plan_replay(h, call_start[p], st.max_iters, &limit, &fin);
+            if (pr == PLAN_ERROR) result[p] = (rcp_status)h->ctl_h->status;
+            if (pr == PLAN_MAXITER) result[p] = RCP_ERR_MAXITER;
+            if (pr != PLAN_RUN) continue;
+            rs.mu = h->mu;
+            rs.eta_x = h->eta_x;
+            rs.eta_k = h->eta_k;
+            rs.tol = h->cfg.tol;
+            rs.iter_limit = limit;
+            rs.final_rung = fin;
+            rs.active = 1;
+            ++active;
+            if (!h->built || h->ctl_h->need_rebuild) flagged.push_back(p);
+        }
+        if (verified) {
+            if (auto s = batch_status(b)) return s;
+            continue;
+        }
+        if (active == 0) break;
+        if (st.max_seconds > 0.0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >= st.max_seconds)
+            break;
+        if (auto s = batch_build(b, flagged)) return s;
+        if (b->autotune && !b->tuned && chunk_phase == 0) {
+            if (auto s = batch_autotune_rows(b)) return s;
+        }
+        if (chunk_phase >= 0) b->chunk = chunks[chunk_phase];
+        if (auto s = batch_capture(b)) return s;
+        BK(cudaMemcpyAsync(b->d_rs, b->h_rs, sizeof(RungSet) * b->B, cudaMemcpyHostToDevice, b->stream));
+        k_batch_set<<<rcp_ceil_div(b->B, 64), 64, 0, b->stream>>>(b->d_packs, b->d_rs, b->B);
+        BK(cudaPeekAtLastError());
+        long long it_before = 0;
+        for (int p = 0; p < b->B; ++p) it_before += b->hs[p]->ctl_h->iter;
+        BK(cudaEventRecord(b->t0, b->stream));
+        BK(cudaGraphLaunch(b->gexec, b->stream));
+        BK(cudaEventRecord(b->t1, b->stream));
+        int per_iter = 2;
+        b->launches += 1 + (long long)b->gT * per_iter;
+        if (auto s = batch_status(b)) return s;
+        if (chunk_phase >= 0) {
+            float ms = 0.f;
+            BK(cudaEventElapsedTime(&ms, b->t0, b->t1));
+            long long it_after = 0;
+            for (int p = 0; p < b->B; ++p) it_after += b->hs[p]->ctl_h->iter;
+            chunk_ms[chunk_phase] += ms;
+            chunk_it[chunk_phase] += it_after - it_before;
+            if (chunk_it[chunk_phase] >= 4LL * b->chunk * b->B || chunk_ms[chunk_phase] > 50.f) ++chunk_phase;
+            if (chunk_phase == 4) {
+                double best = 1e30;
+                int pick = 32;
+                for (int k = 0; k < 4; ++k)
+                    if (chunk_it[k] > 0 && chunk_ms[k] / chunk_it[k] < best) {
+                        best = chunk_ms[k] / chunk_it[k];
+                        pick = chunks[k];
+                    }
+                b->chunk = pick;
+                b->tuned = true;
+                chunk_phase = -1;
+            }
+        }
+    }
+    // shrink the packings that reached the criterion
+    for (int p = 0; p < b->B; ++p) {
+        rcp_ctx* h = b->hs[p];
+        if (h->ctl_h->stopped && st.shrink) {
+            if (do_shrink(h) != RCP_OK) result[p] = RCP_ERR_CUDA;
+        } else {
+            if (sync_ctl(h) != RCP_OK) result[p] = RCP_ERR_CUDA;
+        }
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    rcp_status worst = RCP_OK;
+    for (int p = 0; p < b->B; ++p) {
+        if (outs) fill_result(b->hs[p], &outs[p], secs, b->hs[p]->launches - hl0[p]);
+        if (outs) outs[p].launches = (p == 0) ? b->launches - launches0 : 0;
+        if (result[p] != RCP_OK && worst == RCP_OK) worst = result[p];
+    }
+    if (worst != RCP_OK) bfail(b, worst, "a packing ended with %s", rcp_status_str(worst));
+    return worst;
 }
 
 }  // extern "C"

@@ -473,12 +473,12 @@ __global__ void k_csr(const unsigned long long* pairs, long long P, long long N,
     }
 }
 
-// Rows longer than RCP_LONG_ROW, compacted in ascending order (flags, an
+// Rows longer than long_row, compacted in ascending order (flags, an
 // exclusive scan, then this kernel); the mixed pair kernel gives each a warp.
-__global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int* flags)
+__global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int long_row, unsigned int* flags)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) flags[i] = (rowptr[i + 1] - rowptr[i] > RCP_LONG_ROW) ? 1u : 0u;
+    if (i < N) flags[i] = (rowptr[i + 1] - rowptr[i] > long_row) ? 1u : 0u;
 }
 
 __global__ void k_long_compact(RcpCtl* ctl, const unsigned int* flags, const unsigned int* offs, long long N,

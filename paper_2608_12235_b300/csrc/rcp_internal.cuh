@@ -18,8 +18,8 @@
 #define RCP_SORT_THREADS 256
 #define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
 #define RCP_HASH_EMPTY 0xFFFFFFFFFFFFFFFFull
-#define RCP_LONG_ROW 32        // rows longer than this get a warp in the mixed pair kernel
-#define RCP_LONG_BLOCKS 592    // blocks (8 warps each) that loop over the long rows
+#define RCP_LONG_ROW 32        // default: rows longer than this get a warp in the mixed pair kernel
+#define RCP_LONG_BLOCKS_MAX 592  // most blocks (8 warps each) that loop over the long rows
 
 // Device-resident control block of one packing.  Kernels read the optimiser
 // scalars and the current rung's values from here, so one captured graph
@@ -76,6 +76,32 @@ struct RcpConst {
     double invL[3];         // 1 / L_a
     float Lf[3];            // L_a in binary32
     float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
+    unsigned int long_row;     // rows longer than this get a warp (mixed)
+    unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
+};
+
+// Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
+// 2^32) (integer subtraction wraps, which is exactly the minimum image), the
+// binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0.  One
+// 32-byte sector per gather.
+struct __align__(32) MixRec {
+    int4 q;    // qx, qy, qz, and the bits of the binary32 D_i^0 - fl32(D_i^0)
+    float4 l;  // lx, ly, lz, fl32(D_i^0)
+};
+// Everything a pair kernel and the kappa step need about one packing, for
+// the batched kernels (one device array entry per packing).
+struct PackDev {
+    RcpCtl* ctl;
+    RcpConst c;
+    double4_32a *xA, *xB, *xb;
+    double *m64, *v64;
+    float *m32, *v32;
+    MixRec *rA, *rB, *rb;
+    const unsigned int *rowptr, *col, *long_rows;
+    double *part_e, *part_k;
+    double* g;
+    unsigned int nparts;   // partial sums one pair launch writes
+    unsigned int nblocks;  // blocks of one pair launch
 };
 
 enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
@@ -102,6 +128,24 @@ __global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* 
                          double* part_e, double* part_k, int mode, double* g_out);
 __global__ void k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e, const double* part_k,
                              long long nb, int mode);
+// Per-packing rung values for a batched replay, and the status read back.
+struct RungSet {
+    double mu, eta_x, eta_k, tol;
+    long long iter_limit;
+    int final_rung;
+    int active;   // 0: the packing sits this replay out
+};
+struct BatchStat {
+    long long iter, rebuilds;
+    double kappa, E, maxdelta;
+    unsigned long long pairs;
+    int halted, stopped, need_rebuild, status, verify, parity;
+};
+__global__ void k_batch_set(const PackDev* P, const RungSet* rs, int B);
+__global__ void k_batch_status(const PackDev* P, BatchStat* out, int B);
+__global__ void k_pair64_batch(const PackDev* P, const unsigned int* bstart, int B, int mode);
+__global__ void k_kappa_step_batch(const PackDev* P, int mode);
+__global__ void k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode);
 __global__ void k_tree_pass2(const double* ina, const double* inb, long long n, double* outa, double* outb);
 __global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const double* g, const double4_32a* xb, double eta_x);
@@ -112,14 +156,6 @@ __global__ void k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const d
 __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c);
 
 // ---- mixed precision (rcp_mixed.cu) ----
-// Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
-// 2^32) (integer subtraction wraps, which is exactly the minimum image), the
-// binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0.  One
-// 32-byte sector per gather.
-struct __align__(32) MixRec {
-    int4 q;    // qx, qy, qz, and the bits of the binary32 D_i^0 - fl32(D_i^0)
-    float4 l;  // lx, ly, lz, fl32(D_i^0)
-};
 __global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                            MixRec* rA, MixRec* rB, MixRec* rb);
 __global__ void k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB,
@@ -158,7 +194,7 @@ __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const d
                          unsigned long long* pairs, unsigned long long cap, int nbits);
 __global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits,
                       unsigned int* rowptr, unsigned int* col);
-__global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int* flags);
+__global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int long_row, unsigned int* flags);
 __global__ void k_long_compact(RcpCtl* ctl, const unsigned int* flags, const unsigned int* offs, long long N,
                                unsigned int* long_rows);
 __global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, double4_32a* xb,

@@ -164,6 +164,49 @@ __global__ void k_set_rung(RcpCtl* ctl, double mu, double eta_x, double eta_k, d
 
 __global__ void k_clear_halt(RcpCtl* ctl) { ctl->halted = 0; }
 
+// Rung values of every packing of a batch before a replay (thread p = packing p).
+__global__ void k_batch_set(const PackDev* P, const RungSet* rs, int B)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= B) return;
+    RcpCtl* ctl = P[p].ctl;
+    const RungSet r = rs[p];
+    if (!r.active) {
+        ctl->halted = 1;
+        return;
+    }
+    ctl->mu = r.mu;
+    ctl->eta_x = r.eta_x;
+    ctl->eta_k = r.eta_k;
+    ctl->tol = r.tol;
+    ctl->iter_limit = r.iter_limit;
+    ctl->final_rung = r.final_rung;
+    ctl->halted = ctl->iter >= r.iter_limit ? 1 : 0;
+    ctl->verify = 0;
+}
+
+// The fields the batch driver needs from every packing, in one array.
+__global__ void k_batch_status(const PackDev* P, BatchStat* out, int B)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= B) return;
+    const RcpCtl* c = P[p].ctl;
+    BatchStat s;
+    s.iter = c->iter;
+    s.rebuilds = c->rebuilds;
+    s.kappa = c->kappa;
+    s.E = c->E;
+    s.maxdelta = c->maxdelta;
+    s.pairs = c->pairs;
+    s.halted = c->halted;
+    s.stopped = c->stopped;
+    s.need_rebuild = c->need_rebuild;
+    s.status = c->status;
+    s.verify = c->verify;
+    s.parity = c->parity;
+    out[p] = s;
+}
+
 // Caller positions [N][3] -> (x, y, z, D0) records, wrapped into the box.
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x)
 {
@@ -255,10 +298,10 @@ __device__ __forceinline__ bool skin_exhausted(RcpCtl* ctl, double kappa_new)
 // buffer (rows still gather the current one), plus the skin check; in grad
 // mode g_i is written out.  e_i and k_i are summed per block by the
 // canonical tree; maxd by an atomic max (order-free).
-__global__ void __launch_bounds__(RCP_PAIR_THREADS)
-k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
-         const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
-         double* part_e, double* part_k, int mode, double* g_out)
+__device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, double4_32a* xA, double4_32a* xB,
+                                            double* m, double* v, const unsigned int* rowptr, const unsigned int* col,
+                                            const double4_32a* xb, double* part_e, double* part_k, int mode,
+                                            double* g_out, unsigned int blk)
 {
     __shared__ double sh[RCP_PAIR_THREADS / 32];
     if (ctl->halted) return;
@@ -266,7 +309,7 @@ k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, d
     const double4_32a* __restrict__ xin = parity ? xB : xA;
     double4_32a* __restrict__ xout = parity ? xA : xB;
     const double kappa = ctl->kappa;
-    const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
+    const long long i = (long long)blk * RCP_PAIR_THREADS + threadIdx.x;
     double e = 0.0, k = 0.0, md = 0.0;
     float bud = INFINITY;
     if (i < c.N) {
@@ -321,10 +364,42 @@ k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, d
     double sk = block_tree<RCP_PAIR_THREADS>(k, sh);
     double bm = block_max(md, sh);
     if (threadIdx.x == 0) {
-        part_e[blockIdx.x] = se;
-        part_k[blockIdx.x] = sk;
+        part_e[blk] = se;
+        part_k[blk] = sk;
         if (bm > 0.0) atomicMax(&ctl->maxdelta_bits, dbits(bm));
     }
+}
+
+__global__ void __launch_bounds__(RCP_PAIR_THREADS)
+k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+         const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
+         double* part_e, double* part_k, int mode, double* g_out)
+{
+    pair64_body(ctl, c, xA, xB, m, v, rowptr, col, xb, part_e, part_k, mode, g_out, blockIdx.x);
+}
+
+// Packing of a block in a batched launch: the last p with bstart[p] <= block.
+__device__ __forceinline__ int batch_pack(const unsigned int* bstart, int B, unsigned int block)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bstart[mid] <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched binary64 pair kernel: block b serves packing p = batch_pack(b)
+// with local block b - bstart[p], so each packing computes exactly what its
+// own launch would.
+__global__ void __launch_bounds__(RCP_PAIR_THREADS) k_pair64_batch(const PackDev* P, const unsigned int* bstart,
+                                                                   int B, int mode)
+{
+    const int p = batch_pack(bstart, B, blockIdx.x);
+    const PackDev& q = P[p];
+    pair64_body(q.ctl, q.c, q.xA, q.xB, q.m64, q.v64, q.rowptr, q.col, q.xb, q.part_e, q.part_k, mode, q.g,
+                blockIdx.x - bstart[p]);
 }
 
 // Close an iteration: Adam step of kappa with dE/dkappa of the evaluation,
@@ -357,10 +432,9 @@ __device__ void kappa_adam_tail(RcpCtl* ctl, const RcpConst& c)
 // In Adam mode: the stopping test of App. A on the state just evaluated (the
 // final rung stops when max delta < tol, before that state's Adam step),
 // otherwise the Adam step of kappa, the buffer swap, and the rebuild test.
-__global__ void __launch_bounds__(1024) k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e,
-                                                     const double* part_k, long long nb, int mode)
+__device__ __forceinline__ void kappa_step_body(RcpCtl* ctl, const RcpConst& c, const double* part_e,
+                                                const double* part_k, long long nb, int mode, double* buf)
 {
-    extern __shared__ double buf[];
     if (ctl->halted) return;
     long long M = 1;
     while (M < nb) M <<= 1;
@@ -409,6 +483,21 @@ __global__ void __launch_bounds__(1024) k_kappa_step(RcpCtl* ctl, RcpConst c, co
         }
     }
     kappa_adam_tail(ctl, c);
+}
+
+__global__ void __launch_bounds__(1024) k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e,
+                                                     const double* part_k, long long nb, int mode)
+{
+    extern __shared__ double buf[];
+    kappa_step_body(ctl, c, part_e, part_k, nb, mode, buf);
+}
+
+// Batched kappa step: block p closes the iteration of packing p.
+__global__ void __launch_bounds__(1024) k_kappa_step_batch(const PackDev* P, int mode)
+{
+    extern __shared__ double buf[];
+    const PackDev& q = P[blockIdx.x];
+    kappa_step_body(q.ctl, q.c, q.part_e, q.part_k, q.nparts, mode, buf);
 }
 
 // Binary64 verdict on a binary32 stop candidate: stop on the evaluated state,

@@ -336,10 +336,10 @@ __device__ __forceinline__ float warp_sum2f(float s, float c)
 #ifndef RCP_MIX_MINB
 #define RCP_MIX_MINB 4   // resident blocks per SM the register budget is sized for
 #endif
-__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
-k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB, const unsigned int* rowptr,
-             const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
-             double* part_k, int mode, double* g_out)
+__device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, float* m, float* v, MixRec* rA,
+                                                MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
+                                                const unsigned int* long_rows, const MixRec* rb, double* part_e,
+                                                double* part_k, int mode, double* g_out, unsigned int blk)
 {
     __shared__ MixScalars S;
     if (ctl->halted) return;
@@ -351,10 +351,10 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
     float bud = INFINITY;
-    if (blockIdx.x < RCP_LONG_BLOCKS) {
+    if (blk < c.long_blocks) {
         const unsigned int nlong = ctl->n_long;
-        const unsigned int nw = RCP_LONG_BLOCKS * (RCP_PAIR_THREADS / 32);
-        for (unsigned int r = blockIdx.x * (RCP_PAIR_THREADS / 32) + warp; r < nlong; r += nw) {
+        const unsigned int nw = c.long_blocks * (RCP_PAIR_THREADS / 32);
+        for (unsigned int r = blk * (RCP_PAIR_THREADS / 32) + warp; r < nlong; r += nw) {
             const long long i = long_rows[r];
             const MixRec ri = rin[i];
             PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -379,10 +379,10 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
             if (lane == 0) bud = fminf(bud, row_epilogue(ctl, c, S, i, ri, g0, g1, g2, m, v, rout, rb, mode, g_out));
         }
     } else {
-        const long long i = (long long)(blockIdx.x - RCP_LONG_BLOCKS) * RCP_PAIR_THREADS + threadIdx.x;
+        const long long i = (long long)(blk - c.long_blocks) * RCP_PAIR_THREADS + threadIdx.x;
         if (i < c.N) {
             const unsigned int t0 = rowptr[i], t1 = rowptr[i + 1];
-            if (t1 - t0 <= RCP_LONG_ROW) {
+            if (t1 - t0 <= c.long_row) {
                 const MixRec ri = rin[i];
                 PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 unsigned int t = t0;
@@ -408,7 +408,7 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
     float wm = md;
     for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_down_sync(0xffffffffu, wm, o));
     if (lane == 0) {
-        const unsigned long long w = (unsigned long long)blockIdx.x * (RCP_PAIR_THREADS / 32) + warp;
+        const unsigned long long w = (unsigned long long)blk * (RCP_PAIR_THREADS / 32) + warp;
         part_e[w] = (double)es + (double)ec;
         part_k[w] = (double)ks + (double)kc;
         if (wm > 0.f) {
@@ -416,6 +416,36 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
             if (b > *(volatile unsigned long long*)&ctl->maxdelta_bits) atomicMax(&ctl->maxdelta_bits, b);
         }
     }
+}
+
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB, const unsigned int* rowptr,
+             const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
+             double* part_k, int mode, double* g_out)
+{
+    pair_mixed_body(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out, blockIdx.x);
+}
+
+__device__ __forceinline__ int batch_pack_m(const unsigned int* bstart, int B, unsigned int block)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bstart[mid] <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched mixed pair kernel: block b serves packing p with local block
+// b - bstart[p], so each packing computes exactly what its own launch would.
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode)
+{
+    const int p = batch_pack_m(bstart, B, blockIdx.x);
+    const PackDev& q = P[p];
+    pair_mixed_body(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e, q.part_k,
+                    mode, q.g, blockIdx.x - bstart[p]);
 }
 
 // Binary64 maximum overlap over the listed pairs of the current binary64

@@ -24,7 +24,8 @@ STATUS = {0: "RCP_OK", 1: "RCP_ERR_ARG", 2: "RCP_ERR_IMAGE", 3: "RCP_ERR_OOM", 4
 EXPORTS = ["rcp_config_default", "rcp_create", "rcp_destroy", "rcp_set_stream", "rcp_set_positions",
            "rcp_build_neighbors", "rcp_energy_grad", "rcp_energy_grad_at", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
            "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_status_str", "rcp_last_error",
-           "rcp_energy_grad_noalloc"]
+           "rcp_energy_grad_noalloc", "rcp_batch_create", "rcp_batch_run", "rcp_batch_tuning", "rcp_batch_destroy",
+           "rcp_batch_last_error"]
 
 
 class rcp_config(C.Structure):
@@ -90,6 +91,12 @@ def load(path: str | None = None) -> C.CDLL:
     L.rcp_cell_keys.argtypes = [vp, vp]
     L.rcp_energy_grad_noalloc.argtypes = [vp, vp, C.c_longlong, vp, C.c_double, C.c_double, C.c_double,
                                           vp, vp, vp, vp, vp, vp, vp]
+    L.rcp_batch_create.argtypes = [vp, ip, ip, C.POINTER(vp)]
+    L.rcp_batch_run.argtypes = [vp, C.POINTER(rcp_stop), vp]
+    L.rcp_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rcp_batch_destroy.argtypes = [vp]
+    L.rcp_batch_last_error.argtypes = [vp]
+    L.rcp_batch_last_error.restype = C.c_char_p
     L.rcp_size.argtypes = [vp]
     L.rcp_size.restype = C.c_longlong
     L.rcp_status_str.argtypes = [ip]
@@ -97,7 +104,7 @@ def load(path: str | None = None) -> C.CDLL:
     L.rcp_last_error.argtypes = [vp]
     L.rcp_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("rcp_size", "rcp_status_str", "rcp_last_error"):
+        if name not in ("rcp_size", "rcp_status_str", "rcp_last_error", "rcp_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -322,3 +329,44 @@ class Packing:
 
     def adam_step(self, g, dEdk, lr_x, lr_kappa):
         rcp_adam_step(self.h, g, dEdk, lr_x, lr_kappa)
+
+
+# ----------------------------------------------------------------- batches
+class Batch:
+    """Independent packings advanced together by one graph of batched kernels
+    (rcp_batch_*).  The packings keep ownership of their state."""
+
+    def __init__(self, packings, autotune: bool = False):
+        self.packings = list(packings)
+        arr = (C.c_void_p * len(self.packings))(*[p.h.value for p in self.packings])
+        b = C.c_void_p()
+        st = load().rcp_batch_create(arr, len(self.packings), int(autotune), C.byref(b))
+        if st != 0:
+            raise RcpError(st, load().rcp_last_error(self.packings[0].h).decode())
+        self.b = b
+
+    def run(self, max_iters=0, max_seconds=0.0, shrink=True):
+        n = len(self.packings)
+        outs = (rcp_result * n)()
+        st = rcp_stop(max_iters, max_seconds, int(shrink))
+        code = load().rcp_batch_run(self.b, C.byref(st), outs)
+        if code != 0:
+            raise RcpError(code, load().rcp_batch_last_error(self.b).decode())
+        return [RunSummary(r.iters, r.rebuilds, r.pairs, bool(r.stopped), r.kappa, r.max_delta, r.energy,
+                           r.kappa_c, r.phi, r.seconds, r.launches) for r in outs]
+
+    def tuning(self):
+        a, c = C.c_int(), C.c_int()
+        _check(load().rcp_batch_tuning(self.b, C.byref(a), C.byref(c)))
+        return a.value, c.value
+
+    def close(self):
+        if self.b:
+            load().rcp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
