@@ -387,7 +387,7 @@ rcp_status search_once(rcp_ctx* h)
     const int nbits = bits_for((unsigned long long)N);
     CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
     h->launches += 1;
-    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xf, h->xsf,
+    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xsf,
                                          h->hkeys, h->hvals, h->hcap - 1, h->pairs1, h->pcap, nbits);
     CKL();
     CK(cudaMemcpyAsync(&h->ctl_h->pair_cursor, &h->ctl->pair_cursor, sizeof(unsigned long long),
@@ -735,6 +735,7 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
     c.skin_theta = h->cfg.skin_theta;
     c.stop_margin = h->cfg.precision == RCP_MIXED ? 1e-2 : 0.0;
     c.cell_occ = h->cfg.cell_occupancy > 0.0 ? h->cfg.cell_occupancy : 1.0;
+    c.canon = h->cfg.precision == RCP_FP64 ? 1u : 0u;
     c.long_row = RCP_LONG_ROW;
     {
         // blocks serving long rows: about one per 1536 spheres, at least 2
@@ -899,7 +900,7 @@ rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x, d
     CKS(ensure_list(h));
     // evaluation mode: mu from the argument, no iteration limit involved
     h->launches += 1;
-    k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, mu, 0.0, 0.0, h->cfg.tol, 1LL << 62, 0);
+    k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, h->c, mu, 0.0, 0.0, h->cfg.tol, 1LL << 62, 0);
     CKL();
     h->launches += launch_iteration(h, RCP_MODE_GRAD);
     CKL();
@@ -1056,7 +1057,7 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
         if (!h->built || hc->need_rebuild) CKS(build(h));
         if (!prof) CKS(capture_graph(h));
         h->launches += 1;
-        k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, h->mu, h->eta_x, h->eta_k, h->cfg.tol, limit, R.final_rung);
+        k_set_rung<<<1, 1, 0, h->stream>>>(h->ctl, h->c, h->mu, h->eta_x, h->eta_k, h->cfg.tol, limit, R.final_rung);
         CKL();
         if (prof) {
             h->launches += launch_iteration(h, RCP_MODE_ADAM, prof->ev);

@@ -323,7 +323,8 @@ __device__ __forceinline__ bool hfind(const unsigned long long* hkeys, const uin
 }
 
 // ---------------------------------------------------------------------------
-// Pair search, one pass.  Each thread keeps the entries it finds in a small
+// Pair search, one pass.  Threads take the spheres in cell-key order.  Each
+// thread keeps the entries it finds in a small
 // local buffer; a full buffer is flushed to the global array through one
 // atomic reservation, and the final flush is aggregated over the warp.  The
 // order of entries in the array is arbitrary (they are radix-sorted next);
@@ -357,15 +358,18 @@ __device__ __forceinline__ float wrap_unit(float d)
 // binary64 one.
 __global__ void __launch_bounds__(256)
 k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
-         const unsigned int* idx_sorted, const float4* xf, const float4* xsf, const unsigned long long* hkeys,
+         const unsigned int* idx_sorted, const float4* xsf, const unsigned long long* hkeys,
          const uint2* hvals, unsigned long long hmask, unsigned long long* pairs, unsigned long long cap, int nbits)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // threads take the spheres in cell-key order (size class, then cell), so
+    // a warp shares its size class, its trip counts and most of its cells
+    const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long buf[RCP_SEARCH_BUF];
     int nb = 0;
-    if (i < c.N) {
+    if (ts < c.N) {
+        const long long i = idx_sorted[ts];
         const double4_32a* x = ctl->parity ? xB : xA;
-        const float4 ui = xf[i];
+        const float4 ui = xsf[ts];
         const double ri = rho[i];
         const int li = lvl[i];
         const float L0 = c.Lf[0], L1 = c.Lf[1], L2 = c.Lf[2];
@@ -501,5 +505,6 @@ __global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, cons
         ctl->kbud_bits = RCP_KBUD_INF;
         ctl->rebuilds += 1;
         ctl->pairs = P;
+        if (!c.canon) mix_fill(ctl, c);   // kappa_b and sigma0 changed
     }
 }

@@ -24,6 +24,15 @@
 // Device-resident control block of one packing.  Kernels read the optimiser
 // scalars and the current rung's values from here, so one captured graph
 // serves every rung and both buffer parities.
+// Binary32 scalars of one mixed-precision iteration, derived from the
+// binary64 control values by mix_fill whenever those change (three binary64
+// divisions: far too slow to repeat in every block of the pair kernel).
+struct MixScalars {
+    float kappa, kappa_lo, rkappa, eps, rh1, rh2, be1, be2, o1, o2, eta, aeps;
+    float limA, limB;  // theta sigma_i (1 - 1e-5) = limA D_i + limB
+};
+#define RCP_MIX_SRC 6  // binary64 values the scalars derive from: kappa, b1, b2, eta_x, kappa_b, sigma0
+
 struct RcpCtl {
     // written by the host (through k_set_rung) before a replay
     double mu, eta_x, eta_k, tol;
@@ -58,6 +67,9 @@ struct RcpCtl {
     unsigned long long shrink_bits;
     unsigned long long md64_bits;
     double kappa_c, phi;
+    // binary32 scalars of the next mixed iteration and the values they came from
+    MixScalars mix;
+    double mix_src[RCP_MIX_SRC];
 };
 
 // Kernel parameters that never change during a run.
@@ -76,6 +88,7 @@ struct RcpConst {
     double invL[3];         // 1 / L_a
     float Lf[3];            // L_a in binary32
     float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
+    unsigned int canon;        // 1: binary64 path (canonical sums); 0: mixed path
     unsigned int long_row;     // rows longer than this get a warp (mixed)
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
 };
@@ -111,6 +124,49 @@ enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
+// The binary32 scalars of an iteration from the control block (binary64).
+__device__ __forceinline__ void mix_scalars(const RcpCtl* ctl, const RcpConst& c, MixScalars& s)
+{
+    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+    s.kappa = (float)ctl->kappa;
+    s.kappa_lo = (float)(ctl->kappa - (double)s.kappa);
+    s.rkappa = (float)(1.0 / ctl->kappa);
+    s.eps = (float)c.eps;
+    s.rh1 = (float)(1.0 / (1.0 - b1));
+    s.rh2 = (float)(1.0 / (1.0 - b2));
+    s.be1 = (float)c.beta1;
+    s.be2 = (float)c.beta2;
+    s.o1 = (float)(1.0 - c.beta1);
+    s.o2 = (float)(1.0 - c.beta2);
+    s.eta = (float)ctl->eta_x;
+    s.aeps = (float)c.adam_eps;
+    const double mth = c.skin_theta * (1.0 - 1e-5);
+    s.limA = (float)(mth * c.skin_s * ctl->kappa_b);
+    s.limB = (float)(mth * ctl->sigma0);
+}
+
+__device__ __forceinline__ double mix_src_value(const RcpCtl* ctl, int k)
+{
+    switch (k) {
+    case 0: return ctl->kappa;
+    case 1: return ctl->b1;
+    case 2: return ctl->b2;
+    case 3: return ctl->eta_x;
+    case 4: return ctl->kappa_b;
+    default: return ctl->sigma0;
+    }
+}
+
+// Store the scalars of the next iteration in the control block (one thread;
+// called by every kernel that changes one of the source values).
+__device__ __forceinline__ void mix_fill(RcpCtl* ctl, const RcpConst& c)
+{
+    MixScalars s;
+    mix_scalars(ctl, c, s);
+    ctl->mix = s;
+    for (int k = 0; k < RCP_MIX_SRC; ++k) ctl->mix_src[k] = mix_src_value(ctl, k);
+}
+
 static inline unsigned int rcp_ceil_div(unsigned long long a, unsigned long long b) { return (unsigned int)((a + b - 1) / b); }
 
 // ---- kernels (rcp_kernels.cu) ----
@@ -118,7 +174,7 @@ __global__ void k_init_positions(unsigned long long seed, long long N, RcpConst 
 __global__ void k_tree_terms(const double* D0, long long N, int power, double* out);
 __global__ void k_tree_pass(const double* in, long long n, double* out);
 __global__ void k_kappa0(RcpCtl* ctl, double phi0, double V);
-__global__ void k_set_rung(RcpCtl* ctl, double mu, double eta_x, double eta_k, double tol,
+__global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, double eta_k, double tol,
                            long long iter_limit, int final_rung);
 __global__ void k_clear_halt(RcpCtl* ctl);
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x);
@@ -166,6 +222,7 @@ __global__ void k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, con
 __global__ void k_verify_final(RcpCtl* ctl, RcpConst c);
 __global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, MixRec* rA, MixRec* rB, float* m, float* v, const double* g,
                              const MixRec* rb, double eta_x);
+__global__ void k_mix_refresh(RcpCtl* ctl, RcpConst c);
 __global__ void k_from_fixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const double* D0,
                              double4_32a* xA, double4_32a* xB);
 __global__ void k_snap_records(RcpCtl* ctl, long long N, const MixRec* rA, const MixRec* rB, MixRec* rb);
@@ -189,7 +246,7 @@ __global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* o
 __global__ void k_hash_heads(const unsigned long long* keys, long long n, unsigned long long* hkeys,
                              uint2* hvals, unsigned long long hmask);
 __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
-                         const int* lvl, const unsigned int* idx_sorted, const float4* xf, const float4* xsf,
+                         const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
                          const unsigned long long* hkeys, const uint2* hvals, unsigned long long hmask,
                          unsigned long long* pairs, unsigned long long cap, int nbits);
 __global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits,

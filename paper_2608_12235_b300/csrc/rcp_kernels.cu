@@ -149,7 +149,7 @@ __global__ void k_kappa0(RcpCtl* ctl, double phi0, double V)
     ctl->kappa = y;
 }
 
-__global__ void k_set_rung(RcpCtl* ctl, double mu, double eta_x, double eta_k, double tol,
+__global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, double eta_k, double tol,
                            long long iter_limit, int final_rung)
 {
     ctl->mu = mu;
@@ -160,6 +160,7 @@ __global__ void k_set_rung(RcpCtl* ctl, double mu, double eta_x, double eta_k, d
     ctl->final_rung = final_rung;
     ctl->halted = ctl->iter >= iter_limit ? 1 : 0;
     ctl->verify = 0;
+    if (!c.canon) mix_fill(ctl, c);
 }
 
 __global__ void k_clear_halt(RcpCtl* ctl) { ctl->halted = 0; }
@@ -183,6 +184,7 @@ __global__ void k_batch_set(const PackDev* P, const RungSet* rs, int B)
     ctl->final_rung = r.final_rung;
     ctl->halted = ctl->iter >= r.iter_limit ? 1 : 0;
     ctl->verify = 0;
+    mix_fill(ctl, P[p].c);
 }
 
 // The fields the batch driver needs from every packing, in one array.
@@ -423,6 +425,7 @@ __device__ void kappa_adam_tail(RcpCtl* ctl, const RcpConst& c)
         ctl->need_rebuild = 1;
         ctl->halted = 1;
     }
+    if (!c.canon) mix_fill(ctl, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -557,6 +560,7 @@ __global__ void k_adam_kappa(RcpCtl* ctl, RcpConst c, double dEdk, double eta_k)
     ctl->b2 = b2;
     ctl->iter += 1;
     if (skin_exhausted(ctl, kn)) ctl->need_rebuild = 1;
+    if (!c.canon) mix_fill(ctl, c);
 }
 
 // Skin check of the current state against the last build (after positions or

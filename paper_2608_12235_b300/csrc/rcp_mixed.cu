@@ -105,30 +105,20 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c)
     }
 }
 
-// Per-block scalars, derived once per block from the control block.
-struct MixScalars {
-    float kappa, kappa_lo, rkappa, eps, rh1, rh2, be1, be2, o1, o2, eta, aeps;
-    float limA, limB;  // theta sigma_i (1 - 1e-5) = limA D_i + limB
-};
+__global__ void k_mix_refresh(RcpCtl* ctl, RcpConst c) { mix_fill(ctl, c); }
 
-__device__ __forceinline__ void mix_scalars(const RcpCtl* ctl, const RcpConst& c, MixScalars& s)
+// A warp's private copy of the scalars: lanes copy the stored binary32 words;
+// if a source value changed since they were stored (a path that did not
+// refresh them), the warp derives them itself.  Same values either way.
+__device__ __forceinline__ void mix_load_warp(const RcpCtl* ctl, const RcpConst& c, MixScalars& S, int lane)
 {
-    const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
-    s.kappa = (float)ctl->kappa;
-    s.kappa_lo = (float)(ctl->kappa - (double)s.kappa);
-    s.rkappa = (float)(1.0 / ctl->kappa);
-    s.eps = (float)c.eps;
-    s.rh1 = (float)(1.0 / (1.0 - b1));
-    s.rh2 = (float)(1.0 / (1.0 - b2));
-    s.be1 = (float)c.beta1;
-    s.be2 = (float)c.beta2;
-    s.o1 = (float)(1.0 - c.beta1);
-    s.o2 = (float)(1.0 - c.beta2);
-    s.eta = (float)ctl->eta_x;
-    s.aeps = (float)c.adam_eps;
-    const double mth = c.skin_theta * (1.0 - 1e-5);
-    s.limA = (float)(mth * c.skin_s * ctl->kappa_b);
-    s.limB = (float)(mth * ctl->sigma0);
+    const bool stale = lane < RCP_MIX_SRC && mix_src_value(ctl, lane) != ctl->mix_src[lane];
+    if (__any_sync(0xffffffffu, stale)) {
+        if (lane == 0) mix_scalars(ctl, c, S);
+    } else if (lane < (int)(sizeof(MixScalars) / sizeof(float))) {
+        reinterpret_cast<float*>(&S)[lane] = reinterpret_cast<const float*>(&ctl->mix)[lane];
+    }
+    __syncwarp();
 }
 
 // Adam on one axis of a record: binary32 moments, step added to the
@@ -341,14 +331,14 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                                                 const unsigned int* long_rows, const MixRec* rb, double* part_e,
                                                 double* part_k, int mode, double* g_out, unsigned int blk)
 {
-    __shared__ MixScalars S;
+    __shared__ MixScalars Sw[RCP_PAIR_THREADS / 32];
     if (ctl->halted) return;
-    if (threadIdx.x == 0) mix_scalars(ctl, c, S);
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    MixScalars& S = Sw[warp];
+    mix_load_warp(ctl, c, S, lane);
     const int parity = ctl->parity;
     const MixRec* __restrict__ rin = parity ? rB : rA;
     MixRec* __restrict__ rout = parity ? rA : rB;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
     float bud = INFINITY;
     if (blk < c.long_blocks) {

@@ -48,9 +48,12 @@ def test_initial_positions_and_kappa0_bitexact(rcp, orc, n):
 # ------------------------------------------------------------------ integer work
 @pytest.mark.parametrize("n,sig,S,phi", [(1000, 0.5, 10.0, 0.05), (4097, 1.0, 100.0, 0.4),
                                          (3000, 2.0, 5e4, 0.2), (777, 0.2, 3.0, 0.6)])
-def test_cell_keys_and_list_bitexact(rcp, orc, n, sig, S, phi):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cell_keys_and_list_bitexact(rcp, orc, n, sig, S, phi, precision):
+    # the list does not depend on the precision of the pair arithmetic
     D0 = inputs.lognormal(n, sig, S)
-    p = _mk(rcp, D0, seed=n)
+    prec = rcp.RCP_FP64 if precision == "fp64" else rcp.RCP_MIXED
+    p = _mk(rcp, D0, seed=n, precision=prec)
     x = orc.init_positions(n, n)
     k = orc.kappa0(D0, 1.0, phi)
     p.set_positions(x, k)
