@@ -75,9 +75,8 @@ struct rcp_ctx {
     unsigned int* idx2 = nullptr;
     unsigned int* idx0 = nullptr;
     const unsigned int* idx_sorted = nullptr;
-    unsigned long long* hkeys = nullptr;
-    uint2* hvals = nullptr;
-    unsigned long long hcap = 0;
+    uint2* cells = nullptr;             // dense cell table of all size classes
+    unsigned long long cells_cap = 0;
     unsigned int* cnt = nullptr;   // [N+1]
     unsigned int* offs = nullptr;  // [N+1]
     unsigned long long* pairs1 = nullptr;
@@ -373,9 +372,14 @@ rcp_status build_b(rcp_ctx* h)
     h->idx_sorted = sidx;
     h->launches += 1;
     k_gather_sorted<<<nbN, 256, 0, h->stream>>>(N, h->idx_sorted, h->xf, h->xsf);
-    CK(cudaMemsetAsync(h->hkeys, 0xFF, sizeof(unsigned long long) * h->hcap, h->stream));
+    const unsigned long long ncells = h->ctl_h->cell_off[RCP_KMAX];
+    if (ncells > h->cells_cap) {
+        CKS(dalloc(h, &h->cells, ncells));
+        h->cells_cap = ncells;
+    }
+    CK(cudaMemsetAsync(h->cells, 0, sizeof(uint2) * ncells, h->stream));
     h->launches += 1;
-    k_hash_heads<<<nbN, 256, 0, h->stream>>>(skeys, N, h->hkeys, h->hvals, h->hcap - 1);
+    k_cell_ranges<<<nbN, 256, 0, h->stream>>>(h->ctl, skeys, N, h->cells);
     CKL();
     return search_once(h);
 }
@@ -388,7 +392,7 @@ rcp_status search_once(rcp_ctx* h)
     CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
     h->launches += 1;
     k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xsf,
-                                         h->hkeys, h->hvals, h->hcap - 1, h->pairs1, h->pcap, nbits);
+                                         h->cells, h->pairs1, h->pcap, nbits);
     CKL();
     CK(cudaMemcpyAsync(&h->ctl_h->pair_cursor, &h->ctl->pair_cursor, sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, h->stream));
@@ -671,7 +675,7 @@ rcp_status rcp_destroy(rcp_handle h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
-                    h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->hkeys, h->hvals, h->cnt,
+                    h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->cells, h->cnt,
                     h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->hist, h->scan_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -791,10 +795,6 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CKS(dalloc(h, &h->idx0, n));
         CKS(dalloc(h, &h->idx1, n));
         CKS(dalloc(h, &h->idx2, n));
-        h->hcap = 64;
-        while (h->hcap < 2 * (unsigned long long)n) h->hcap <<= 1;
-        CKS(dalloc(h, &h->hkeys, h->hcap));
-        CKS(dalloc(h, &h->hvals, h->hcap));
         CKS(dalloc(h, &h->cnt, n + 1));
         CKS(dalloc(h, &h->offs, n + 1));
         CKS(dalloc(h, &h->rowptr, n + 1));

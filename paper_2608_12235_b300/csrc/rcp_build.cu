@@ -125,6 +125,13 @@ __global__ void k_grid(RcpCtl* ctl, RcpConst c)
         if (r > 0.0) nlev = k + 1;
     }
     ctl->nlev = nlev;
+    unsigned long long off = 0;
+    for (int k = 0; k <= RCP_KMAX; ++k) {
+        ctl->cell_off[k] = off;
+        if (k < nlev && ctl->rho_lvl[k] > 0.0)
+            off += (unsigned long long)ctl->ng[k][0] * (unsigned long long)ctl->ng[k][1] *
+                   (unsigned long long)ctl->ng[k][2];
+    }
     const double rmax = bitsd(ctl->rho_max_bits);
     if (!(4.0 * rmax < c.Lmin)) {
         ctl->status = RCP_ERR_IMAGE;
@@ -275,18 +282,19 @@ __global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* o
 }
 
 // ---------------------------------------------------------------------------
-// Open-addressing hash of occupied cells: key -> [start, end) in the sorted
-// order.  Linear probing; the table has at least twice as many slots as
-// spheres, so an empty slot always ends a probe sequence.
-__device__ __forceinline__ unsigned long long hmix(unsigned long long z)
+// Dense cell table: for every cell of every size class, the range [x, y) of
+// its spheres in the sorted order (empty cells stay (0, 0)).  A class with
+// count spheres has at most count / cell_occupancy cells (k_grid), so the
+// table holds at most N / cell_occupancy entries; class k starts at
+// ctl->cell_off[k] and is laid out (z, y, x) row-major.
+__device__ __forceinline__ unsigned long long cell_index(const RcpCtl* ctl, unsigned int k, unsigned int cz,
+                                                         unsigned int cy, unsigned int cx)
 {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
+    return ctl->cell_off[k] +
+           ((unsigned long long)cz * (unsigned int)ctl->ng[k][1] + cy) * (unsigned int)ctl->ng[k][0] + cx;
 }
 
-__global__ void k_hash_heads(const unsigned long long* keys, long long n, unsigned long long* hkeys, uint2* hvals,
-                             unsigned long long hmask)
+__global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys, long long n, uint2* cells)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -294,32 +302,11 @@ __global__ void k_hash_heads(const unsigned long long* keys, long long n, unsign
     const bool head = (t == 0) || keys[t - 1] != key;
     const bool tail = (t == n - 1) || keys[t + 1] != key;
     if (!head && !tail) return;
-    unsigned long long s = hmix(key) & hmask;
-    for (unsigned long long probe = 0; probe <= hmask; ++probe) {
-        unsigned long long prev = atomicCAS(&hkeys[s], RCP_HASH_EMPTY, key);
-        if (prev == RCP_HASH_EMPTY || prev == key) {
-            if (head) hvals[s].x = (unsigned int)t;
-            if (tail) hvals[s].y = (unsigned int)(t + 1);
-            return;
-        }
-        s = (s + 1) & hmask;
-    }
-}
-
-__device__ __forceinline__ bool hfind(const unsigned long long* hkeys, const uint2* hvals, unsigned long long hmask,
-                                      unsigned long long key, uint2& out)
-{
-    unsigned long long s = hmix(key) & hmask;
-    for (unsigned long long probe = 0; probe <= hmask; ++probe) {
-        const unsigned long long k = hkeys[s];
-        if (k == key) {
-            out = hvals[s];
-            return true;
-        }
-        if (k == RCP_HASH_EMPTY) return false;
-        s = (s + 1) & hmask;
-    }
-    return false;
+    const unsigned long long m = (1ull << 19) - 1ull;
+    const unsigned long long ci = cell_index(ctl, (unsigned int)(key >> 57), (unsigned int)((key >> 38) & m),
+                                             (unsigned int)((key >> 19) & m), (unsigned int)(key & m));
+    if (head) cells[ci].x = (unsigned int)t;
+    if (tail) cells[ci].y = (unsigned int)(t + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,8 +345,8 @@ __device__ __forceinline__ float wrap_unit(float d)
 // binary64 one.
 __global__ void __launch_bounds__(256)
 k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
-         const unsigned int* idx_sorted, const float4* xsf, const unsigned long long* hkeys,
-         const uint2* hvals, unsigned long long hmask, unsigned long long* pairs, unsigned long long cap, int nbits)
+         const unsigned int* idx_sorted, const float4* xsf, const uint2* cells, unsigned long long* pairs,
+         unsigned long long cap, int nbits)
 {
     // threads take the spheres in cell-key order (size class, then cell), so
     // a warp shares its size class, its trip counts and most of its cells
@@ -397,14 +384,15 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
                     nc[a] = (unsigned int)(h - l + 1);
                 }
             }
+            const uint2* ck = cells + ctl->cell_off[k];
             for (unsigned int cz = 0; cz < nc[2]; ++cz) {
                 const unsigned int z = (unsigned int)(lo[2] + (int)cz) & (ng[2] - 1);
                 for (unsigned int cy = 0; cy < nc[1]; ++cy) {
                     const unsigned int y = (unsigned int)(lo[1] + (int)cy) & (ng[1] - 1);
+                    const uint2* row = ck + ((unsigned long long)z * ng[1] + y) * ng[0];
                     for (unsigned int cx = 0; cx < nc[0]; ++cx) {
                         const unsigned int xx = (unsigned int)(lo[0] + (int)cx) & (ng[0] - 1);
-                        uint2 range;
-                        if (!hfind(hkeys, hvals, hmask, pack_key((unsigned int)k, z, y, xx), range)) continue;
+                        const uint2 range = row[xx];
                         for (unsigned int t = range.x; t < range.y; ++t) {
                             const float4 uj = xsf[t];
                             const float dx = wrap_unit(ui.x - uj.x) * L0;

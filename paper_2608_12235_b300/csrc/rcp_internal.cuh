@@ -17,7 +17,6 @@
 #define RCP_TREE 1024          // elements per block of a tree-reduction pass
 #define RCP_SORT_THREADS 256
 #define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
-#define RCP_HASH_EMPTY 0xFFFFFFFFFFFFFFFFull
 #define RCP_LONG_ROW 32        // default: rows longer than this get a warp in the mixed pair kernel
 #define RCP_LONG_BLOCKS_MAX 592  // most blocks (8 warps each) that loop over the long rows
 
@@ -59,6 +58,7 @@ struct RcpCtl {
     double rho_lvl[RCP_KMAX];
     int nlev;
     int ng[RCP_KMAX][3];
+    unsigned long long cell_off[RCP_KMAX + 1];  // first entry of each class in the dense cell table
     long long rebuilds;
     unsigned long long pairs;
     unsigned int n_long;      // rows longer than RCP_LONG_ROW
@@ -243,11 +243,10 @@ __global__ void k_radix_scatter(const unsigned long long* keys, const unsigned i
                                 unsigned long long* okeys, unsigned int* ovals);
 __global__ void k_scan_block(const unsigned int* in, long long n, unsigned int* out, unsigned int* totals);
 __global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* offs);
-__global__ void k_hash_heads(const unsigned long long* keys, long long n, unsigned long long* hkeys,
-                             uint2* hvals, unsigned long long hmask);
+__global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys, long long n, uint2* cells);
 __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
                          const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
-                         const unsigned long long* hkeys, const uint2* hvals, unsigned long long hmask,
+                         const uint2* cells,
                          unsigned long long* pairs, unsigned long long cap, int nbits);
 __global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits,
                       unsigned int* rowptr, unsigned int* col);
