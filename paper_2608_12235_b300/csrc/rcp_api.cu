@@ -331,7 +331,7 @@ rcp_status build_a(rcp_ctx* h)
     h->launches += 1;
     k_level<<<nbN, 256, 0, h->stream>>>(h->ctl, N, h->rho, h->lvl);
     h->launches += 1;
-    k_grid<<<1, 1, 0, h->stream>>>(h->ctl, h->c);
+    k_grid<<<1, 128, 0, h->stream>>>(h->ctl, h->c);
     CKL();
     CK(cudaMemcpyAsync(h->ctl_h, h->ctl, sizeof(RcpCtl), cudaMemcpyDeviceToHost, h->stream));
     return RCP_OK;

@@ -83,10 +83,22 @@ __global__ void __launch_bounds__(256) k_level(RcpCtl* ctl, long long N, const d
     __syncthreads();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
-        const double rmax = bitsd(ctl->rho_max_bits);
+        const unsigned long long bm = ctl->rho_max_bits;
         const double r = rho[i];
-        int k = 0;
-        while (k + 1 < RCP_KMAX && ldexp(r, k + 1) <= rmax) ++k;
+        const unsigned long long br = dbits(r);
+        const int er = (int)(br >> 52), em = (int)(bm >> 52);   // biased exponents (r, rho_max > 0)
+        int k;
+        if (er > 0) {
+            // r 2^k <= rho_max  <=>  (er + k, fraction of r) <= (em, fraction of rho_max)
+            const unsigned long long fmask = (1ull << 52) - 1ull;
+            k = em - er - ((br & fmask) > (bm & fmask) ? 1 : 0);
+            k = k < 0 ? 0 : (k > RCP_KMAX - 1 ? RCP_KMAX - 1 : k);
+        } else {
+            // subnormal radius: the plain search over k
+            const double rmax = bitsd(bm);
+            k = 0;
+            while (k + 1 < RCP_KMAX && ldexp(r, k + 1) <= rmax) ++k;
+        }
         lvl[i] = k;
         atomicMax(&smax[k], dbits(r));
         atomicAdd(&scnt[k], 1u);
@@ -106,24 +118,28 @@ __global__ void __launch_bounds__(256) k_level(RcpCtl* ctl, long long N, const d
 // be closer than half a box edge, i.e. 4 rho_max < min L.
 __global__ void k_grid(RcpCtl* ctl, RcpConst c)
 {
-    int nlev = 0;
-    for (int k = 0; k < RCP_KMAX; ++k) {
-        double r = bitsd(ctl->rho_lvl_bits[k]);
+    // one thread per (class, axis)
+    const int t = threadIdx.x;
+    if (t < RCP_KMAX * 3) {
+        const int k = t / 3, a = t % 3;
+        const double r = bitsd(ctl->rho_lvl_bits[k]);
         const double cnt = (double)ctl->lvl_count[k];
-        ctl->rho_lvl[k] = r;
-        for (int a = 0; a < 3; ++a) {
-            unsigned int n = 1;
-            if (r > 0.0)
-                for (;;) {
-                    if (n >= RCP_NMAX_AXIS) break;
-                    const double h = c.L[a] / (double)(2 * n);
-                    if (!(((h * h) * h) * cnt >= c.cell_occ * c.V)) break;
-                    n *= 2;
-                }
-            ctl->ng[k][a] = (int)n;
-        }
-        if (r > 0.0) nlev = k + 1;
+        if (a == 0) ctl->rho_lvl[k] = r;
+        unsigned int n = 1;
+        if (r > 0.0)
+            for (;;) {
+                if (n >= RCP_NMAX_AXIS) break;
+                const double h = c.L[a] / (double)(2 * n);
+                if (!(((h * h) * h) * cnt >= c.cell_occ * c.V)) break;
+                n *= 2;
+            }
+        ctl->ng[k][a] = (int)n;
     }
+    __syncthreads();
+    if (t != 0) return;
+    int nlev = 0;
+    for (int k = 0; k < RCP_KMAX; ++k)
+        if (ctl->rho_lvl[k] > 0.0) nlev = k + 1;
     ctl->nlev = nlev;
     unsigned long long off = 0;
     for (int k = 0; k <= RCP_KMAX; ++k) {

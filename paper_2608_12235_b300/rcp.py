@@ -226,6 +226,17 @@ def rcp_state(h):
     return x, m, v, s
 
 
+def rcp_positions(h, out=None):
+    """Current positions only ([N, 3] binary64), written into `out` when given
+    (e.g. a page-locked array, for a direct device-to-host copy)."""
+    n = load().rcp_size(h)
+    x = np.zeros((n, 3)) if out is None else out
+    if x.shape != (n, 3) or x.dtype != np.float64 or not x.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array of shape (N, 3)")
+    _check(load().rcp_state(h, x.ctypes.data, None, None, None), h)
+    return x
+
+
 def rcp_load_state(h, x, m, v, s: rcp_scalars):
     x, m, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, m, v))
     _check(load().rcp_load_state(h, x.ctypes.data, m.ctypes.data, v.ctypes.data, C.byref(s)), h)
@@ -312,8 +323,8 @@ class Packing:
     def state(self):
         return rcp_state(self.h)
 
-    def positions(self):
-        return rcp_state(self.h)[0]
+    def positions(self, out=None):
+        return rcp_positions(self.h, out)
 
     def neighbors(self):
         return rcp_neighbors(self.h)
