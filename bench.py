@@ -52,6 +52,29 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def pair_traffic(args, Pn):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, when
+    that summary was taken on this workload and on the kernel source as it is
+    now (sha256 prefix of rcp_mixed.cu), else None."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_pair_mixed-lognormal-n1e6-s5e5.md")) as f:
+            text = f.read()
+        with open(os.path.join(ROOT, "paper_2608_12235_b300", "csrc", "rcp_mixed.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        want = re.search(r"sha256 prefix `([0-9a-f]+)`", text).group(1)
+        traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+        pairs = int(re.search(r"traffic_pairs: (\d+)", text).group(1))
+    except Exception:
+        return None, None
+    same_state = (args.workload == "lognormal-n1e6-s5e5" and args.skin_abs == 100.0
+                  and args.densify + (args.warmup + args.steps) * args.iters_per_step == 8300)
+    if not sha.startswith(want) or not same_state:
+        return None, None
+    return float(traffic), pairs
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
@@ -301,6 +324,7 @@ def main():
     bytes_per_launch = 148.0 * w["N"] + 4.0 * Pn
     gbs = bytes_per_launch / (ms_pair / nl / 1e3) / 1e9
     peak, peak_kind = peaks()
+    traffic, traffic_pairs = pair_traffic(args, Pn)
 
     # ---- binary64 at the same state
     q = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_FP64, skin_abs=args.skin_abs)
@@ -359,7 +383,8 @@ def main():
             "fp64": {"value": value64, "unit": "iters/s", "speedup_mixed_over_fp64": value / value64},
             "rebuilds_in_timed_region": rebuilds - (rebuild0 or 0), "listed_pairs": Pn,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "peak_kind": peak_kind, "traffic": None, "kernel": "k_pair_mixed",
+                         "peak_kind": peak_kind, "traffic": traffic, "traffic_pairs": traffic_pairs,
+                         "kernel": "k_pair_mixed",
                          "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_pair / nl},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_rate, "unit": "iters/s", "h2d_bytes_per_step": 24 * w["N"],
