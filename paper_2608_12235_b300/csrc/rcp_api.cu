@@ -7,6 +7,7 @@
 // the host from device-reduced sums, in the same binary64 expressions as the
 // definition (compiled with -ffp-contract=off); every per-particle and
 // per-pair operation runs in the kernels.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -75,6 +76,14 @@ struct rcp_ctx {
     unsigned int* idx2 = nullptr;
     unsigned int* idx0 = nullptr;
     const unsigned int* idx_sorted = nullptr;
+    const unsigned long long* skeys = nullptr;  // sorted cell keys of the last build
+    // mixed path: the state is kept in cell-key order; perm[i] is the caller's
+    // index of internal sphere i (NULL in binary64 mode: caller order)
+    unsigned int* perm = nullptr;
+    unsigned int* perm_alt = nullptr;
+    double* D0_alt = nullptr;
+    double* rho_alt = nullptr;
+    int* lvl_alt = nullptr;
     uint2* cells = nullptr;             // dense cell table of all size classes
     unsigned long long cells_cap = 0;
     unsigned int* cnt = nullptr;   // [N+1]
@@ -177,6 +186,20 @@ rcp_status materialize(rcp_ctx* h)
     h->launches += 1;
     k_from_fixed<<<rcp_ceil_div(h->N, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->D0, h->xA, h->xB);
     CK(cudaPeekAtLastError());
+    return RCP_OK;
+}
+
+// The caller's index of every internal sphere, to the host (identity in
+// binary64 mode).
+rcp_status copy_perm(rcp_ctx* h, unsigned int* out)
+{
+    const size_t n = (size_t)h->N;
+    if (!h->perm) {
+        for (size_t i = 0; i < n; ++i) out[i] = (unsigned int)i;
+        return RCP_OK;
+    }
+    CK(cudaMemcpyAsync(out, h->perm, sizeof(unsigned int) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return RCP_OK;
 }
 
@@ -370,8 +393,28 @@ rcp_status build_b(rcp_ctx* h)
     CKS(radix_sort(h, h->key, h->idx0, (unsigned long long)N, shifts, h->key1, h->idx1, h->key2, h->idx2, &skeys,
                    &sidx));
     h->idx_sorted = sidx;
+    h->skeys = skeys;
     h->launches += 1;
     k_gather_sorted<<<nbN, 256, 0, h->stream>>>(N, h->idx_sorted, h->xf, h->xsf);
+    if (h->perm) {
+        // mixed path: move the state into cell-key order (moments through the
+        // gradient buffer, which holds nothing between evaluations)
+        float* m2 = reinterpret_cast<float*>(h->g);
+        float* v2 = m2 + 3 * (size_t)N;
+        h->launches += 2;
+        k_permute_state<<<nbN, 256, 0, h->stream>>>(h->ctl, N, sidx, h->rA, h->rB, h->xA, h->xB, h->m32, h->v32, m2,
+                                                    v2, h->D0, h->D0_alt, h->rho, h->rho_alt, h->lvl, h->lvl_alt,
+                                                    h->perm, h->perm_alt);
+        k_flip_parity<<<1, 1, 0, h->stream>>>(h->ctl);
+        CKL();
+        CK(cudaMemcpyAsync(h->m32, m2, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->v32, v2, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToDevice, h->stream));
+        std::swap(h->D0, h->D0_alt);
+        std::swap(h->rho, h->rho_alt);
+        std::swap(h->lvl, h->lvl_alt);
+        std::swap(h->perm, h->perm_alt);
+        h->idx_sorted = nullptr;   // sphere t is now the t-th in key order
+    }
     const unsigned long long ncells = h->ctl_h->cell_off[RCP_KMAX];
     if (ncells > h->cells_cap) {
         CKS(dalloc(h, &h->cells, ncells));
@@ -676,7 +719,8 @@ rcp_status rcp_destroy(rcp_handle h)
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
                     h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->cells, h->cnt,
-                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->hist, h->scan_tmp};
+                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->hist, h->scan_tmp, h->perm, h->perm_alt, h->D0_alt, h->rho_alt,
+                    h->lvl_alt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->ctl_h) cudaFreeHost(h->ctl_h);
@@ -766,6 +810,12 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
             CKS(dalloc(h, &h->rA, n));
             CKS(dalloc(h, &h->rB, n));
             CKS(dalloc(h, &h->rb, n));
+            CKS(dalloc(h, &h->perm, n));
+            CKS(dalloc(h, &h->perm_alt, n));
+            CKS(dalloc(h, &h->D0_alt, n));
+            CKS(dalloc(h, &h->rho_alt, n));
+            CKS(dalloc(h, &h->lvl_alt, n));
+            k_iota<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>((long long)n, h->perm);
             CK(cudaMemsetAsync(h->m32, 0, sizeof(float) * 3 * n, h->stream));
             CK(cudaMemsetAsync(h->v32, 0, sizeof(float) * 3 * n, h->stream));
         } else {
@@ -868,7 +918,7 @@ rcp_status rcp_set_positions(rcp_handle h, const double* x, double kappa, int on
     CKS(sync_ctl(h));
     double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
     h->launches += 1;
-    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur);
+    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur, h->perm);
     CKL();
     if (kappa > 0.0) CK(cudaMemcpyAsync(&h->ctl->kappa, &kappa, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     if (h->cfg.precision == RCP_MIXED) {
@@ -905,14 +955,22 @@ rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x, d
     h->launches += launch_iteration(h, RCP_MODE_GRAD);
     CKL();
     const size_t n = (size_t)h->N;
+    const double* gsrc = h->g;
+    if (h->perm && grad_x) {
+        // internal order -> the caller's
+        h->launches += 1;
+        k_perm3<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->perm, h->g, h->xtmp, 1);
+        CKL();
+        gsrc = h->xtmp;
+    }
     if (on_device) {
-        if (grad_x) CK(cudaMemcpyAsync(grad_x, h->g, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
+        if (grad_x) CK(cudaMemcpyAsync(grad_x, gsrc, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
         if (E) CK(cudaMemcpyAsync(E, &h->ctl->E, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         if (dE_dkappa) CK(cudaMemcpyAsync(dE_dkappa, &h->ctl->dEdk, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         if (max_delta) CK(cudaMemcpyAsync(max_delta, &h->ctl->maxdelta, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         return RCP_OK;
     }
-    if (grad_x) CK(cudaMemcpyAsync(grad_x, h->g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    if (grad_x) CK(cudaMemcpyAsync(grad_x, gsrc, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
     CKS(sync_ctl(h));
     if (h->ctl_h->status == RCP_ERR_NAN) return fail(h, RCP_ERR_NAN, "non-finite energy or gradient");
     if (E) *E = h->ctl_h->E;
@@ -931,7 +989,7 @@ rcp_status rcp_energy_grad_at(rcp_handle h, const double* x_dev, const double* k
     CKS(sync_ctl(h));  // parity and build state
     double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
     h->launches += 1;
-    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur);
+    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur, h->perm);
     CKL();
     if (h->cfg.precision == RCP_MIXED) {
         h->launches += 1;
@@ -951,12 +1009,20 @@ rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, d
 {
     if (!h || !grad_x) return RCP_ERR_ARG;
     const size_t n = (size_t)h->N;
+    if (!h->built) CKS(build(h));   // before the copy: a build uses h->g as scratch
     CK(cudaMemcpyAsync(h->g, grad_x, sizeof(double) * 3 * n,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
-    if (!h->built) CKS(build(h));
+    const double* gin = h->g;
+    if (h->perm) {
+        // the caller's order -> internal
+        h->launches += 1;
+        k_perm3<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->perm, h->g, h->xtmp, 0);
+        CKL();
+        gin = h->xtmp;
+    }
     h->launches += 1;
     if (h->cfg.precision == RCP_MIXED)
-        k_adam_mixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->m32, h->v32, h->g,
+        k_adam_mixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->m32, h->v32, gin,
                                                                   h->rb, lr_x);
     else
         k_adam64<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->g,
@@ -1143,21 +1209,25 @@ rcp_status rcp_state(rcp_handle h, double* x, double* m, double* v, rcp_scalars*
         CKS(materialize(h));
         const double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
         h->launches += 1;
-        k_get_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, cur, h->xtmp);
+        k_get_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, cur, h->xtmp, h->perm);
         CKL();
         CK(cudaMemcpyAsync(x, h->xtmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
     }
     if (h->cfg.precision == RCP_MIXED) {
         std::vector<float> tmp(m || v ? 3 * n : 0);
+        std::vector<unsigned int> pm(m || v ? n : 0);
+        if (m || v) CKS(copy_perm(h, pm.data()));
         if (m) {
             CK(cudaMemcpyAsync(tmp.data(), h->m32, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
-            for (size_t i = 0; i < 3 * n; ++i) m[i] = tmp[i];
+            for (size_t i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) m[3 * (size_t)pm[i] + a] = tmp[3 * i + a];
         }
         if (v) {
             CK(cudaMemcpyAsync(tmp.data(), h->v32, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
-            for (size_t i = 0; i < 3 * n; ++i) v[i] = tmp[i];
+            for (size_t i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) v[3 * (size_t)pm[i] + a] = tmp[3 * i + a];
         }
     } else {
         if (m) CK(cudaMemcpyAsync(m, h->m64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
@@ -1187,13 +1257,19 @@ rcp_status rcp_load_state(rcp_handle h, const double* x, const double* m, const 
     if (x) CKS(rcp_set_positions(h, x, s ? s->kappa : 0.0, 0));
     if (h->cfg.precision == RCP_MIXED) {
         std::vector<float> tmp(3 * n);
+        std::vector<unsigned int> pm(m || v ? n : 0);
+        if (m || v) CKS(copy_perm(h, pm.data()));
         if (m) {
-            for (size_t i = 0; i < 3 * n; ++i) tmp[i] = (float)m[i];
-            CK(cudaMemcpy(h->m32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+            for (size_t i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) tmp[3 * i + a] = (float)m[3 * (size_t)pm[i] + a];
+            CK(cudaMemcpyAsync(h->m32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
         }
         if (v) {
-            for (size_t i = 0; i < 3 * n; ++i) tmp[i] = (float)v[i];
-            CK(cudaMemcpy(h->v32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+            for (size_t i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) tmp[3 * i + a] = (float)v[3 * (size_t)pm[i] + a];
+            CK(cudaMemcpyAsync(h->v32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
         }
     } else {
         if (m) CK(cudaMemcpyAsync(h->m64, m, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
@@ -1228,11 +1304,35 @@ rcp_status rcp_neighbors(rcp_handle h, long long* rowptr, int* col, long long ca
     std::vector<unsigned int> rp(n + 1);
     CK(cudaMemcpyAsync(rp.data(), h->rowptr, sizeof(unsigned int) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    for (size_t i = 0; i <= n; ++i) rowptr[i] = rp[i];
     *P = (long long)h->P;
-    if (col && (long long)h->P <= cap) {
-        CK(cudaMemcpyAsync(col, h->col, sizeof(unsigned int) * h->P, cudaMemcpyDeviceToHost, h->stream));
+    const bool want_col = col && (long long)h->P <= cap;
+    if (!h->perm) {
+        for (size_t i = 0; i <= n; ++i) rowptr[i] = rp[i];
+        if (want_col) {
+            CK(cudaMemcpyAsync(col, h->col, sizeof(unsigned int) * h->P, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        }
+        return RCP_OK;
+    }
+    // mixed path: rows and columns are internal indices; return the list in
+    // the caller's order, columns ascending per row
+    std::vector<unsigned int> pm(n), inv(n), cs(want_col ? h->P : 0);
+    CKS(copy_perm(h, pm.data()));
+    if (want_col) {
+        CK(cudaMemcpyAsync(cs.data(), h->col, sizeof(unsigned int) * h->P, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+    }
+    for (size_t i = 0; i < n; ++i) inv[pm[i]] = (unsigned int)i;
+    rowptr[0] = 0;
+    for (size_t u = 0; u < n; ++u) {
+        const size_t r = inv[u];
+        const unsigned int len = rp[r + 1] - rp[r];
+        if (want_col) {
+            int* out = col + rowptr[u];
+            for (unsigned int t = 0; t < len; ++t) out[t] = (int)pm[cs[rp[r] + t]];
+            std::sort(out, out + len);
+        }
+        rowptr[u + 1] = rowptr[u] + len;
     }
     return RCP_OK;
 }
@@ -1241,8 +1341,18 @@ rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys)
 {
     if (!h || !keys) return RCP_ERR_ARG;
     if (!h->built) CKS(build(h));
-    CK(cudaMemcpyAsync(keys, h->key, sizeof(unsigned long long) * (size_t)h->N, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    const size_t n = (size_t)h->N;
+    if (!h->perm) {
+        CK(cudaMemcpyAsync(keys, h->key, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return RCP_OK;
+    }
+    // mixed path: internal sphere t holds the t-th sorted key
+    std::vector<unsigned long long> sk(n);
+    std::vector<unsigned int> pm(n);
+    CK(cudaMemcpyAsync(sk.data(), h->skeys, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, h->stream));
+    CKS(copy_perm(h, pm.data()));
+    for (size_t t = 0; t < n; ++t) keys[pm[t]] = sk[t];
     return RCP_OK;
 }
 

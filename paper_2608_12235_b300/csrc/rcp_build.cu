@@ -61,6 +61,41 @@ __global__ void __launch_bounds__(256) k_rho(RcpCtl* ctl, RcpConst c, const doub
     }
 }
 
+// Mixed path: the per-sphere state in cell-key order (sphere t of the new
+// order is sphere sorted[t] of the old), so that the rows a warp evaluates
+// lie in neighbouring cells of one size class and their partners sit close
+// together in memory.  Records and the binary64 view of the current parity go
+// to the other buffers (k_flip_parity then makes them current); moments,
+// diameters, radii, classes and the caller-order map go to the scratch arrays.
+__global__ void k_permute_state(const RcpCtl* ctl, long long N, const unsigned int* sorted, MixRec* rA, MixRec* rB,
+                                double4_32a* xA, double4_32a* xB, const float* m, const float* v, float* m2,
+                                float* v2, const double* D0, double* D02, const double* rho, double* rho2,
+                                const int* lvl, int* lvl2, const unsigned int* perm, unsigned int* perm2)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int parity = ctl->parity;
+    const long long s = sorted[t];
+    (parity ? rA : rB)[t] = (parity ? rB : rA)[s];
+    (parity ? xA : xB)[t] = (parity ? xB : xA)[s];
+    for (int a = 0; a < 3; ++a) {
+        m2[3 * t + a] = m[3 * s + a];
+        v2[3 * t + a] = v[3 * s + a];
+    }
+    D02[t] = D0[s];
+    rho2[t] = rho[s];
+    lvl2[t] = lvl[s];
+    perm2[t] = perm[s];
+}
+
+__global__ void k_flip_parity(RcpCtl* ctl) { ctl->parity ^= 1; }
+
+__global__ void k_iota(long long N, unsigned int* out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) out[t] = (unsigned int)t;
+}
+
 // The binary32 copies in cell order, so the candidates of one cell are
 // contiguous.
 __global__ void k_gather_sorted(long long N, const unsigned int* idx_sorted, const float4* xf, float4* xsf)
@@ -365,12 +400,13 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
          unsigned long long cap, int nbits)
 {
     // threads take the spheres in cell-key order (size class, then cell), so
-    // a warp shares its size class, its trip counts and most of its cells
+    // a warp shares its size class, its trip counts and most of its cells;
+    // idx_sorted is NULL when the state itself is in that order
     const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long buf[RCP_SEARCH_BUF];
     int nb = 0;
     if (ts < c.N) {
-        const long long i = idx_sorted[ts];
+        const long long i = idx_sorted ? (long long)idx_sorted[ts] : ts;
         const double4_32a* x = ctl->parity ? xB : xA;
         const float4 ui = xsf[ts];
         const double ri = rho[i];
@@ -418,7 +454,7 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
                             const float cut = ui.w + uj.w;
                             const float hi = (cut * up + Eabs) * up;
                             if (r2 > hi * hi) continue;                    // certainly not listed
-                            const unsigned int j = idx_sorted[t];
+                            const unsigned int j = idx_sorted ? idx_sorted[t] : t;
                             if ((long long)j == i) continue;
                             const float lo_in = (cut * dn - Eabs) * dn;
                             bool in = lo_in > 0.0f && r2 < lo_in * lo_in;   // certainly listed

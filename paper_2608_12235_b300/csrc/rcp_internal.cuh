@@ -177,8 +177,10 @@ __global__ void k_kappa0(RcpCtl* ctl, double phi0, double V);
 __global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, double eta_k, double tol,
                            long long iter_limit, int final_rung);
 __global__ void k_clear_halt(RcpCtl* ctl);
-__global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x);
-__global__ void k_get_positions(long long N, const double4_32a* x, double* out);
+__global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
+                                const unsigned int* perm);
+__global__ void k_get_positions(long long N, const double4_32a* x, double* out, const unsigned int* perm);
+__global__ void k_perm3(long long N, const unsigned int* perm, const double* in, double* out, int to_caller);
 __global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
                          double* part_e, double* part_k, int mode, double* g_out);
@@ -243,6 +245,12 @@ __global__ void k_radix_scatter(const unsigned long long* keys, const unsigned i
                                 unsigned long long* okeys, unsigned int* ovals);
 __global__ void k_scan_block(const unsigned int* in, long long n, unsigned int* out, unsigned int* totals);
 __global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* offs);
+__global__ void k_permute_state(const RcpCtl* ctl, long long N, const unsigned int* sorted, MixRec* rA, MixRec* rB,
+                                double4_32a* xA, double4_32a* xB, const float* m, const float* v, float* m2,
+                                float* v2, const double* D0, double* D02, const double* rho, double* rho2,
+                                const int* lvl, int* lvl2, const unsigned int* perm, unsigned int* perm2);
+__global__ void k_flip_parity(RcpCtl* ctl);
+__global__ void k_iota(long long N, unsigned int* out);
 __global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys, long long n, uint2* cells);
 __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
                          const int* lvl, const unsigned int* idx_sorted, const float4* xsf,

@@ -210,27 +210,45 @@ __global__ void k_batch_status(const PackDev* P, BatchStat* out, int B)
 }
 
 // Caller positions [N][3] -> (x, y, z, D0) records, wrapped into the box.
-__global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x)
+// Positions from a caller's [N][3] array (sphere order of the caller; perm,
+// when not NULL, gives the caller's index of each internal sphere).
+__global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
+                                const unsigned int* perm)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const long long u = perm ? (long long)perm[i] : i;
     double p[3];
     for (int a = 0; a < 3; ++a) {
-        double v = xin[3 * i + a];
+        double v = xin[3 * u + a];
         if (v < 0.0 || v >= c.L[a]) v = v - c.L[a] * floor(v / c.L[a]);
         p[a] = wrap_step(v, c.L[a]);
     }
     x[i] = make_double4_32a(p[0], p[1], p[2], D0[i]);
 }
 
-__global__ void k_get_positions(long long N, const double4_32a* x, double* out)
+__global__ void k_get_positions(long long N, const double4_32a* x, double* out, const unsigned int* perm)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const long long u = perm ? (long long)perm[i] : i;
     double4_32a p = x[i];
-    out[3 * i + 0] = p.x;
-    out[3 * i + 1] = p.y;
-    out[3 * i + 2] = p.z;
+    out[3 * u + 0] = p.x;
+    out[3 * u + 1] = p.y;
+    out[3 * u + 2] = p.z;
+}
+
+// [N][3] vectors between the caller's order and the internal one:
+// to_caller: out[perm[i]] = in[i]; otherwise out[i] = in[perm[i]].
+__global__ void k_perm3(long long N, const unsigned int* perm, const double* in, double* out, int to_caller)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long u = perm[i];
+    const long long s = to_caller ? i : u, d = to_caller ? u : i;
+    out[3 * d + 0] = in[3 * s + 0];
+    out[3 * d + 1] = in[3 * s + 1];
+    out[3 * d + 2] = in[3 * s + 2];
 }
 
 // ---------------------------------------------------------------------------

@@ -207,6 +207,39 @@ def test_energy_grad_mixed_within_tolerance(rcp, orc):
         p.close()
 
 
+def test_mixed_state_follows_the_caller_order(rcp, orc):
+    """The mixed path keeps its spheres in cell-key order inside the library
+    (rebuilt at every neighbour build): positions, moments and a caller's
+    gradient must still come and go in the caller's sphere order."""
+    D0, x, k = _states(orc)[0]
+    p = _mk(rcp, D0, precision=rcp.RCP_MIXED)
+    p.set_positions(x, k)
+    rcp.rcp_build_neighbors(p.h)  # reorders the internal state
+    assert np.allclose(p.positions(), x, rtol=0.0, atol=1e-15)
+    rng = np.random.default_rng(0)
+    xo, mo, vo = x.ravel().copy(), np.zeros(x.size), np.zeros(x.size)
+    b1 = b2 = 1.0
+    for _ in range(3):
+        g = rng.standard_normal(x.shape)
+        p.adam_step(g, 0.0, 1e-3, 0.0)
+        b1 *= 0.9
+        b2 *= 0.999
+        orc.adam_update(xo, mo, vo, g, 1e-3, b1, b2)
+        xo = np.array([orc.wrap(a, 1.0) for a in xo])
+        rcp.rcp_build_neighbors(p.h)  # and again, from the moved state
+    xs, ms, vs, s = p.state()
+    d = np.abs(xs.ravel() - xo)
+    d = np.minimum(d, 1.0 - d)  # a coordinate may sit across the periodic wrap
+    assert d.max() <= 1e-9
+    assert np.allclose(ms.ravel(), mo, rtol=1e-6, atol=1e-12)
+    assert np.allclose(vs.ravel(), vo, rtol=1e-6, atol=1e-15)
+    rcp.rcp_load_state(p.h, xs, ms, vs, s)
+    x2, m2, v2, _ = p.state()
+    assert np.array_equal(m2, ms) and np.array_equal(v2, vs)
+    assert np.allclose(x2, xs, rtol=0.0, atol=1e-15)
+    p.close()
+
+
 def test_energy_grad_mixed_near_contact(rcp, orc):
     """Small overlaps (delta ~ 1e-3, a relaxed packing inflated by 0.2 %): the
     regime where a plain binary32 d - r would cancel."""
