@@ -231,8 +231,9 @@ def test_mixed_state_follows_the_caller_order(rcp, orc):
     d = np.abs(xs.ravel() - xo)
     d = np.minimum(d, 1.0 - d)  # a coordinate may sit across the periodic wrap
     assert d.max() <= 1e-9
-    assert np.allclose(ms.ravel(), mo, rtol=1e-6, atol=1e-12)
-    assert np.allclose(vs.ravel(), vo, rtol=1e-6, atol=1e-15)
+    # binary32 moments: absolute error a few ulp of the moment's scale
+    assert np.allclose(ms.ravel(), mo, rtol=1e-5, atol=1e-7)
+    assert np.allclose(vs.ravel(), vo, rtol=1e-5, atol=1e-10)
     rcp.rcp_load_state(p.h, xs, ms, vs, s)
     x2, m2, v2, _ = p.state()
     assert np.array_equal(m2, ms) and np.array_equal(v2, vs)
