@@ -52,17 +52,28 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def library_sha():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2608_12235_b300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def pair_traffic(args, Pn):
     """DRAM bytes per pair-kernel launch from the committed ncu summary, when
-    that summary was taken on this workload and on the kernel source as it is
-    now (sha256 prefix of rcp_mixed.cu), else None."""
+    that summary was taken on this workload and on the library source as it
+    is now (sha256 prefix over csrc/*.cu and csrc/*.cuh in name order; the
+    data layout the kernel sees comes from the build kernels too), else None."""
     import hashlib
     import re
     try:
         with open(os.path.join(ROOT, "profiles", "k_pair_mixed-lognormal-n1e6-s5e5.md")) as f:
             text = f.read()
-        with open(os.path.join(ROOT, "paper_2608_12235_b300", "csrc", "rcp_mixed.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = library_sha()
         want = re.search(r"sha256 prefix `([0-9a-f]+)`", text).group(1)
         traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
         pairs = int(re.search(r"traffic_pairs: (\d+)", text).group(1))

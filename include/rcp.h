@@ -86,6 +86,13 @@ typedef struct {
     double    cell_occupancy; /* spheres per cell each size class's grid aims at:
                                  cells are the smallest power-of-two grid with at
                                  least this many per cell on average (1) */
+    int       placement;    /* initial positions: 0 uniform in the box (default);
+                               1 without overlap at phi0 (App. A: the particles are
+                               placed without overlap at low volume fraction): rounds
+                               of random sequential addition, larger spheres first,
+                               round 0 being the uniform draw */
+    int       place_rounds; /* most placement rounds before rcp_create gives up
+                               with RCP_ERR_CAPACITY (10000) */
 } rcp_config;
 
 /* When rcp_run returns early. */

@@ -63,6 +63,9 @@ def lib():
         L.orc_splitmix64_at.restype = C.c_uint64
         L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_init_positions.argtypes = [C.c_uint64, C.c_long, C.c_int, _dp, _dp]
+        L.orc_place.argtypes = [C.c_uint64, C.c_long, C.c_int, _dp, _dp, C.c_double, C.c_int, _dp,
+                                np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")]
+        L.orc_place.restype = C.c_int
         L.orc_tree_sum.restype = C.c_double
         L.orc_tree_sum.argtypes = [_dp, C.c_long]
         L.orc_cbrt.restype = C.c_double
@@ -136,6 +139,17 @@ def init_positions(seed: int, n: int, L=1.0, d: int = 3) -> np.ndarray:
     x = np.zeros(n * d)
     lib().orc_init_positions(seed, n, d, _box(L, d), x)
     return x.reshape(n, d)
+
+
+def place(seed: int, D0, kappa: float, L=1.0, d: int = 3, max_rounds: int = 10000):
+    """Non-overlapping placement by rounds of random sequential addition
+    (orc_place).  Returns (positions [n, d], round of each sphere, rounds or -1)."""
+    D0 = f64(D0)
+    n = D0.size
+    x = np.zeros(n * d)
+    rounds = np.zeros(n, dtype=np.int32)
+    r = lib().orc_place(seed, n, d, _box(L, d), D0, kappa, max_rounds, x, rounds)
+    return x.reshape(n, d), rounds, int(r)
 
 
 def tree_sum(a) -> float:

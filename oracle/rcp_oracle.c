@@ -72,6 +72,94 @@ void orc_init_positions(uint64_t seed, long n, int d, const double* L, double* x
         }
 }
 
+/* Non-overlapping placement (App. A: the particles are first placed without
+ * overlap at low volume fraction by a cell-list procedure; the paper does not
+ * give the procedure).  Reading: random sequential addition by size class,
+ * largest class first, each class in rounds.  With rho_i = (kappa D_i^0) / 2
+ * the class is k_i = max{k in [0, 31] : rho_i 2^k <= max rho} (the neighbour
+ * structure's rule with no skin).  In round a of class k every sphere of the
+ * class not yet placed draws candidate a from SplitMix64 outputs
+ * d (a n + i) + c (axis c), so every first draw is the uniform initial state
+ * of orc_init_positions.  A candidate is kept unless it overlaps a sphere
+ * already placed (any earlier class or round) or the candidate of a sphere of
+ * the class that precedes it (larger D^0, then lower index).  Overlap:
+ * r_ij^2 < (rho_i + rho_j)^2, minimum image.  Brute force: every candidate is
+ * tested against every sphere.  attempt[i] (optional) receives the round in
+ * which sphere i was placed.  Returns the largest number of rounds a class
+ * took, or -1 if a class still has spheres unplaced after max_rounds (those
+ * keep their last candidates). */
+int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, double kappa, int max_rounds,
+              double* x, int* attempt)
+{
+    char* placed = (char*)calloc((size_t)n, 1);
+    char* keep = (char*)malloc((size_t)n);
+    int* cls = (int*)malloc(sizeof(int) * (size_t)n);
+    double* rad = (double*)malloc(sizeof(double) * (size_t)n);
+    double* cand = (double*)malloc(sizeof(double) * (size_t)(n * d));
+    orc_init_positions(seed, n, d, L, cand);   /* every sphere's first draw */
+    double rmax = 0.0;
+    for (long i = 0; i < n; ++i) {
+        rad[i] = orc_rho(D0[i], kappa, 0.0, 0.0);
+        if (rad[i] > rmax) rmax = rad[i];
+    }
+    int kmax = 0;
+    for (long i = 0; i < n; ++i) {
+        int k = 0;
+        while (k + 1 < ORC_KMAX && ldexp(rad[i], k + 1) <= rmax) ++k;
+        cls[i] = k;
+        if (k > kmax) kmax = k;
+    }
+    int worst = 0, failed = 0;
+    for (int k = 0; k <= kmax && !failed; ++k) {
+        long left = 0;
+        for (long i = 0; i < n; ++i) left += cls[i] == k;
+        int r = 0;
+        for (; r < max_rounds && left > 0; ++r) {
+            for (long i = 0; i < n; ++i) {
+                if (cls[i] != k || placed[i]) continue;
+                for (int a = 0; a < d; ++a) {
+                    uint64_t z = orc_splitmix64_at(seed, (uint64_t)d * ((uint64_t)r * (uint64_t)n + (uint64_t)i) +
+                                                             (uint64_t)a);
+                    double u = (double)(z >> 11) * 0x1.0p-53;
+                    cand[d * i + a] = orc_wrap(L[a] * u, L[a]);
+                }
+            }
+            for (long i = 0; i < n; ++i) {
+                if (cls[i] != k || placed[i]) continue;
+                keep[i] = 1;
+                for (long j = 0; j < n && keep[i]; ++j) {
+                    if (j == i) continue;
+                    if (placed[j]) {
+                        if (orc_listed(&cand[d * i], &x[d * j], d, L, rad[i], rad[j])) keep[i] = 0;
+                    } else if (cls[j] == k && (D0[j] > D0[i] || (D0[j] == D0[i] && j < i))) {
+                        if (orc_listed(&cand[d * i], &cand[d * j], d, L, rad[i], rad[j])) keep[i] = 0;
+                    }
+                }
+            }
+            for (long i = 0; i < n; ++i) {
+                if (cls[i] != k || placed[i] || !keep[i]) continue;
+                for (int a = 0; a < d; ++a) x[d * i + a] = cand[d * i + a];
+                placed[i] = 1;
+                if (attempt) attempt[i] = r;
+                --left;
+            }
+        }
+        if (r > worst) worst = r;
+        if (left > 0) failed = 1;
+    }
+    for (long i = 0; i < n; ++i)
+        if (!placed[i]) {
+            if (attempt) attempt[i] = -1;
+            for (int a = 0; a < d; ++a) x[d * i + a] = cand[d * i + a];
+        }
+    free(placed);
+    free(keep);
+    free(cls);
+    free(rad);
+    free(cand);
+    return failed ? -1 : worst;
+}
+
 /* Pairwise tree sum: sum(a[0:m]) = sum(a[0:m/2]) + sum(a[m/2:m]) with m the
  * smallest power of two >= n and a[i] = 0 for i >= n. */
 static double tree_rec(const double* a, long lo, long len, long n)

@@ -60,6 +60,8 @@ typedef struct {
 /* ---- input-side primitives ---- */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
 void   orc_init_positions(uint64_t seed, long n, int d, const double* L, double* x);
+int    orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, double kappa,
+                 int max_rounds, double* x, int* round_of);
 double orc_tree_sum(const double* a, long n);
 double orc_cbrt(double a);
 void   orc_moments(const double* D0, long n, double out[3]); /* sum D, D^3, D^4 */

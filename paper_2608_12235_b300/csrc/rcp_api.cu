@@ -99,6 +99,11 @@ struct rcp_ctx {
     unsigned int* scan_tmp = nullptr;
     unsigned long long scan_tmp_cap = 0;
     bool built = false;
+    bool placing = false;        // placement rounds: build_b ends with the conflict search
+    unsigned char* place_flags = nullptr;   // placement: sphere placed
+    unsigned char* place_reject = nullptr;  // placement: candidate gives way this round
+    int place_class = 0;         // placement: the size class being placed
+    int place_rounds_used = 0;
     unsigned long long P = 0;
 
     // schedule
@@ -346,7 +351,7 @@ rcp_status build_a(rcp_ctx* h)
 {
     const long long N = h->N;
     const unsigned int nbN = rcp_ceil_div(N, 256);
-    CKS(materialize(h));
+    if (!h->placing) CKS(materialize(h));   // placement writes the binary64 positions itself
     h->launches += 1;
     k_build_begin<<<1, 1, 0, h->stream>>>(h->ctl, h->sigma0);
     h->launches += 1;
@@ -396,7 +401,7 @@ rcp_status build_b(rcp_ctx* h)
     h->skeys = skeys;
     h->launches += 1;
     k_gather_sorted<<<nbN, 256, 0, h->stream>>>(N, h->idx_sorted, h->xf, h->xsf);
-    if (h->perm) {
+    if (h->perm && !h->placing) {
         // mixed path: move the state into cell-key order (moments through the
         // gradient buffer, which holds nothing between evaluations)
         float* m2 = reinterpret_cast<float*>(h->g);
@@ -432,6 +437,14 @@ rcp_status search_once(rcp_ctx* h)
     const long long N = h->N;
     const unsigned int nbN = rcp_ceil_div(N, 256);
     const int nbits = bits_for((unsigned long long)N);
+    if (h->placing) {
+        h->launches += 1;
+        k_place_conflicts<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted,
+                                                      h->xsf, h->cells, h->D0, h->place_flags, h->place_reject,
+                                                      h->place_class);
+        CKL();
+        return RCP_OK;
+    }
     CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
     h->launches += 1;
     k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xsf,
@@ -688,6 +701,8 @@ rcp_status rcp_config_default(rcp_config* cfg)
     cfg->max_iters = 2000000;
     cfg->chunk = 32;
     cfg->cell_occupancy = 1.0;
+    cfg->placement = 0;
+    cfg->place_rounds = 10000;
     return RCP_OK;
 }
 
@@ -730,6 +745,75 @@ rcp_status rcp_destroy(rcp_handle h)
     delete h;
     return RCP_OK;
 }
+// Non-overlapping placement at kappa_0 (rcp_config.placement = 1): random
+// sequential addition by size class, largest class first, each class in
+// rounds.  A round draws candidates for the class's spheres not yet placed
+// (k_place_draw), finds every overlap of a candidate with a placed sphere or
+// a class-mate's candidate with the neighbour search at rho = kappa_0 D^0 / 2
+// (no skin; only candidates search), marks the candidate that gives way
+// (k_place_conflicts) and keeps the rest (k_place_accept).  Runs before any
+// build, in the caller's order.
+rcp_status place_nonoverlapping(rcp_ctx* h, unsigned long long seed)
+{
+    const long long N = h->N;
+    const unsigned int nbN = rcp_ceil_div(N, 256);
+    unsigned char *placed = nullptr, *reject = nullptr;
+    CK(cudaMalloc((void**)&placed, (size_t)N));
+    if (cudaMalloc((void**)&reject, (size_t)N) != cudaSuccess) {
+        cudaFree(placed);
+        return fail(h, RCP_ERR_OOM, "placement flags");
+    }
+    h->place_flags = placed;
+    h->place_reject = reject;
+    const double skin_s = h->c.skin_s, sigma0 = h->sigma0;
+    h->c.skin_s = 0.0;   // interaction radius rho = kappa_0 D^0 / 2
+    h->sigma0 = 0.0;
+    h->placing = true;
+    rcp_status st = [&]() -> rcp_status {
+        CK(cudaMemsetAsync(placed, 0, (size_t)N, h->stream));
+        CKS(build_a(h));   // the classes (they depend on D^0 and kappa_0 only)
+        CK(cudaStreamSynchronize(h->stream));
+        const int nlev = h->ctl_h->nlev;
+        unsigned long long counts[RCP_KMAX];
+        for (int k = 0; k < RCP_KMAX; ++k) counts[k] = h->ctl_h->lvl_count[k];
+        int worst = 0;
+        for (int k = 0; k < nlev; ++k) {
+            unsigned long long left = counts[k];
+            int r = 0;
+            for (; r < h->cfg.place_rounds && left > 0; ++r) {
+                h->launches += 1;
+                k_place_draw<<<nbN, 256, 0, h->stream>>>(seed, N, r, k, h->c, h->D0, h->lvl, placed, reject, h->xA);
+                CKL();
+                h->place_class = k;
+                CKS(build_a(h));
+                CK(cudaStreamSynchronize(h->stream));
+                CKS(build_b(h));   // ends with the conflict search of class k
+                CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
+                h->launches += 1;
+                k_place_accept<<<nbN, 256, 0, h->stream>>>(h->ctl, N, k, h->lvl, placed, reject);
+                CKL();
+                CK(cudaMemcpyAsync(&left, &h->ctl->pair_cursor, sizeof(left), cudaMemcpyDeviceToHost, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+            }
+            if (left > 0)
+                return fail(h, RCP_ERR_CAPACITY,
+                            "%llu spheres of size class %d still overlap after %d placement rounds (phi0 too high?)",
+                            left, k, r);
+            if (r > worst) worst = r;
+        }
+        h->place_rounds_used = worst;
+        return RCP_OK;
+    }();
+    h->c.skin_s = skin_s;
+    h->sigma0 = sigma0;
+    h->placing = false;
+    h->built = false;
+    h->place_flags = h->place_reject = nullptr;
+    cudaFree(placed);
+    cudaFree(reject);
+    return st;
+}
+
 
 rcp_status rcp_create(const double* diameters, long long N, int d, const double* box, unsigned long long seed,
                       const rcp_config* cfg, rcp_handle* out)
@@ -883,6 +967,7 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         h->Neff = h->SD3 / ((h->Dref * h->Dref) * h->Dref);
         h->sigma0 = h->cfg.skin_abs * ((h->cfg.lr_x * h->kappa0) * h->Dref);
         build_rungs(h);
+        if (h->cfg.placement == 1) CKS(place_nonoverlapping(h, seed));
         if (h->cfg.precision == RCP_MIXED) {
             h->launches += 1;
             k_to_fixed<<<nb, 256, 0, h->stream>>>(h->ctl, c, h->xA, h->xB, h->rA, h->rB, nullptr);

@@ -394,10 +394,15 @@ __device__ __forceinline__ float wrap_unit(float d)
 // margins on top; pairs inside the band where those bounds cannot decide are
 // settled by the exact binary64 predicate, so the listed set is exactly the
 // binary64 one.
-__global__ void __launch_bounds__(256)
-k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
-         const unsigned int* idx_sorted, const float4* xsf, const uint2* cells, unsigned long long* pairs,
-         unsigned long long cap, int nbits)
+// PLACE: the same walk for the placement rounds; an overlapping pair marks
+// the candidate that must give way (D0, placed and reject are used only then).
+template <bool PLACE>
+__device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, const double4_32a* xA,
+                                            const double4_32a* xB, const double* rho, const int* lvl,
+                                            const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
+                                            unsigned long long* pairs, unsigned long long cap, int nbits,
+                                            const double* D0, const unsigned char* placed, unsigned char* reject,
+                                            int kcur)
 {
     // threads take the spheres in cell-key order (size class, then cell), so
     // a warp shares its size class, its trip counts and most of its cells;
@@ -405,8 +410,15 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
     const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long buf[RCP_SEARCH_BUF];
     int nb = 0;
+    long long i0 = -1;
     if (ts < c.N) {
-        const long long i = idx_sorted ? (long long)idx_sorted[ts] : ts;
+        i0 = idx_sorted ? (long long)idx_sorted[ts] : ts;
+        // placement: only the candidates of the current class search (every
+        // overlap with a placed sphere or a class-mate is found from their side)
+        if (PLACE && (placed[i0] || lvl[i0] != kcur)) i0 = -1;
+    }
+    if (i0 >= 0) {
+        const long long i = i0;
         const double4_32a* x = ctl->parity ? xB : xA;
         const float4 ui = xsf[ts];
         const double ri = rho[i];
@@ -469,6 +481,18 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
                                 in = d2 < cc * cc;
                             }
                             if (!in) continue;
+                            if (PLACE) {
+                                // i is a candidate of class kcur; it gives way to
+                                // a placed sphere and to a class-mate candidate
+                                // that precedes it (larger D0, then lower index);
+                                // spheres of later classes are not there yet
+                                if (placed[j]) reject[i] = 1;
+                                else if (lvl[j] == kcur) {
+                                    const bool j_first = D0[j] > D0[i] || (D0[j] == D0[i] && (long long)j < i);
+                                    reject[j_first ? i : (long long)j] = 1;
+                                }
+                                continue;
+                            }
                             const int need = (k < li) ? 2 : 1;
                             if (nb + need > RCP_SEARCH_BUF) {
                                 const unsigned long long base = atomicAdd(&ctl->pair_cursor, (unsigned long long)nb);
@@ -483,6 +507,7 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
             }
         }
     }
+    if (PLACE) return;
     // warp-aggregated final flush
     const int lane = threadIdx.x & 31;
     unsigned int incl = (unsigned int)nb;
@@ -495,6 +520,24 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
     if (lane == 31 && total) base = atomicAdd(&ctl->pair_cursor, (unsigned long long)total);
     base = __shfl_sync(0xffffffffu, base, 31);
     flush_entries(pairs, cap, base + (incl - (unsigned int)nb), buf, nb);
+}
+
+__global__ void __launch_bounds__(256)
+k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
+         const unsigned int* idx_sorted, const float4* xsf, const uint2* cells, unsigned long long* pairs,
+         unsigned long long cap, int nbits)
+{
+    search_body<false>(ctl, c, xA, xB, rho, lvl, idx_sorted, xsf, cells, pairs, cap, nbits, nullptr, nullptr,
+                       nullptr, 0);
+}
+
+__global__ void __launch_bounds__(256)
+k_place_conflicts(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
+                  const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
+                  const double* D0, const unsigned char* placed, unsigned char* reject, int kcur)
+{
+    search_body<true>(ctl, c, xA, xB, rho, lvl, idx_sorted, xsf, cells, nullptr, 0ull, 0, D0, placed, reject,
+                      kcur);
 }
 
 // CSR from the sorted pair keys: columns are the low bits; rowptr[i] is the

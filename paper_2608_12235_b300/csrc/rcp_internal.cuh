@@ -180,6 +180,14 @@ __global__ void k_clear_halt(RcpCtl* ctl);
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
                                 const unsigned int* perm);
 __global__ void k_get_positions(long long N, const double4_32a* x, double* out, const unsigned int* perm);
+__global__ void k_place_draw(unsigned long long seed, long long N, long long r, int k, RcpConst c, const double* D0,
+                             const int* lvl, const unsigned char* placed, unsigned char* reject, double4_32a* x);
+__global__ void k_place_accept(RcpCtl* ctl, long long N, int k, const int* lvl, unsigned char* placed,
+                               const unsigned char* reject);
+__global__ void k_place_conflicts(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                                  const double* rho, const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
+                                  const uint2* cells, const double* D0, const unsigned char* placed,
+                                  unsigned char* reject, int kcur);
 __global__ void k_perm3(long long N, const unsigned int* perm, const double* in, double* out, int to_caller);
 __global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,

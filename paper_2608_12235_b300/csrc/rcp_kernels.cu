@@ -54,6 +54,36 @@ __global__ void k_init_positions(unsigned long long seed, long long N, RcpConst 
     x[i] = make_double4_32a(p[0], p[1], p[2], D0[i]);
 }
 
+// Non-overlapping placement, round r of size class k (random sequential
+// addition by class): every sphere of the class not yet placed draws its
+// candidate, SplitMix64 outputs 3 (r N + i) + a (round 0 = the uniform state
+// above); rejection marks are cleared for the round.
+__global__ void k_place_draw(unsigned long long seed, long long N, long long r, int k, RcpConst c, const double* D0,
+                             const int* lvl, const unsigned char* placed, unsigned char* reject, double4_32a* x)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    reject[i] = 0;
+    if (placed[i] || lvl[i] != k) return;
+    double p[3];
+    for (int a = 0; a < 3; ++a) {
+        unsigned long long z = splitmix64_at(seed, (unsigned long long)(3 * (r * N + i) + a));
+        double u = (double)(z >> 11) * 0x1.0p-53;
+        p[a] = wrap_step(c.L[a] * u, c.L[a]);
+    }
+    x[i] = make_double4_32a(p[0], p[1], p[2], D0[i]);
+}
+
+// Keep the candidates of class k that nothing rejected; count the rest.
+__global__ void k_place_accept(RcpCtl* ctl, long long N, int k, const int* lvl, unsigned char* placed,
+                               const unsigned char* reject)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || placed[i] || lvl[i] != k) return;
+    if (!reject[i]) placed[i] = 1;
+    else atomicAdd(&ctl->pair_cursor, 1ull);
+}
+
 // ---------------------------------------------------------------------------
 // Canonical tree of the values held by the threads of a block, in thread
 // order: adjacent lanes first (shuffle offsets 1, 2, 4, 8, 16), then adjacent

@@ -163,6 +163,41 @@ def test_full_run_fp64_bitexact_lognormal_n1000(rcp, orc):
     p.close()
 
 
+@pytest.mark.parametrize("n,sig,S,phi0", [(2000, 0.5, 10.0, 0.05), (3000, 1.5, 200.0, 0.3)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_placement_matches_the_oracle(rcp, orc, n, sig, S, phi0, precision):
+    """Non-overlapping placement by rounds: the same positions as the oracle's
+    sequential rounds (binary64 positions bit for bit; the mixed handle holds
+    them in fixed point)."""
+    D0 = inputs.lognormal(n, sig, S)
+    prec = rcp.RCP_FP64 if precision == "fp64" else rcp.RCP_MIXED
+    p = _mk(rcp, D0, seed=11, precision=prec, placement=1, phi0=phi0)
+    k = orc.kappa0(D0, 1.0, phi0)
+    x, rnd, R = orc.place(11, D0, k)
+    assert R >= 1
+    got = p.positions()
+    if precision == "fp64":
+        assert np.array_equal(got, x)
+    else:
+        assert np.allclose(got, x, rtol=0.0, atol=1e-15)
+    p.close()
+
+
+def test_full_run_from_placement_fp64_bitexact(rcp, orc):
+    """The protocol from the non-overlapping start: same trajectory as the
+    oracle's run from the oracle's placement."""
+    D0 = inputs.lognormal(800, 0.5, 10.0)
+    k = orc.kappa0(D0, 1.0, 0.05)
+    x0, _, _ = orc.place(4, D0, k)
+    ref = orc.run(D0, seed=4, x0=x0)
+    p = _mk(rcp, D0, seed=4, placement=1)
+    r = p.run()
+    assert r.stopped and ref.stopped and r.iters == ref.iters
+    assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
+    assert np.array_equal(p.positions(), ref.x)
+    p.close()
+
+
 def test_resume_is_bitexact(rcp):
     D0 = inputs.lognormal(500, 0.5, 10.0)
     a = _mk(rcp, D0, seed=3)

@@ -397,3 +397,69 @@ def test_rebuild_criterion_keeps_every_overlap_listed(orc):
         np.fill_diagonal(over, False)
         for i, j in zip(*np.nonzero(over)):
             assert (int(i), int(j)) in listed
+
+
+# ------------------------------------------------------------------ placement
+def _splitmix64_at(seed: int, k: int) -> int:
+    """SplitMix64 output k of a stream seeded with `seed` (Steele, Lea and Flood
+    2014), written here from its definition for an independent check."""
+    M = (1 << 64) - 1
+    z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def _overlap(a, b, ra, rb):
+    d = a - b
+    d = d - np.round(d)  # unit box, minimum image
+    return float(d @ d) < (ra + rb) ** 2
+
+
+def test_place_rounds_follow_their_definition(orc):
+    """Random sequential addition by size class (reading of App. A's placement),
+    checked with numpy rather than with the oracle's own predicate: no overlap
+    at the end; every sphere sits at one of its own draws (SplitMix64 outputs
+    3 (a n + i) + c for its round a); in the largest class, which nothing
+    precedes, a sphere keeps its first draw exactly when that draw overlaps no
+    first draw of a class-mate that comes before it (larger D0, lower index)."""
+    n = 1500
+    D0 = inputs.lognormal(n, 1.0, 30.0)
+    k = orc.kappa0(D0, 1.0, 0.2)
+    x, att, R = orc.place(7, D0, k)
+    assert R > 1 and (att >= 0).all() and att.max() == R - 1
+    rad = 0.5 * k * D0
+    d = x[:, None, :] - x[None, :, :]
+    d -= np.round(d)
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    c = rad[:, None] + rad[None, :]
+    assert (r2 >= c * c * (1 - 1e-12)).all()
+    for i in range(n):
+        a = int(att[i])
+        want = [(_splitmix64_at(7, 3 * (a * n + i) + ax) >> 11) * 2.0 ** -53 for ax in range(3)]
+        assert np.array_equal(x[i], np.array(want))
+    u = orc.init_positions(7, n)
+    cls = np.floor(np.log2(rad.max() / rad) + 1e-12).astype(int)  # factor-2 classes by radius
+    top = np.where(cls == 0)[0]
+    assert top.size > 10
+    for i in top:
+        before = [j for j in top if D0[j] > D0[i] or (D0[j] == D0[i] and j < i)]
+        hit = any(_overlap(u[i], u[j], rad[i], rad[j]) for j in before)
+        assert hit == (att[i] > 0)
+
+
+def test_place_two_spheres_by_hand(orc):
+    """Two equal spheres whose round-0 draws overlap: sphere 0 (lower index)
+    keeps its draw, sphere 1 moves to a later round's draw."""
+    D0 = np.array([1.0, 1.0])
+    for seed in range(1000):   # a seed whose two first draws are close
+        u = orc.init_positions(seed, 2)
+        d = u[0] - u[1]
+        d -= np.round(d)
+        if np.sqrt(d @ d) < 0.2:
+            break
+    kappa = np.sqrt(d @ d) * 1.01   # diameter just above the distance: they overlap
+    x, att, R = orc.place(seed, D0, kappa)
+    assert R >= 2 and att[0] == 0 and np.array_equal(x[0], u[0])
+    assert att[1] >= 1 and not _overlap(x[0], x[1], kappa / 2, kappa / 2)
