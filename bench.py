@@ -79,7 +79,7 @@ def pair_traffic(args, Pn):
         pairs = int(re.search(r"traffic_pairs: (\d+)", text).group(1))
     except Exception:
         return None, None
-    same_state = (args.workload == "lognormal-n1e6-s5e5" and args.skin_abs == 100.0
+    same_state = (args.workload == "lognormal-n1e6-s5e5" and args.skin_abs == 100.0 and args.skin_s == 0.02
                   and args.densify + (args.warmup + args.steps) * args.iters_per_step == 8300)
     if not sha.startswith(want) or not same_state:
         return None, None
@@ -126,10 +126,10 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(D0, iters, phi=0.5, seed=0):
+def cpu_baseline(D0, iters, phi=0.5, seed=0, skin_abs=100.0, skin_s=0.02):
     """The oracle as it stands, single thread, on a bounded sample of the same
-    workload: `iters` protocol iterations (one list build included) from
-    uniform positions at packing fraction `phi`."""
+    workload (same skin settings): `iters` protocol iterations (one list build
+    included) from uniform positions at packing fraction `phi`."""
     import oracle
     from paper_2608_12235_b300 import rcp
     cfg = rcp.rcp_config_default()
@@ -138,11 +138,12 @@ def cpu_baseline(D0, iters, phi=0.5, seed=0):
     k0 = oracle.kappa0(D0, 1.0, cfg.phi0)
     m = oracle.moments(D0)
     Dref = m[2] / m[1]
-    sigma0 = cfg.skin_abs * ((cfg.lr_x * k0) * Dref)
+    sigma0 = skin_abs * ((cfg.lr_x * k0) * Dref)
     Neff = m[1] / (Dref ** 3)
     mu = (((3.0 * cfg.delta_star0) * cfg.eps) * Neff) / (k * m[0])
     t0 = time.perf_counter()
-    builds = oracle.sample_iterations(D0, x, k, mu, (cfg.lr_x * k) * Dref, cfg.lr_kappa * k, sigma0, iters)
+    builds = oracle.sample_iterations(D0, x, k, mu, (cfg.lr_x * k) * Dref, cfg.lr_kappa * k, sigma0, iters,
+                                      skin_s=skin_s)
     dt = time.perf_counter() - t0
     return iters / dt, dt, builds
 
@@ -233,8 +234,8 @@ def run_reference(args, w):
     if rank != 0:
         return
     D0 = diameters(w)
-    cpu_baseline(D0, max(1, args.warmup))
-    rate, dt, builds = cpu_baseline(D0, max(1, args.steps))
+    cpu_baseline(D0, max(1, args.warmup), skin_abs=args.skin_abs, skin_s=args.skin_s)
+    rate, dt, builds = cpu_baseline(D0, max(1, args.steps), skin_abs=args.skin_abs, skin_s=args.skin_s)
     sample = (f"{args.steps} protocol iterations (one neighbour-list build, {builds} builds in all) from uniform "
               f"positions at phi=0.5, N={w['N']}, single thread")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iters/s", "n_gpus": 0,
@@ -256,6 +257,8 @@ def main():
     ap.add_argument("--iters-per-step", type=int, default=100)
     ap.add_argument("--densify", type=int, default=6000)
     ap.add_argument("--skin-abs", type=float, default=100.0)
+    ap.add_argument("--skin-s", type=float, default=0.02,
+                    help="size-proportional skin fraction (Adam moves large and small spheres alike)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -288,7 +291,7 @@ def main():
             dist.barrier()
 
     # ---- mixed precision: densify, warm up, time
-    p = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs)
+    p = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs, skin_s=args.skin_s)
     rcp.rcp_set_stream(p.h, stream.cuda_stream)
     p.run(max_iters=args.densify, shrink=False)
     for _ in range(args.warmup):
@@ -338,7 +341,7 @@ def main():
     traffic, traffic_pairs = pair_traffic(args, Pn)
 
     # ---- binary64 at the same state
-    q = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_FP64, skin_abs=args.skin_abs)
+    q = rcp.Packing(D0, box=1.0, seed=rank, precision=rcp.RCP_FP64, skin_abs=args.skin_abs, skin_s=args.skin_s)
     rcp.rcp_set_stream(q.h, stream.cuda_stream)
     rcp.rcp_load_state(q.h, *snap)
     q.run(max_iters=ips, shrink=False)
@@ -376,7 +379,7 @@ def main():
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, builds = cpu_baseline(D0, args.cpu_iters)
+        rate, dt, builds = cpu_baseline(D0, args.cpu_iters, skin_abs=args.skin_abs, skin_s=args.skin_s)
         cpu = {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} protocol iterations incl. one neighbour-list build from uniform "
                          f"positions at phi=0.5, N={w['N']} ({dt:.1f} s)"}
@@ -388,7 +391,7 @@ def main():
             "vs_baseline": None, "dtype": "f32 pair math, f64 state and reductions", "data": "synthetic",
             "config": {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"],
                        "precision": "mixed", "iters_per_step": ips, "densify_iters": args.densify,
-                       "skin_abs": args.skin_abs,
+                       "skin_abs": args.skin_abs, "skin_s": args.skin_s,
                        "phi_at_timing": round(phi_now, 4), "l2": "working set larger than L2 (>250 MB)"},
             "pair_evals_per_s": pair_evals,
             "fp64": {"value": value64, "unit": "iters/s", "speedup_mixed_over_fp64": value / value64},
