@@ -225,18 +225,23 @@ struct PairAcc {
     float g0, g1, g2, c0, c1, c2;
 };
 
-__device__ __forceinline__ void pair_term(const MixRec& ri, const MixRec& rj, long long i, unsigned int j,
-                                          const MixScalars& S, const RcpConst& c, PairAcc& a, float& es, float& ec,
-                                          float& ks, float& kc, float& md)
+// Plain binary32 test: false when the pair certainly does not overlap.
+__device__ __forceinline__ bool pair_may_overlap(const MixRec& ri, const MixRec& rj, const MixScalars& S,
+                                                 const RcpConst& c)
 {
-    {
-        const float fx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, c.qscale[0]);
-        const float fy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, c.qscale[1]);
-        const float fz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, c.qscale[2]);
-        const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
-        const float d = S.kappa * (0.5f * (ri.l.w + rj.l.w));
-        if (r2 > (d * d) * 1.00001f) return;
-    }
+    const float fx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, c.qscale[0]);
+    const float fy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, c.qscale[1]);
+    const float fz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, c.qscale[2]);
+    const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
+    const float d = S.kappa * (0.5f * (ri.l.w + rj.l.w));
+    return !(r2 > (d * d) * 1.00001f);
+}
+
+// The terms of a pair that passed pair_may_overlap.
+__device__ __forceinline__ void pair_term_precise(const MixRec& ri, const MixRec& rj, long long i, unsigned int j,
+                                                  const MixScalars& S, const RcpConst& c, PairAcc& a, float& es,
+                                                  float& ec, float& ks, float& kc, float& md)
+{
     float dx, dy, dz, r;
     const float delta = precise_delta(ri, rj, S, c, dx, dy, dz, r);
     if (!(delta > 0.0f)) return;
@@ -317,14 +322,19 @@ __device__ __forceinline__ float warp_sum2f(float s, float c)
     return s + c;
 }
 
-// The pair kernel of the mixed path.  Blocks [0, RCP_LONG_BLOCKS) give one
-// warp to each row longer than RCP_LONG_ROW (the rows of the largest spheres,
+// The pair kernel of the mixed path.  Blocks [0, c.long_blocks) give one
+// warp to each row longer than c.long_row (the rows of the largest spheres,
 // which hold hundreds of small neighbours): lanes stride over the row and the
 // gradient is reduced with compensated shuffles.  The other blocks give one
-// thread to each remaining row, loading partners four at a time.  Both end
-// with the row's Adam step; block partials of e and k go to part_e/part_k.
+// thread to each remaining row.  Every row is taken in two passes: the plain
+// binary32 test over all partners (two or four loads in flight), keeping a
+// bit per partner that may overlap, then the precise terms for the marked
+// partners only, in the row's order (so the sums are those of a single walk).
+// Without the precise arithmetic inside the first loop the kernel fits in 40
+// registers, 6 blocks per SM.  Both paths end with the row's Adam step; warp
+// partials of e and k go to part_e/part_k.
 #ifndef RCP_MIX_MINB
-#define RCP_MIX_MINB 4   // resident blocks per SM the register budget is sized for
+#define RCP_MIX_MINB 6   // resident blocks per SM the register budget is sized for
 #endif
 __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, float* m, float* v, MixRec* rA,
                                                 MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
@@ -349,19 +359,29 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
             const MixRec ri = rin[i];
             PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const unsigned int t1 = rowptr[i + 1];
-            unsigned int t = rowptr[i] + lane;
-            // four strides of the warp per round trip to memory
-            for (; t + 96 < t1; t += 128) {
-                const unsigned int j0 = col[t], j1 = col[t + 32], j2 = col[t + 64], j3 = col[t + 96];
-                const MixRec r0 = rin[j0], r1 = rin[j1], r2 = rin[j2], r3 = rin[j3];
-                pair_term(ri, r0, i, j0, S, c, a, es, ec, ks, kc, md);
-                pair_term(ri, r1, i, j1, S, c, a, es, ec, ks, kc, md);
-                pair_term(ri, r2, i, j2, S, c, a, es, ec, ks, kc, md);
-                pair_term(ri, r3, i, j3, S, c, a, es, ec, ks, kc, md);
-            }
-            for (; t < t1; t += 32) {
-                const unsigned int j = col[t];
-                pair_term(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
+            // windows of 32 warp strides: pass 1 marks, per lane, the strides
+            // whose partner may overlap (four strides per round trip to
+            // memory); pass 2 takes those in order through the precise terms
+            for (unsigned int w0 = rowptr[i] + lane; w0 < t1; w0 += 32u * 32u) {
+                unsigned int hit = 0u;
+                unsigned int m = 0u;
+                for (; m < 32u && w0 + 32u * (m + 3u) < t1; m += 4u) {
+                    const unsigned int t = w0 + 32u * m;
+                    const unsigned int j0 = col[t], j1 = col[t + 32], j2 = col[t + 64], j3 = col[t + 96];
+                    const MixRec r0 = rin[j0], r1 = rin[j1], r2 = rin[j2], r3 = rin[j3];
+                    if (pair_may_overlap(ri, r0, S, c)) hit |= 1u << m;
+                    if (pair_may_overlap(ri, r1, S, c)) hit |= 2u << m;
+                    if (pair_may_overlap(ri, r2, S, c)) hit |= 4u << m;
+                    if (pair_may_overlap(ri, r3, S, c)) hit |= 8u << m;
+                }
+                for (; m < 32u && w0 + 32u * m < t1; ++m)
+                    if (pair_may_overlap(ri, rin[col[w0 + 32u * m]], S, c)) hit |= 1u << m;
+                while (hit) {
+                    const unsigned int k = (unsigned int)__ffs(hit) - 1u;
+                    hit &= hit - 1u;
+                    const unsigned int j = col[w0 + 32u * k];
+                    pair_term_precise(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
+                }
             }
             const float g0 = warp_sum2f(a.g0, a.c0);
             const float g1 = warp_sum2f(a.g1, a.c1);
@@ -375,16 +395,23 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
             if (t1 - t0 <= c.long_row) {
                 const MixRec ri = rin[i];
                 PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                // pass 1: the plain binary32 test marks the partners that may
+                // overlap (a row holds at most 32 entries here); pass 2 takes
+                // them again, in the same order, through the precise terms
+                unsigned int hit = 0u;
                 unsigned int t = t0;
                 for (; t + 2 <= t1; t += 2) {
                     const unsigned int j0 = col[t], j1 = col[t + 1];
                     const MixRec r0 = rin[j0], r1 = rin[j1];
-                    pair_term(ri, r0, i, j0, S, c, a, es, ec, ks, kc, md);
-                    pair_term(ri, r1, i, j1, S, c, a, es, ec, ks, kc, md);
+                    if (pair_may_overlap(ri, r0, S, c)) hit |= 1u << (t - t0);
+                    if (pair_may_overlap(ri, r1, S, c)) hit |= 2u << (t - t0);
                 }
-                for (; t < t1; ++t) {
-                    const unsigned int j = col[t];
-                    pair_term(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
+                if (t < t1 && pair_may_overlap(ri, rin[col[t]], S, c)) hit |= 1u << (t - t0);
+                while (hit) {
+                    const unsigned int k = (unsigned int)__ffs(hit) - 1u;
+                    hit &= hit - 1u;
+                    const unsigned int j = col[t0 + k];
+                    pair_term_precise(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
                 }
                 bud = row_epilogue(ctl, c, S, i, ri, a.g0 + a.c0, a.g1 + a.c1, a.g2 + a.c2, m, v, rout, rb, mode,
                                    g_out);
