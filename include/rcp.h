@@ -87,9 +87,9 @@ typedef struct {
                                  cells are the smallest power-of-two grid with at
                                  least this many per cell on average (1) */
     int       placement;    /* initial positions: 0 uniform in the box (default);
-                               1 without overlap at phi0 (App. A: the particles are
-                               placed without overlap at low volume fraction): rounds
-                               of random sequential addition, larger spheres first,
+                               1 without overlap at phi0 (App. A starts the run from
+                               a dilute configuration with no overlaps): rounds of
+                               random sequential addition, larger spheres first,
                                round 0 being the uniform draw */
     int       place_rounds; /* most placement rounds before rcp_create gives up
                                with RCP_ERR_CAPACITY (10000) */
@@ -131,9 +131,8 @@ typedef struct {
 /* Fill *cfg with the defaults listed above. */
 rcp_status rcp_config_default(rcp_config* cfg);
 
-/* Create a packing (Sec. II: "a prescribed list of N relative diameters, a
- * spatial dimension, and a boundary geometry"; here the geometry is a
- * periodic box).
+/* Create a packing (Sec. II: the caller supplies the N relative diameters,
+ * the dimension and the boundary; here the boundary is a periodic box).
  *   diameters: host array of N positive finite relative diameters D_i^0;
  *   N >= 1; d must be 3 (else RCP_ERR_UNSUPPORTED);
  *   box: host array of d positive box edges;

@@ -72,9 +72,8 @@ void orc_init_positions(uint64_t seed, long n, int d, const double* L, double* x
         }
 }
 
-/* Non-overlapping placement (App. A: the particles are first placed without
- * overlap at low volume fraction by a cell-list procedure; the paper does not
- * give the procedure).  Reading: random sequential addition by size class,
+/* Non-overlapping placement (App. A starts from a dilute configuration with
+ * no overlaps, built with cell lists; the paper gives no further detail).  Reading: random sequential addition by size class,
  * largest class first, each class in rounds.  With rho_i = (kappa D_i^0) / 2
  * the class is k_i = max{k in [0, 31] : rho_i 2^k <= max rho} (the neighbour
  * structure's rule with no skin).  In round a of class k every sphere of the
