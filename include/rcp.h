@@ -134,10 +134,11 @@ rcp_status rcp_config_default(rcp_config* cfg);
 /* Create a packing (Sec. II: the caller supplies the N relative diameters,
  * the dimension and the boundary; here the boundary is a periodic box).
  *   diameters: host array of N positive finite relative diameters D_i^0;
- *   N >= 1; d must be 3 (else RCP_ERR_UNSUPPORTED);
+ *   N >= 1; d is 3 (spheres) or 2 (disks; else RCP_ERR_UNSUPPORTED); every
+ *   position, gradient and moment array of the other calls has d columns;
  *   box: host array of d positive box edges;
  *   seed: positions are uniform in the box, coordinate a of sphere i taken
- *         from output 3 i + a of SplitMix64 seeded with `seed`;
+ *         from output d i + a of SplitMix64 seeded with `seed`;
  *   cfg: NULL for the defaults;
  *   kappa_0 is set so that the packing fraction equals cfg->phi0.
  * On success *out receives the handle, which owns a new non-blocking stream
@@ -238,6 +239,9 @@ rcp_status rcp_cell_keys(rcp_handle h, unsigned long long* keys);
 
 /* Number of spheres. */
 long long rcp_size(rcp_handle h);
+
+/* Dimension d given at creation (2 or 3; 0 for NULL). */
+int rcp_dim(rcp_handle h);
 
 /* ---- batches: many independent packings in one graph of batched kernels ---- */
 typedef struct rcp_batch_ctx* rcp_batch;

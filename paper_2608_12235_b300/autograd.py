@@ -2,7 +2,7 @@
 
     E = RcpEnergy.apply(x, kappa, packing, mu)
 
-x is an (N, 3) float64 CUDA tensor, kappa a 0-d float64 CUDA tensor, packing
+x is an (N, d) float64 CUDA tensor, kappa a 0-d float64 CUDA tensor, packing
 an rcp.Packing (its diameters, box and precision), mu the growth weight of
 Eq. energy.  The forward is one pass of the fused pair kernel, which yields E
 together with dE/dx and dE/dkappa; the hand-written backward scales those by
@@ -21,8 +21,8 @@ class RcpEnergy(torch.autograd.Function):
     def forward(ctx, x, kappa, packing, mu):
         if not (x.is_cuda and kappa.is_cuda):
             raise ValueError("RcpEnergy needs CUDA tensors")
-        if x.dtype != torch.float64 or kappa.dtype != torch.float64 or x.shape != (packing.n, 3):
-            raise ValueError("x must be float64 (N, 3) and kappa a float64 scalar")
+        if x.dtype != torch.float64 or kappa.dtype != torch.float64 or x.shape != (packing.n, packing.d):
+            raise ValueError("x must be float64 (N, d) and kappa a float64 scalar")
         x = x.contiguous()
         kappa = kappa.reshape(1).contiguous()
         rcp.rcp_set_stream(packing.h, rcp.torch_stream(x.device))

@@ -640,7 +640,7 @@ rcp_status capture_graph(rcp_ctx* h)
 void build_rungs(rcp_ctx* h)
 {
     const rcp_config& p = h->cfg;
-    double nt = (4000.0 * (double)p.Y + (double)p.X * std::sqrt((double)(h->N * 3LL))) - 2000.0;
+    double nt = (4000.0 * (double)p.Y + (double)p.X * std::sqrt((double)(h->N * (long long)h->c.dim))) - 2000.0;
     long long b0 = (long long)std::ceil(nt);
     if (b0 < p.n_min) b0 = p.n_min;
     long long bq = (long long)std::ceil(nt / 4.0);
@@ -726,6 +726,8 @@ const char* rcp_status_str(rcp_status s)
 const char* rcp_last_error(rcp_handle h) { return h ? h->err : ""; }
 
 long long rcp_size(rcp_handle h) { return h ? h->N : 0; }
+
+int rcp_dim(rcp_handle h) { return h ? h->c.dim : 0; }
 
 rcp_status rcp_destroy(rcp_handle h)
 {
@@ -821,10 +823,14 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
     if (!out) return RCP_ERR_ARG;
     *out = nullptr;
     if (!diameters || !box || N < 1) return RCP_ERR_ARG;
-    if (d != 3) return RCP_ERR_UNSUPPORTED;
+    if (d != 2 && d != 3) return RCP_ERR_UNSUPPORTED;
     if (N >= (1LL << 31)) return RCP_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < d; ++a)
         if (!(box[a] > 0.0) || !std::isfinite(box[a])) return RCP_ERR_ARG;
+    // d = 2: disks held in the plane z = L_z / 2 of a box whose third edge is
+    // the larger of the two (every z difference is exactly zero)
+    const double box3[3] = {box[0], box[1], d == 3 ? box[2] : (box[0] > box[1] ? box[0] : box[1])};
+    box = box3;
     for (long long i = 0; i < N; ++i)
         if (!(diameters[i] > 0.0) || !std::isfinite(diameters[i])) return RCP_ERR_ARG;
     rcp_ctx* h = new rcp_ctx();
@@ -858,7 +864,8 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         if (box[a] < c.Lmin) c.Lmin = box[a];
         if (box[a] > c.Lmax) c.Lmax = box[a];
     }
-    c.V = (box[0] * box[1]) * box[2];
+    c.V = d == 2 ? box[0] * box[1] : (box[0] * box[1]) * box[2];   // area when d = 2
+    c.dim = d;
     c.eps = h->cfg.eps;
     c.beta1 = h->cfg.beta1;
     c.beta2 = h->cfg.beta2;
@@ -954,9 +961,10 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         CKL();
         CKS(tree_sum_D(h, 1, &h->ctl->SD));
         CKS(tree_sum_D(h, 3, &h->ctl->SD3));
+        if (d == 2) CKS(tree_sum_D(h, 2, &h->ctl->SD2));
         CKS(tree_sum_D(h, 4, &h->ctl->SD4));
         h->launches += 1;
-        k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.V);
+        k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.V, d);
         CKL();
         CKS(sync_ctl(h));
         h->SD = h->ctl_h->SD;
@@ -998,8 +1006,9 @@ rcp_status rcp_set_positions(rcp_handle h, const double* x, double kappa, int on
 {
     if (!h || !x) return RCP_ERR_ARG;
     const size_t n = (size_t)h->N;
-    if (on_device) CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
-    else CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    const size_t nd = (size_t)h->c.dim * n;
+    if (on_device) CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
+    else CK(cudaMemcpyAsync(h->xtmp, x, sizeof(double) * nd, cudaMemcpyHostToDevice, h->stream));
     CKS(sync_ctl(h));
     double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
     h->launches += 1;
@@ -1041,21 +1050,22 @@ rcp_status rcp_energy_grad(rcp_handle h, double mu, double* E, double* grad_x, d
     CKL();
     const size_t n = (size_t)h->N;
     const double* gsrc = h->g;
-    if (h->perm && grad_x) {
-        // internal order -> the caller's
+    const size_t nd = (size_t)h->c.dim * n;
+    if ((h->perm || h->c.dim != 3) && grad_x) {
+        // internal order and layout -> the caller's
         h->launches += 1;
-        k_perm3<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->perm, h->g, h->xtmp, 1);
+        k_perm3<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->perm, h->g, h->xtmp, 1);
         CKL();
         gsrc = h->xtmp;
     }
     if (on_device) {
-        if (grad_x) CK(cudaMemcpyAsync(grad_x, gsrc, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
+        if (grad_x) CK(cudaMemcpyAsync(grad_x, gsrc, sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
         if (E) CK(cudaMemcpyAsync(E, &h->ctl->E, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         if (dE_dkappa) CK(cudaMemcpyAsync(dE_dkappa, &h->ctl->dEdk, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         if (max_delta) CK(cudaMemcpyAsync(max_delta, &h->ctl->maxdelta, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         return RCP_OK;
     }
-    if (grad_x) CK(cudaMemcpyAsync(grad_x, gsrc, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    if (grad_x) CK(cudaMemcpyAsync(grad_x, gsrc, sizeof(double) * nd, cudaMemcpyDeviceToHost, h->stream));
     CKS(sync_ctl(h));
     if (h->ctl_h->status == RCP_ERR_NAN) return fail(h, RCP_ERR_NAN, "non-finite energy or gradient");
     if (E) *E = h->ctl_h->E;
@@ -1069,7 +1079,7 @@ rcp_status rcp_energy_grad_at(rcp_handle h, const double* x_dev, const double* k
 {
     if (!h || !x_dev || !kappa_dev) return RCP_ERR_ARG;
     const size_t n = (size_t)h->N;
-    CK(cudaMemcpyAsync(h->xtmp, x_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->xtmp, x_dev, sizeof(double) * h->c.dim * n, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemcpyAsync(&h->ctl->kappa, kappa_dev, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CKS(sync_ctl(h));  // parity and build state
     double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
@@ -1095,13 +1105,13 @@ rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, d
     if (!h || !grad_x) return RCP_ERR_ARG;
     const size_t n = (size_t)h->N;
     if (!h->built) CKS(build(h));   // before the copy: a build uses h->g as scratch
-    CK(cudaMemcpyAsync(h->g, grad_x, sizeof(double) * 3 * n,
+    CK(cudaMemcpyAsync(h->g, grad_x, sizeof(double) * h->c.dim * n,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     const double* gin = h->g;
-    if (h->perm) {
-        // the caller's order -> internal
+    if (h->perm || h->c.dim != 3) {
+        // the caller's order and layout -> internal
         h->launches += 1;
-        k_perm3<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->perm, h->g, h->xtmp, 0);
+        k_perm3<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->perm, h->g, h->xtmp, 0);
         CKL();
         gin = h->xtmp;
     }
@@ -1290,13 +1300,14 @@ rcp_status rcp_state(rcp_handle h, double* x, double* m, double* v, rcp_scalars*
     if (!h) return RCP_ERR_ARG;
     CKS(sync_ctl(h));
     const size_t n = (size_t)h->N;
+    const int dc = h->c.dim;
     if (x) {
         CKS(materialize(h));
         const double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
         h->launches += 1;
-        k_get_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, cur, h->xtmp, h->perm);
+        k_get_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, cur, h->xtmp, h->perm);
         CKL();
-        CK(cudaMemcpyAsync(x, h->xtmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(x, h->xtmp, sizeof(double) * h->c.dim * n, cudaMemcpyDeviceToHost, h->stream));
     }
     if (h->cfg.precision == RCP_MIXED) {
         std::vector<float> tmp(m || v ? 3 * n : 0);
@@ -1306,17 +1317,30 @@ rcp_status rcp_state(rcp_handle h, double* x, double* m, double* v, rcp_scalars*
             CK(cudaMemcpyAsync(tmp.data(), h->m32, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
             for (size_t i = 0; i < n; ++i)
-                for (int a = 0; a < 3; ++a) m[3 * (size_t)pm[i] + a] = tmp[3 * i + a];
+                for (int a = 0; a < dc; ++a) m[dc * (size_t)pm[i] + a] = tmp[3 * i + a];
         }
         if (v) {
             CK(cudaMemcpyAsync(tmp.data(), h->v32, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
             CK(cudaStreamSynchronize(h->stream));
             for (size_t i = 0; i < n; ++i)
-                for (int a = 0; a < 3; ++a) v[3 * (size_t)pm[i] + a] = tmp[3 * i + a];
+                for (int a = 0; a < dc; ++a) v[dc * (size_t)pm[i] + a] = tmp[3 * i + a];
         }
     } else {
-        if (m) CK(cudaMemcpyAsync(m, h->m64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
-        if (v) CK(cudaMemcpyAsync(v, h->v64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        if (dc == 3) {
+            if (m) CK(cudaMemcpyAsync(m, h->m64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+            if (v) CK(cudaMemcpyAsync(v, h->v64, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            std::vector<double> tmp(m || v ? 3 * n : 0);
+            for (int w = 0; w < 2; ++w) {
+                double* out = w == 0 ? m : v;
+                if (!out) continue;
+                CK(cudaMemcpyAsync(tmp.data(), w == 0 ? h->m64 : h->v64, sizeof(double) * 3 * n,
+                                   cudaMemcpyDeviceToHost, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+                for (size_t i = 0; i < n; ++i)
+                    for (int a = 0; a < dc; ++a) out[dc * i + a] = tmp[3 * i + a];
+            }
+        }
     }
     CK(cudaStreamSynchronize(h->stream));
     if (s) {
@@ -1339,6 +1363,7 @@ rcp_status rcp_load_state(rcp_handle h, const double* x, const double* m, const 
 {
     if (!h) return RCP_ERR_ARG;
     const size_t n = (size_t)h->N;
+    const int dc = h->c.dim;
     if (x) CKS(rcp_set_positions(h, x, s ? s->kappa : 0.0, 0));
     if (h->cfg.precision == RCP_MIXED) {
         std::vector<float> tmp(3 * n);
@@ -1346,19 +1371,32 @@ rcp_status rcp_load_state(rcp_handle h, const double* x, const double* m, const 
         if (m || v) CKS(copy_perm(h, pm.data()));
         if (m) {
             for (size_t i = 0; i < n; ++i)
-                for (int a = 0; a < 3; ++a) tmp[3 * i + a] = (float)m[3 * (size_t)pm[i] + a];
+                for (int a = 0; a < 3; ++a) tmp[3 * i + a] = a < dc ? (float)m[dc * (size_t)pm[i] + a] : 0.0f;
             CK(cudaMemcpyAsync(h->m32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream));
             CK(cudaStreamSynchronize(h->stream));
         }
         if (v) {
             for (size_t i = 0; i < n; ++i)
-                for (int a = 0; a < 3; ++a) tmp[3 * i + a] = (float)v[3 * (size_t)pm[i] + a];
+                for (int a = 0; a < 3; ++a) tmp[3 * i + a] = a < dc ? (float)v[dc * (size_t)pm[i] + a] : 0.0f;
             CK(cudaMemcpyAsync(h->v32, tmp.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream));
             CK(cudaStreamSynchronize(h->stream));
         }
     } else {
-        if (m) CK(cudaMemcpyAsync(h->m64, m, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-        if (v) CK(cudaMemcpyAsync(h->v64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+        if (dc == 3) {
+            if (m) CK(cudaMemcpyAsync(h->m64, m, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+            if (v) CK(cudaMemcpyAsync(h->v64, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+        } else {
+            std::vector<double> tmp(3 * n);
+            for (int w = 0; w < 2; ++w) {
+                const double* in = w == 0 ? m : v;
+                if (!in) continue;
+                for (size_t i = 0; i < n; ++i)
+                    for (int a = 0; a < 3; ++a) tmp[3 * i + a] = a < dc ? in[dc * i + a] : 0.0;
+                CK(cudaMemcpyAsync(w == 0 ? h->m64 : h->v64, tmp.data(), sizeof(double) * 3 * n,
+                                   cudaMemcpyHostToDevice, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+            }
+        }
     }
     if (s) {
         CKS(sync_ctl(h));

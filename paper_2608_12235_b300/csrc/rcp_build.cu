@@ -161,11 +161,12 @@ __global__ void k_grid(RcpCtl* ctl, RcpConst c)
         const double cnt = (double)ctl->lvl_count[k];
         if (a == 0) ctl->rho_lvl[k] = r;
         unsigned int n = 1;
-        if (r > 0.0)
+        if (r > 0.0 && a < c.dim)   // d = 2: one cell layer in z, area occupancy in x and y
             for (;;) {
                 if (n >= RCP_NMAX_AXIS) break;
                 const double h = c.L[a] / (double)(2 * n);
-                if (!(((h * h) * h) * cnt >= c.cell_occ * c.V)) break;
+                const double cell = c.dim == 2 ? h * h : (h * h) * h;
+                if (!(cell * cnt >= c.cell_occ * c.V)) break;
                 n *= 2;
             }
         ctl->ng[k][a] = (int)n;

@@ -63,7 +63,7 @@ struct RcpCtl {
     unsigned long long pairs;
     unsigned int n_long;      // rows longer than RCP_LONG_ROW
     // constants and one-off results
-    double SD, SD3, SD4;
+    double SD, SD2, SD3, SD4;
     unsigned long long shrink_bits;
     unsigned long long md64_bits;
     double kappa_c, phi;
@@ -89,6 +89,7 @@ struct RcpConst {
     float Lf[3];            // L_a in binary32
     float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
     unsigned int canon;        // 1: binary64 path (canonical sums); 0: mixed path
+    int dim;                   // the caller's dimension: 3, or 2 (disks held in the plane z = L_z / 2)
     unsigned int long_row;     // rows longer than this get a warp (mixed)
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
 };
@@ -173,13 +174,13 @@ static inline unsigned int rcp_ceil_div(unsigned long long a, unsigned long long
 __global__ void k_init_positions(unsigned long long seed, long long N, RcpConst c, const double* D0, double4_32a* x);
 __global__ void k_tree_terms(const double* D0, long long N, int power, double* out);
 __global__ void k_tree_pass(const double* in, long long n, double* out);
-__global__ void k_kappa0(RcpCtl* ctl, double phi0, double V);
+__global__ void k_kappa0(RcpCtl* ctl, double phi0, double V, int dim);
 __global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, double eta_k, double tol,
                            long long iter_limit, int final_rung);
 __global__ void k_clear_halt(RcpCtl* ctl);
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
                                 const unsigned int* perm);
-__global__ void k_get_positions(long long N, const double4_32a* x, double* out, const unsigned int* perm);
+__global__ void k_get_positions(long long N, RcpConst c, const double4_32a* x, double* out, const unsigned int* perm);
 __global__ void k_place_draw(unsigned long long seed, long long N, long long r, int k, RcpConst c, const double* D0,
                              const int* lvl, const unsigned char* placed, unsigned char* reject, double4_32a* x);
 __global__ void k_place_accept(RcpCtl* ctl, long long N, int k, const int* lvl, unsigned char* placed,
@@ -188,7 +189,8 @@ __global__ void k_place_conflicts(RcpCtl* ctl, RcpConst c, const double4_32a* xA
                                   const double* rho, const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
                                   const uint2* cells, const double* D0, const unsigned char* placed,
                                   unsigned char* reject, int kcur);
-__global__ void k_perm3(long long N, const unsigned int* perm, const double* in, double* out, int to_caller);
+__global__ void k_perm3(long long N, RcpConst c, const unsigned int* perm, const double* in, double* out,
+                        int to_caller);
 __global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
                          double* part_e, double* part_k, int mode, double* g_out);

@@ -47,7 +47,11 @@ __global__ void k_init_positions(unsigned long long seed, long long N, RcpConst 
     if (i >= N) return;
     double p[3];
     for (int a = 0; a < 3; ++a) {
-        unsigned long long z = splitmix64_at(seed, (unsigned long long)(3 * i + a));
+        if (a >= c.dim) {   // d = 2: every disk in the plane z = L_z / 2
+            p[a] = c.halfL[a];
+            continue;
+        }
+        unsigned long long z = splitmix64_at(seed, (unsigned long long)(c.dim * i + a));
         double u = (double)(z >> 11) * 0x1.0p-53;
         p[a] = wrap_step(c.L[a] * u, c.L[a]);
     }
@@ -67,7 +71,11 @@ __global__ void k_place_draw(unsigned long long seed, long long N, long long r, 
     if (placed[i] || lvl[i] != k) return;
     double p[3];
     for (int a = 0; a < 3; ++a) {
-        unsigned long long z = splitmix64_at(seed, (unsigned long long)(3 * (r * N + i) + a));
+        if (a >= c.dim) {
+            p[a] = c.halfL[a];
+            continue;
+        }
+        unsigned long long z = splitmix64_at(seed, (unsigned long long)(c.dim * (r * N + i) + a));
         double u = (double)(z >> 11) * 0x1.0p-53;
         p[a] = wrap_step(c.L[a] * u, c.L[a]);
     }
@@ -134,6 +142,7 @@ __global__ void __launch_bounds__(RCP_TREE) k_tree_terms(const double* D0, long 
     if (i < N) {
         double D = D0[i];
         if (power == 1) v = D;
+        else if (power == 2) v = D * D;
         else if (power == 3) v = (D * D) * D;
         else v = (D * D) * (D * D);
     }
@@ -168,8 +177,12 @@ __global__ void __launch_bounds__(RCP_TREE) k_tree_pass2(const double* ina, cons
 // kappa_0: the cube root of phi0 V / (pi/6 sum D^3) by 200 Newton steps
 // y <- (2y + a/y^2)/3 from y = 1 (correctly rounded operations only, so the
 // bits do not depend on a math library).
-__global__ void k_kappa0(RcpCtl* ctl, double phi0, double V)
+__global__ void k_kappa0(RcpCtl* ctl, double phi0, double V, int dim)
 {
+    if (dim == 2) {   // area fraction of disks: kappa^2 (pi/4) sum D^2 = phi0 A
+        ctl->kappa = sqrt((phi0 * V) / ((RCP_PI / 4.0) * ctl->SD2));
+        return;
+    }
     double a = (phi0 * V) / ((RCP_PI / 6.0) * ctl->SD3);
     double y = 1.0;
     if (a > 0.0)
@@ -250,35 +263,44 @@ __global__ void k_set_positions(long long N, RcpConst c, const double* xin, cons
     const long long u = perm ? (long long)perm[i] : i;
     double p[3];
     for (int a = 0; a < 3; ++a) {
-        double v = xin[3 * u + a];
+        if (a >= c.dim) {   // d = 2: the plane z = L_z / 2
+            p[a] = c.halfL[a];
+            continue;
+        }
+        double v = xin[c.dim * u + a];
         if (v < 0.0 || v >= c.L[a]) v = v - c.L[a] * floor(v / c.L[a]);
         p[a] = wrap_step(v, c.L[a]);
     }
     x[i] = make_double4_32a(p[0], p[1], p[2], D0[i]);
 }
 
-__global__ void k_get_positions(long long N, const double4_32a* x, double* out, const unsigned int* perm)
+__global__ void k_get_positions(long long N, RcpConst c, const double4_32a* x, double* out, const unsigned int* perm)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const long long u = perm ? (long long)perm[i] : i;
     double4_32a p = x[i];
-    out[3 * u + 0] = p.x;
-    out[3 * u + 1] = p.y;
-    out[3 * u + 2] = p.z;
+    out[c.dim * u + 0] = p.x;
+    out[c.dim * u + 1] = p.y;
+    if (c.dim == 3) out[3 * u + 2] = p.z;
 }
 
-// [N][3] vectors between the caller's order and the internal one:
-// to_caller: out[perm[i]] = in[i]; otherwise out[i] = in[perm[i]].
-__global__ void k_perm3(long long N, const unsigned int* perm, const double* in, double* out, int to_caller)
+// Vectors between the caller's layout ([N][dim], caller order) and the
+// internal one ([N][3], internal order; perm NULL: the same order).
+// to_caller: out[perm[i]] = in[i], the z column dropped when dim = 2;
+// otherwise out[i] = in[perm[i]], z = 0 when dim = 2.
+__global__ void k_perm3(long long N, RcpConst c, const unsigned int* perm, const double* in, double* out,
+                        int to_caller)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const long long u = perm[i];
-    const long long s = to_caller ? i : u, d = to_caller ? u : i;
-    out[3 * d + 0] = in[3 * s + 0];
-    out[3 * d + 1] = in[3 * s + 1];
-    out[3 * d + 2] = in[3 * s + 2];
+    const long long u = perm ? (long long)perm[i] : i;
+    const int dc = c.dim;
+    if (to_caller) {
+        for (int a = 0; a < dc; ++a) out[dc * u + a] = in[3 * i + a];
+    } else {
+        for (int a = 0; a < 3; ++a) out[3 * i + a] = a < dc ? in[dc * u + a] : 0.0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -669,5 +691,6 @@ __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c)
     if (q < kc) kc = q;
     kc = kc * (1.0 - 0x1.0p-50);
     ctl->kappa_c = kc;
-    ctl->phi = (((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) / c.V;
+    if (c.dim == 2) ctl->phi = (((RCP_PI / 4.0) * (kc * kc)) * ctl->SD2) / c.V;
+    else ctl->phi = (((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) / c.V;
 }

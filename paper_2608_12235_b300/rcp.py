@@ -23,7 +23,7 @@ STATUS = {0: "RCP_OK", 1: "RCP_ERR_ARG", 2: "RCP_ERR_IMAGE", 3: "RCP_ERR_OOM", 4
 # every symbol include/rcp.h declares
 EXPORTS = ["rcp_config_default", "rcp_create", "rcp_destroy", "rcp_set_stream", "rcp_set_positions",
            "rcp_build_neighbors", "rcp_energy_grad", "rcp_energy_grad_at", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
-           "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_status_str", "rcp_last_error",
+           "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_dim", "rcp_status_str", "rcp_last_error",
            "rcp_energy_grad_noalloc", "rcp_batch_create", "rcp_batch_run", "rcp_batch_tuning", "rcp_batch_destroy",
            "rcp_batch_last_error"]
 
@@ -100,12 +100,14 @@ def load(path: str | None = None) -> C.CDLL:
     L.rcp_batch_last_error.restype = C.c_char_p
     L.rcp_size.argtypes = [vp]
     L.rcp_size.restype = C.c_longlong
+    L.rcp_dim.argtypes = [vp]
+    L.rcp_dim.restype = C.c_int
     L.rcp_status_str.argtypes = [ip]
     L.rcp_status_str.restype = C.c_char_p
     L.rcp_last_error.argtypes = [vp]
     L.rcp_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("rcp_size", "rcp_status_str", "rcp_last_error", "rcp_batch_last_error"):
+        if name not in ("rcp_size", "rcp_dim", "rcp_status_str", "rcp_last_error", "rcp_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -138,7 +140,7 @@ def rcp_config_default(**overrides) -> rcp_config:
 
 def rcp_create(diameters, box=1.0, seed: int = 0, cfg: rcp_config | None = None, d: int = 3):
     D0 = np.ascontiguousarray(diameters, dtype=np.float64)
-    b = np.full(3, float(box)) if np.isscalar(box) else np.ascontiguousarray(box, dtype=np.float64)
+    b = np.full(d, float(box)) if np.isscalar(box) else np.ascontiguousarray(box, dtype=np.float64)
     h = C.c_void_p()
     _check(load().rcp_create(D0.ctypes.data, D0.size, d, b.ctypes.data, seed,
                              C.byref(cfg) if cfg is not None else None, C.byref(h)))
@@ -220,20 +222,20 @@ def rcp_shrink(h):
 
 
 def rcp_state(h):
-    n = load().rcp_size(h)
-    x, m, v = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    n, d = load().rcp_size(h), load().rcp_dim(h)
+    x, m, v = np.zeros((n, d)), np.zeros((n, d)), np.zeros((n, d))
     s = rcp_scalars()
     _check(load().rcp_state(h, x.ctypes.data, m.ctypes.data, v.ctypes.data, C.byref(s)), h)
     return x, m, v, s
 
 
 def rcp_positions(h, out=None):
-    """Current positions only ([N, 3] binary64), written into `out` when given
+    """Current positions only ([N, d] binary64), written into `out` when given
     (e.g. a page-locked array, for a direct device-to-host copy)."""
-    n = load().rcp_size(h)
-    x = np.zeros((n, 3)) if out is None else out
-    if x.shape != (n, 3) or x.dtype != np.float64 or not x.flags.c_contiguous:
-        raise ValueError("out must be a C-contiguous float64 array of shape (N, 3)")
+    n, d = load().rcp_size(h), load().rcp_dim(h)
+    x = np.zeros((n, d)) if out is None else out
+    if x.shape != (n, d) or x.dtype != np.float64 or not x.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array of shape (N, d)")
     _check(load().rcp_state(h, x.ctypes.data, None, None, None), h)
     return x
 
@@ -275,6 +277,10 @@ def rcp_size(h) -> int:
     return int(load().rcp_size(h))
 
 
+def rcp_dim(h) -> int:
+    return int(load().rcp_dim(h))
+
+
 # ----------------------------------------------------------------- convenience
 @dataclass
 class RunSummary:
@@ -294,10 +300,11 @@ class RunSummary:
 class Packing:
     """One packing on the GPU (owns an rcp handle)."""
 
-    def __init__(self, diameters, box=1.0, seed: int = 0, precision: int = RCP_FP64, **cfg):
+    def __init__(self, diameters, box=1.0, seed: int = 0, precision: int = RCP_FP64, d: int = 3, **cfg):
         self.cfg = rcp_config_default(precision=precision, **cfg)
         self.n = int(np.size(diameters))
-        self.h = rcp_create(diameters, box, seed, self.cfg)
+        self.d = int(d)
+        self.h = rcp_create(diameters, box, seed, self.cfg, d=self.d)
 
     def close(self):
         if self.h:
@@ -312,7 +319,7 @@ class Packing:
 
     def energy_grad(self, mu: float):
         E, dk, md = np.zeros(1), np.zeros(1), np.zeros(1)
-        g = np.zeros((self.n, 3))
+        g = np.zeros((self.n, self.d))
         rcp_energy_grad(self.h, mu, E, g, dk, md)
         return float(E[0]), g, float(dk[0]), float(md[0])
 

@@ -49,5 +49,5 @@ def test_create_rejects_bad_input_before_touching_the_gpu(lib):
         rcp.rcp_create(np.array([1.0, -1.0]), 1.0, 0)
     assert e.value.status == 1
     with pytest.raises(rcp.RcpError) as e:
-        rcp.rcp_create(np.ones(4), 1.0, 0, d=2)
+        rcp.rcp_create(np.ones(4), np.ones(4), 0, d=4)   # d is 2 or 3
     assert e.value.status == 9

@@ -349,3 +349,61 @@ def test_periodic_image_rule_is_enforced(rcp):
         rcp.rcp_build_neighbors(p.h)
     assert e.value.status == 2
     p.close()
+
+
+# ------------------------------------------------------------------ two dimensions
+# d = 2 handles hold disks in the plane z = L_z / 2 of the three-axis layout;
+# everything the caller sees has two columns and must match the oracle's d = 2
+# definitions bit for bit in binary64.
+def test_two_dimensional_initial_state_and_kappa0_bitexact(rcp, orc):
+    D0 = inputs.lognormal(700, 0.5, 10.0)
+    p = _mk(rcp, D0, seed=9, d=2)
+    assert rcp.rcp_dim(p.h) == 2
+    assert np.array_equal(p.positions(), orc.init_positions(9, 700, 1.0, d=2))
+    assert p.state()[3].kappa == orc.kappa0(D0, 1.0, 0.05, d=2)
+    p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_dimensional_list_and_energy(rcp, orc, precision):
+    n = 1200
+    D0 = inputs.lognormal(n, 1.0, 30.0)
+    prec = rcp.RCP_FP64 if precision == "fp64" else rcp.RCP_MIXED
+    p = _mk(rcp, D0, seed=3, d=2, precision=prec)
+    x = orc.init_positions(3, n, 1.0, d=2)
+    k = orc.kappa0(D0, 1.0, 0.45, d=2)
+    p.set_positions(x, k)
+    rp, col = p.neighbors()
+    s0 = _sigma0(orc, D0, orc.kappa0(D0, 1.0, 0.05, d=2), p.cfg)
+    orp, ocol = orc.list_brute(x, D0, 1.0, k, p.cfg.skin_s, s0, d=2)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    E, g, dk, md = p.energy_grad(0.01)
+    oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, 0.01, d=2)
+    assert g.shape == (n, 2)
+    if precision == "fp64":
+        assert E == oE and dk == odk and md == omd and np.array_equal(g, og)
+    else:
+        assert abs(E - oE) <= 1e-5 * abs(oE) and abs(dk - odk) <= 1e-5 * abs(odk)
+        assert np.linalg.norm(g - og) <= 1e-5 * np.linalg.norm(og)
+    p.close()
+
+
+def test_two_dimensional_full_run_fp64_bitexact(rcp, orc):
+    """Disks, lognormal sigma_ln = 0.5, S = 10, N = 400, run to the stop: the
+    oracle's d = 2 trajectory, iteration count and area fraction."""
+    D0 = inputs.lognormal(400, 0.5, 10.0)
+    ref = orc.run(D0, seed=1, d=2)
+    p = _mk(rcp, D0, seed=1, d=2)
+    r = p.run()
+    assert r.stopped and ref.stopped and r.iters == ref.iters
+    assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
+    assert np.array_equal(p.positions(), ref.x)
+    p.close()
+
+
+def test_two_dimensional_placement_matches_the_oracle(rcp, orc):
+    D0 = inputs.lognormal(1500, 1.0, 30.0)
+    p = _mk(rcp, D0, seed=6, d=2, placement=1, phi0=0.2)
+    x, _, R = orc.place(6, D0, orc.kappa0(D0, 1.0, 0.2, d=2), d=2)
+    assert R >= 1 and np.array_equal(p.positions(), x)
+    p.close()
