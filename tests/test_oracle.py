@@ -463,3 +463,48 @@ def test_place_two_spheres_by_hand(orc):
     x, att, R = orc.place(seed, D0, kappa)
     assert R >= 2 and att[0] == 0 and np.array_equal(x[0], u[0])
     assert att[1] >= 1 and not _overlap(x[0], x[1], kappa / 2, kappa / 2)
+
+
+# ------------------------------------------------------------------ two dimensions
+def test_two_dimensional_inputs_follow_their_definition(orc):
+    """d = 2: coordinate a of disk i is SplitMix64 output 2 i + a (checked with
+    the generator written out in Python), the rung budget uses sqrt(2 N), and
+    the listed pairs are those of the definition (numpy, minimum image)."""
+    n = 600
+    x = orc.init_positions(4, n, 1.0, d=2)
+    want = np.array([[(_splitmix64_at(4, 2 * i + a) >> 11) * 2.0 ** -53 for a in range(2)] for i in range(n)])
+    assert np.array_equal(x, want)
+    assert orc.n_trig(1000, 2, 2, 9) == pytest.approx(6000 + 9 * math.sqrt(2000.0), rel=1e-15)
+    D0 = inputs.lognormal(n, 1.0, 30.0)
+    k = orc.kappa0(D0, 1.0, 0.4, d=2)
+    s, s0 = 0.1, 1e-3
+    rp, col = orc.list_brute(x, D0, 1.0, k, s, s0, d=2)
+    rho = (k * D0) * (0.5 + s) + s0
+    d = x[:, None, :] - x[None, :, :]
+    d -= np.round(d)
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    want_pairs = r2 < (rho[:, None] + rho[None, :]) ** 2
+    got = np.zeros_like(want_pairs)
+    for i in range(n):
+        got[i, col[rp[i]:rp[i + 1]]] = True
+    # the oracle's left-to-right squared distance and numpy's may differ in the
+    # last bit only for pairs at the cut; there are none at this seed
+    assert np.array_equal(got, want_pairs)
+
+
+def test_two_dimensional_run_reaches_the_criterion(orc):
+    """A d = 2 run stops below the overlap tolerance, shrink leaves no overlap
+    (checked with numpy), and the area fraction is that of a dense disk
+    packing."""
+    D0 = inputs.lognormal(300, 0.5, 10.0)
+    r = orc.run(D0, seed=2, d=2)
+    assert r.stopped and r.max_delta < 5e-4 and r.x.shape == (300, 2)
+    d = r.x[:, None, :] - r.x[None, :, :]
+    d -= np.round(d)
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    c = 0.5 * r.kappa_c * (D0[:, None] + D0[None, :])
+    assert (r2 >= c * c * (1 - 1e-12)).all()
+    assert r.phi == pytest.approx(math.pi / 4 * r.kappa_c ** 2 * np.sum(D0 ** 2), rel=1e-12)
+    assert 0.8 < r.phi < 0.9
