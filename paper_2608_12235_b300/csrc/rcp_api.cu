@@ -469,8 +469,8 @@ rcp_status build_c(rcp_ctx* h)
         P = h->ctl_h->pair_cursor;
     }
     if (P >= (1ull << 32)) return fail(h, RCP_ERR_CAPACITY, "more than 2^32 listed pairs");
-    std::vector<int> ps = field_shifts(0, nbits);
-    for (int s : field_shifts(nbits, nbits)) ps.push_back(s);
+    // row and column fields are adjacent: 8-bit digits over all 2 nbits bits
+    std::vector<int> ps = field_shifts(0, 2 * nbits);
     const unsigned long long* spairs = nullptr;
     CKS(radix_sort(h, h->pairs1, nullptr, P, ps, h->pairs2, nullptr, h->pairs1, nullptr, &spairs, nullptr));
     h->launches += 1;
