@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("skin_abs", C.c_double), ("lr_x", C.c_double), ("lr_kappa", C.c_double),
                 ("delta_star0", C.c_double), ("tol", C.c_double), ("Y", C.c_int), ("X", C.c_int),
                 ("n_min", C.c_long), ("n_down", C.c_int), ("n_cycles", C.c_int),
-                ("max_iters", C.c_long)]
+                ("max_iters", C.c_long), ("kappa_init", C.c_double)]
 
 
 class Result(C.Structure):
@@ -141,12 +141,13 @@ def init_positions(seed: int, n: int, L=1.0, d: int = 3) -> np.ndarray:
     return x.reshape(n, d)
 
 
-def place(seed: int, D0, kappa: float, L=1.0, d: int = 3, max_rounds: int = 10000):
+def place(seed: int, D0, kappa: float, L=1.0, d: int = 3, max_rounds: int = 10000, x_frozen=None):
     """Non-overlapping placement by rounds of random sequential addition
-    (orc_place).  Returns (positions [n, d], round of each sphere, rounds or -1)."""
+    (orc_place).  Frozen spheres (D0 < 0) stay where x_frozen [n, d] has them.
+    Returns (positions [n, d], round of each sphere, rounds or -1)."""
     D0 = f64(D0)
     n = D0.size
-    x = np.zeros(n * d)
+    x = np.zeros(n * d) if x_frozen is None else f64(x_frozen).ravel().copy()
     rounds = np.zeros(n, dtype=np.int32)
     r = lib().orc_place(seed, n, d, _box(L, d), D0, kappa, max_rounds, x, rounds)
     return x.reshape(n, d), rounds, int(r)
@@ -322,6 +323,87 @@ def run(D0, seed=0, x0=None, trace_len=0, **params) -> RunResult:
     return RunResult(res.iters, res.rebuilds, bool(res.stopped), res.kappa, res.max_delta,
                      res.energy, res.kappa_c, res.phi, x.reshape(n, p.d),
                      tr.reshape(-1, 4)[: min(trace_len, res.iters + 1)] if tr is not None else None)
+
+
+# ---------------------------------------------------------------- the cascade
+def seated_state(fixed_d, fixed_x, D0, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, phi0=0.05):
+    """Initial state of a seated packing (Sec. IV: a finer class seated into
+    the voids of coarser spheres held fixed).  Spheres 0..nf-1 are frozen, with
+    contact diameters fixed_d and positions fixed_x (wrapped into the box);
+    spheres nf.. are mobile with relative diameters D0 and positions from the
+    uniform draw of the whole index range, or from placement among the frozen
+    ones at kappa_0 (placement = 1).  Returns (encoded D0 [n], x [n, d])."""
+    fixed_d = f64(fixed_d).ravel()
+    nf = fixed_d.size
+    Dall = np.concatenate([-fixed_d, f64(D0).ravel()])
+    n = Dall.size
+    box = _box(L, d)
+    x = init_positions(seed, n, L, d)
+    fx = f64(fixed_x).reshape(nf, d)
+    for i in range(nf):
+        for a in range(d):
+            x[i, a] = wrap(fx[i, a], box[a])
+    if placement:
+        k0 = kappa0(Dall, L, phi0, d)
+        x, _, r = place(seed, Dall, k0, L, d, place_rounds, x_frozen=x)
+        if r < 0:
+            raise RuntimeError("placement did not finish")
+    return Dall, x
+
+
+def cascade(D0, cls, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, **params):
+    """Sequential multimodal cascade (Sec. IV), one class at a time, class 0
+    first.  Stage 0 packs class 0 alone.  Stage s >= 1 seats class s among the
+    packed spheres, frozen at their contact diameters (seed + s, mobile
+    spheres in ascending caller index after the frozen ones, also in
+    ascending caller index), runs the protocol to the stop and shrinks to
+    contact; then releases every sphere: a packing of all of them at their
+    contact diameters, kappa starting at 1 (phi0 = the seated phi, so that
+    kappa_0 and its skin are of that scale), run to the stop and shrunk.  After
+    each stage the diameters are the contact diameters (kappa_c D).
+    Returns (x [n, d] in caller order, contact diameters [n], list of
+    (stage, phase, phi, iters))."""
+    D0 = f64(D0).ravel()
+    cls = np.asarray(cls).ravel()
+    n = D0.size
+    nclass = int(cls.max()) + 1
+    phi0 = params.pop("phi0", 0.05)
+    order = []          # caller indices of the packed spheres, in stage order
+    diam = None         # their contact diameters
+    xs = None           # their positions
+    log = []
+    for s_ in range(nclass):
+        new = np.flatnonzero(cls == s_)
+        if s_ == 0:
+            if placement:
+                k0 = kappa0(D0[new], L, phi0, d)
+                x0, _, r = place(seed, D0[new], k0, L, d, place_rounds)
+                if r < 0:
+                    raise RuntimeError("placement did not finish")
+            else:
+                x0 = None
+            res = run(D0[new], seed=seed, x0=x0, d=d, L=L, phi0=phi0, **params)
+            order = list(new)
+            diam = res.kappa_c * D0[new]
+            xs = res.x
+            log.append((0, "pack", res.phi, res.iters))
+            continue
+        Dall, x0 = seated_state(diam, xs, D0[new], seed + s_, L, d, placement, place_rounds, phi0)
+        res = run(Dall, seed=seed + s_, x0=x0, d=d, L=L, phi0=phi0, **params)
+        log.append((s_, "seat", res.phi, res.iters))
+        nf = diam.size
+        diam = np.concatenate([diam, res.kappa_c * D0[new]])
+        order = order + list(new)
+        res = run(diam, seed=seed + s_, x0=res.x, d=d, L=L, phi0=res.phi, kappa_init=1.0, **params)
+        log.append((s_, "release", res.phi, res.iters))
+        diam = res.kappa_c * diam
+        xs = res.x
+        assert nf + new.size == diam.size
+    x_out = np.zeros((n, d))
+    d_out = np.zeros(n)
+    x_out[order] = xs
+    d_out[order] = diam
+    return x_out, d_out, log
 
 
 def sample_iterations(D0, x, kappa, mu, eta_x, eta_k, sigma0, iters, **params) -> int:

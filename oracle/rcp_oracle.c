@@ -27,6 +27,15 @@
  *     implementation's, not the paper's k-d tree (App. A); the energy and the
  *     gradient never depend on it, because a pair that is listed but does not
  *     overlap contributes exactly nothing.
+ *   - frozen spheres, for the stages of the sequential cascade (Sec. IV: a
+ *     finer class is seated into the voids of the coarser ones and inflated
+ *     to contact while those are held fixed): an entry D0[i] < 0 marks sphere
+ *     i as frozen, with contact diameter -D0[i] that kappa does not scale and
+ *     a position that Adam does not move.  Its coordinates are constants of
+ *     the energy, not variables: their gradient is zero.  The growth term and
+ *     the moments that scale the schedule sum over the mobile spheres only.
+ *     The whole encoding is a reading; the paper describes the protocol, not
+ *     its arithmetic.
  */
 #include "rcp_oracle.h"
 #include <math.h>
@@ -36,6 +45,13 @@
 #define ORC_PI 3.141592653589793
 #define ORC_KMAX 32
 #define ORC_NMAX (1L << 19)
+
+/* Contact diameter of a sphere at scale kappa: kappa D^0 for a mobile sphere,
+ * the fixed -D0 for a frozen one (D0 < 0). */
+static double size_at(double D0, double kappa) { return D0 >= 0.0 ? kappa * D0 : -D0; }
+
+/* The part of D0 that kappa scales: D0 for a mobile sphere, 0 for a frozen one. */
+static double mobile_part(double D0) { return D0 > 0.0 ? D0 : 0.0; }
 
 /* ------------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014; Vigna's reference form): the
@@ -86,11 +102,13 @@ void orc_init_positions(uint64_t seed, long n, int d, const double* L, double* x
  * tested against every sphere.  attempt[i] (optional) receives the round in
  * which sphere i was placed.  Returns the largest number of rounds a class
  * took, or -1 if a class still has spheres unplaced after max_rounds (those
- * keep their last candidates). */
+ * keep their last candidates).  Frozen spheres (D0 < 0) count as placed from
+ * the start, at the positions x holds on entry; they never draw. */
 int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, double kappa, int max_rounds,
               double* x, int* attempt)
 {
     char* placed = (char*)calloc((size_t)n, 1);
+    for (long i = 0; i < n; ++i) placed[i] = D0[i] < 0.0;
     char* keep = (char*)malloc((size_t)n);
     int* cls = (int*)malloc(sizeof(int) * (size_t)n);
     double* rad = (double*)malloc(sizeof(double) * (size_t)n);
@@ -111,7 +129,7 @@ int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, d
     int worst = 0, failed = 0;
     for (int k = 0; k <= kmax && !failed; ++k) {
         long left = 0;
-        for (long i = 0; i < n; ++i) left += cls[i] == k;
+        for (long i = 0; i < n; ++i) left += cls[i] == k && !placed[i];
         int r = 0;
         for (; r < max_rounds && left > 0; ++r) {
             for (long i = 0; i < n; ++i) {
@@ -150,6 +168,8 @@ int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, d
         if (!placed[i]) {
             if (attempt) attempt[i] = -1;
             for (int a = 0; a < d; ++a) x[d * i + a] = cand[d * i + a];
+        } else if (D0[i] < 0.0 && attempt) {
+            attempt[i] = 0;
         }
     free(placed);
     free(keep);
@@ -188,15 +208,16 @@ double orc_cbrt(double a)
     return y;
 }
 
-/* out[0] = sum D, out[1] = sum D^3, out[2] = sum D^4 (tree sums). */
+/* out[0] = sum D, out[1] = sum D^3, out[2] = sum D^4 (tree sums) over the
+ * mobile spheres (a frozen sphere's term is 0). */
 void orc_moments(const double* D0, long n, double out[3])
 {
     double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    for (long i = 0; i < n; ++i) t[i] = D0[i];
+    for (long i = 0; i < n; ++i) t[i] = mobile_part(D0[i]);
     out[0] = orc_tree_sum(t, n);
-    for (long i = 0; i < n; ++i) t[i] = (D0[i] * D0[i]) * D0[i];
+    for (long i = 0; i < n; ++i) { double D = mobile_part(D0[i]); t[i] = (D * D) * D; }
     out[1] = orc_tree_sum(t, n);
-    for (long i = 0; i < n; ++i) t[i] = (D0[i] * D0[i]) * (D0[i] * D0[i]);
+    for (long i = 0; i < n; ++i) { double D = mobile_part(D0[i]); t[i] = (D * D) * (D * D); }
     out[2] = orc_tree_sum(t, n);
     free(t);
 }
@@ -206,16 +227,17 @@ static double box_volume(int d, const double* L)
     return d == 2 ? L[0] * L[1] : (L[0] * L[1]) * L[2];
 }
 
-/* kappa such that the solid-volume fraction of {kappa D_i^0} equals phi0. */
+/* kappa such that the solid-volume fraction of {kappa D_i^0} equals phi0
+ * (mobile spheres only: a frozen sphere's term is 0). */
 double orc_kappa0(const double* D0, long n, int d, const double* L, double phi0)
 {
     double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double V = box_volume(d, L), k;
     if (d == 2) {
-        for (long i = 0; i < n; ++i) t[i] = D0[i] * D0[i];
+        for (long i = 0; i < n; ++i) { double D = mobile_part(D0[i]); t[i] = D * D; }
         k = sqrt((phi0 * V) / ((ORC_PI / 4.0) * orc_tree_sum(t, n)));
     } else {
-        for (long i = 0; i < n; ++i) t[i] = (D0[i] * D0[i]) * D0[i];
+        for (long i = 0; i < n; ++i) { double D = mobile_part(D0[i]); t[i] = (D * D) * D; }
         k = orc_cbrt((phi0 * V) / ((ORC_PI / 6.0) * orc_tree_sum(t, n)));
     }
     free(t);
@@ -233,10 +255,10 @@ double orc_n_trig(long n, int d, int Y, int X)
  * rho_i = kappa_b D_i^0 (1/2 + s) + sigma0, i.e. half its diameter plus its
  * skin sigma_i = s kappa_b D_i^0 + sigma0.  A pair is listed iff its
  * minimum-image distance is below rho_i + rho_j = kappa_b d_ij^0 + sigma_i +
- * sigma_j. */
+ * sigma_j.  A frozen sphere has its fixed diameter in place of kappa_b D_i^0. */
 double orc_rho(double D0, double kappa_b, double s, double sigma0)
 {
-    return (kappa_b * D0) * (0.5 + s) + sigma0;
+    return size_at(D0, kappa_b) * (0.5 + s) + sigma0;
 }
 
 /* Minimum-image displacement x_i - x_j on every axis, squared distance
@@ -512,14 +534,17 @@ long orc_list_grid_occ(const double* x, const double* D0, long n, int d, const d
 }
 
 /* ------------------------------------------------------------------------ */
-/* One pair of Eq. energy.  delta = 1 - r/d with d = kappa (D_i^0 + D_j^0)/2.
- * Returns delta; fills the minimum-image displacement and r. */
+/* One pair of Eq. energy.  delta = 1 - r/d with d = kappa (D_i^0 + D_j^0)/2
+ * when both spheres are mobile; with a frozen one, d is the mean of the two
+ * contact diameters (size_at).  Returns delta; fills the minimum-image
+ * displacement and r. */
 static double pair_delta(const double* xi, const double* xj, double D0i, double D0j,
                          int d, const double* L, double kappa, double* dx, double* r, double* dd)
 {
     double r2 = min_image(xi, xj, d, L, dx);
     *r = sqrt(r2);
-    *dd = kappa * (0.5 * (D0i + D0j));
+    if (D0i > 0.0 && D0j > 0.0) *dd = kappa * (0.5 * (D0i + D0j));
+    else *dd = 0.5 * (size_at(D0i, kappa) + size_at(D0j, kappa));
     return 1.0 - *r / *dd;
 }
 
@@ -527,7 +552,10 @@ static double pair_delta(const double* xi, const double* xj, double D0i, double 
  * d E / d x_i = - sum_j eps delta_ij / (d_ij r_ij) (x_i - x_j)_mi; energy and
  * kappa-derivative take j > i only:
  *   e_i = sum eps/2 delta^2,  k_i = sum eps delta (1 - delta) / kappa,
- * the latter from d delta / d kappa = (1 - delta)/kappa. */
+ * the latter from d delta / d kappa = (1 - delta)/kappa.  With a frozen
+ * sphere in the pair, d d/d kappa = (mobile parts of D^0)/2 instead of d/kappa:
+ *   k_i += eps delta (1 - delta) (mobile D_i^0 + mobile D_j^0)/2 / d,
+ * and a frozen row takes no gradient (its coordinates are not variables). */
 typedef struct { double g[3], e, k, md; } rowacc;
 
 static void row_begin(rowacc* a) { a->g[0] = a->g[1] = a->g[2] = 0.0; a->e = a->k = a->md = 0.0; }
@@ -538,13 +566,16 @@ static void row_add(rowacc* a, long i, long j, const double* x, const double* D0
     double dx[3], r, dd;
     double delta = pair_delta(&x[d * i], &x[d * j], D0[i], D0[j], d, L, kappa, dx, &r, &dd);
     if (!(delta > 0.0)) return;
-    if (r > 0.0) {
+    if (r > 0.0 && D0[i] > 0.0) {
         double coef = (eps * delta) / (dd * r);
         for (int c = 0; c < d; ++c) a->g[c] = a->g[c] - coef * dx[c];
     }
     if (j > i) {
         a->e = a->e + (0.5 * eps) * (delta * delta);
-        a->k = a->k + ((eps * delta) * (1.0 - delta)) / kappa;
+        if (D0[i] > 0.0 && D0[j] > 0.0)
+            a->k = a->k + ((eps * delta) * (1.0 - delta)) / kappa;
+        else
+            a->k = a->k + (((eps * delta) * (1.0 - delta)) * (0.5 * (mobile_part(D0[i]) + mobile_part(D0[j])))) / dd;
     }
     if (delta > a->md) a->md = delta;
 }
@@ -552,7 +583,10 @@ static void row_add(rowacc* a, long i, long j, const double* x, const double* D0
 static void finish_sums(const double* e, const double* k, const double* D0, long n,
                         double kappa, double mu, double* E, double* dEdk)
 {
-    double SD = orc_tree_sum(D0, n);
+    double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (long i = 0; i < n; ++i) t[i] = mobile_part(D0[i]);
+    double SD = orc_tree_sum(t, n);
+    free(t);
     double Se = orc_tree_sum(e, n);
     double Sk = orc_tree_sum(k, n);
     if (E) *E = Se - mu * (kappa * SD);
@@ -648,7 +682,11 @@ void orc_adam_update(double* p, double* m, double* v, const double* g, long n,
  * and min_{i<j} r_ij / d_ij^0 (a pair touching exactly does not overlap).
  * Reading: that quotient is rounded, so the result is lowered by the factor
  * (1 - 2^-50) -- a few units in the last place -- which guarantees that a
- * binary64 re-evaluation at kappa_c finds no overlap at all. */
+ * binary64 re-evaluation at kappa_c finds no overlap at all.
+ * A pair with one frozen sphere (fixed diameter F) touches at
+ * kappa = (r - F/2) / (D_a^0 / 2); the subtraction can cancel bits, so that
+ * quotient is lowered by (1 - 2^-40) first, and clamped at 0.  Two frozen
+ * spheres do not depend on kappa and set no bound. */
 double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const double* L,
                         double kappa, const long* rowptr, const int* col)
 {
@@ -659,25 +697,48 @@ double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const 
             if (j <= i) continue;
             double dx[3];
             double r = sqrt(min_image(&x[d * i], &x[d * j], d, L, dx));
-            double q = r / (0.5 * (D0[i] + D0[j]));
+            double q;
+            if (D0[i] > 0.0 && D0[j] > 0.0) {
+                q = r / (0.5 * (D0[i] + D0[j]));
+            } else if (D0[i] > 0.0 || D0[j] > 0.0) {
+                double Da = D0[i] > 0.0 ? D0[i] : D0[j];
+                double F = D0[i] > 0.0 ? -D0[j] : -D0[i];
+                q = ((r - 0.5 * F) / (0.5 * Da)) * (1.0 - 0x1.0p-40);
+                if (q < 0.0) q = 0.0;
+            } else {
+                continue;
+            }
             if (q < kc) kc = q;
         }
     return kc * (1.0 - 0x1.0p-50);
 }
 
-/* Solid-volume fraction of spheres (disks for d = 2) of diameters kappa D^0. */
+/* Solid-volume fraction of spheres (disks for d = 2) of diameters kappa D^0;
+ * frozen spheres add their fixed volumes:
+ *   phi = ((pi/6) kappa^3 sum_mobile D^3 + (pi/6) sum_frozen F^3) / V. */
 double orc_phi(const double* D0, long n, int d, const double* L, double kappa)
 {
     double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* f = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double V = box_volume(d, L), phi;
     if (d == 2) {
-        for (long i = 0; i < n; ++i) t[i] = D0[i] * D0[i];
-        phi = (((ORC_PI / 4.0) * (kappa * kappa)) * orc_tree_sum(t, n)) / V;
+        for (long i = 0; i < n; ++i) {
+            double D = mobile_part(D0[i]), F = mobile_part(-D0[i]);
+            t[i] = D * D;
+            f[i] = F * F;
+        }
+        phi = ((((ORC_PI / 4.0) * (kappa * kappa)) * orc_tree_sum(t, n)) + (ORC_PI / 4.0) * orc_tree_sum(f, n)) / V;
     } else {
-        for (long i = 0; i < n; ++i) t[i] = (D0[i] * D0[i]) * D0[i];
-        phi = (((ORC_PI / 6.0) * ((kappa * kappa) * kappa)) * orc_tree_sum(t, n)) / V;
+        for (long i = 0; i < n; ++i) {
+            double D = mobile_part(D0[i]), F = mobile_part(-D0[i]);
+            t[i] = (D * D) * D;
+            f[i] = (F * F) * F;
+        }
+        phi = ((((ORC_PI / 6.0) * ((kappa * kappa) * kappa)) * orc_tree_sum(t, n)) + (ORC_PI / 6.0) * orc_tree_sum(f, n)) /
+              V;
     }
     free(t);
+    free(f);
     return phi;
 }
 
@@ -710,11 +771,13 @@ void orc_params_default(orc_params* p)
 /* Rebuild test (the list criterion above): a pair listed at kappa_b with
  * margin sigma_i + sigma_j stays non-overlapping while every sphere keeps
  * |x_i - x_i^b| + (kappa - kappa_b) D_i^0 / 2 <= theta sigma_i, theta <= 1.
- * Returns 1 if some sphere broke it (1e-9 margins cover rounding). */
+ * Returns 1 if some sphere broke it (1e-9 margins cover rounding).  A frozen
+ * sphere neither moves nor grows and never breaks it. */
 static int skin_spent(const double* x, const double* xb, const double* D0, long n, int d, const double* L,
                       double kappa, double kb, double s, double th, double sigma0)
 {
     for (long i = 0; i < n; ++i) {
+        if (!(D0[i] > 0.0)) continue;
         double dx[3];
         double disp = sqrt(min_image(&x[d * i], &xb[d * i], d, L, dx)) * (1.0 + 1e-9);
         double sig = th * (s * kb * D0[i] + sigma0) * (1.0 - 1e-9);
@@ -751,6 +814,17 @@ static int build_rungs(const orc_params* p, long n, rung* R, int cap)
     }
     R[c].dstar = 0.0; R[c].lrs = lrs * 0.5; R[c].budget = p->max_iters; R[c].final = 1; ++c;
     return c;
+}
+
+/* Adam on the coordinates of the mobile spheres; frozen ones keep their
+ * positions and moments. */
+static void adam_positions(double* x, double* m, double* v, const double* g, const double* D0, long n, int d,
+                           double eta, const orc_params* p, double b1, double b2)
+{
+    for (long i = 0; i < n; ++i)
+        if (D0[i] > 0.0)
+            orc_adam_update(&x[d * i], &m[d * i], &v[d * i], &g[d * i], d, eta, p->beta1, p->beta2, p->adam_eps, b1,
+                            b2);
 }
 
 static long build_list(const double* x, const double* D0, long n, int d, const double* L,
@@ -794,13 +868,16 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
     double Neff = SD3 / ((Dref * Dref) * Dref);
     double kappa = orc_kappa0(D0, n, d, L, p->phi0);
     double sigma0 = p->skin_abs * ((p->lr_x * kappa) * Dref);
+    if (p->kappa_init > 0.0) kappa = p->kappa_init;   /* sigma0 stays that of kappa_0 */
     double mk = 0.0, vk = 0.0, b1 = 1.0, b2 = 1.0;
     double s = p->skin_s, th = p->skin_theta;
     double Lmin = L[0];
     for (int a = 1; a < d; ++a) if (L[a] < Lmin) Lmin = L[a];
 
+    long n_mobile = 0;
+    for (long i = 0; i < n; ++i) n_mobile += D0[i] > 0.0;
     rung R[64];
-    int nr = build_rungs(p, n, R, 60);
+    int nr = build_rungs(p, n_mobile, R, 60);
     long it = 0, rebuilds = 0;
     int need = 1, stopped = 0, status = 0;
     double kb = kappa, E = 0.0, md = 0.0, dEdk = 0.0;
@@ -833,7 +910,7 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
             if (R[r].final && md < p->tol) { stopped = 1; break; }
             b1 = b1 * p->beta1;
             b2 = b2 * p->beta2;
-            orc_adam_update(x, m, v, g, nd, eta_x, p->beta1, p->beta2, p->adam_eps, b1, b2);
+            adam_positions(x, m, v, g, D0, n, d, eta_x, p, b1, b2);
             for (long i = 0; i < n; ++i)
                 for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
             orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);
@@ -901,7 +978,7 @@ long orc_sample_iterations(const orc_params* p, const double* D0, long n, double
         orc_energy_grad_list(x, D0, n, d, L, kappa, mu, p->eps, rowptr, col, &E, g, &dEdk, &md);
         b1 = b1 * p->beta1;
         b2 = b2 * p->beta2;
-        orc_adam_update(x, m, v, g, nd, eta_x, p->beta1, p->beta2, p->adam_eps, b1, b2);
+        adam_positions(x, m, v, g, D0, n, d, eta_x, p, b1, b2);
         for (long i = 0; i < n; ++i)
             for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
         orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);

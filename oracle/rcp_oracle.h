@@ -44,6 +44,8 @@ typedef struct {
     int    n_down;       /* number of rungs after the first (mu / 10 each) */
     int    n_cycles;     /* mu cycles after the descent */
     long   max_iters;    /* safety cap on the total iteration count */
+    double kappa_init;   /* > 0: start the run at this kappa instead of kappa_0
+                            (sigma0 is still that of kappa_0); 0: kappa_0 */
 } orc_params;
 
 typedef struct {
@@ -56,6 +58,10 @@ typedef struct {
     double kappa_c;      /* shrink-to-contact kappa */
     double phi;          /* shrink-to-contact packing fraction */
 } orc_result;
+
+/* Frozen spheres (stages of the sequential cascade, Sec. IV): wherever a
+ * function takes D0, an entry D0[i] < 0 marks sphere i as frozen, with fixed
+ * contact diameter -D0[i] and a position that the run does not move. */
 
 /* ---- input-side primitives ---- */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
