@@ -243,6 +243,58 @@ long long rcp_size(rcp_handle h);
 /* Dimension d given at creation (2 or 3; 0 for NULL). */
 int rcp_dim(rcp_handle h);
 
+/* ---- the sequential multimodal cascade (Sec. IV) ----
+ * The paper packs a multimodal grading class by class, coarsest first: the
+ * finer class is seated into the voids of the packed coarser spheres and
+ * inflated to contact with those held fixed, then everything is released and
+ * relaxed together, and so on down the classes.  The calls below give the
+ * "held fixed" part: frozen spheres keep their positions and a contact
+ * diameter that kappa does not scale.  Binary64 path only. */
+
+/* Create a seated packing: Nf >= 1 frozen spheres (internal indices
+ * 0..Nf-1) and N >= 1 mobile ones (indices Nf..Nf+N-1; every array of the
+ * other calls has Nf + N rows in that order).
+ *   fixed_d: host [Nf] contact diameters F_i > 0 of the frozen spheres;
+ *   fixed_x: host [Nf][d] their positions (wrapped into the box);
+ *   diameters: host [N] relative diameters D_i^0 of the mobile spheres;
+ *   d, box, seed: as for rcp_create (the uniform draw covers all Nf + N
+ *         indices; the frozen rows are then replaced by fixed_x);
+ *   cfg: required, precision RCP_FP64 (else RCP_ERR_UNSUPPORTED).
+ * Pairs with a frozen sphere have d_ij = (F_i + kappa D_j^0)/2 (or (F_i +
+ * F_j)/2), so dE/dkappa takes (mobile D^0)/2 from them; a frozen sphere's
+ * gradient is zero and Adam does not move it; the growth term -mu kappa sum
+ * D^0, the moments that scale the schedule (D_ref, N_eff), kappa_0 (phi0 of
+ * the mobile spheres alone) and the rung budgets (Eq. trigger with the mobile
+ * count) take the mobile spheres only; cfg->placement = 1 places the mobile
+ * spheres around the frozen ones, which count as placed from the start.
+ * Shrink to contact bounds kappa by every pair with a mobile sphere (a pair
+ * with a frozen one touches at kappa = (r - F/2)/(D^0/2), lowered by
+ * (1 - 2^-40)); phi adds the frozen spheres' fixed volumes. */
+rcp_status rcp_create_seated(const double* fixed_d, const double* fixed_x, long long Nf, const double* diameters,
+                             long long N, int d, const double* box, unsigned long long seed,
+                             const rcp_config* cfg, rcp_handle* out);
+
+/* Number of frozen spheres (0 for rcp_create handles and NULL). */
+long long rcp_frozen(rcp_handle h);
+
+/* The whole cascade.  cls[i] in 0..C-1 is the class of sphere i (class 0
+ * first; every class non-empty).  Stage 0 packs class 0 alone (rcp_create,
+ * seed).  Stage s >= 1 seats class s (rcp_create_seated with seed + s, the
+ * packed spheres frozen in ascending caller index, then the class in
+ * ascending caller index), runs it to the stop and shrinks it; then releases
+ * every sphere: rcp_create of the contact diameters with phi0 = the seated
+ * phi and placement off, positions from the seated run with kappa = 1, run to
+ * the stop and shrunk.  After each stage the diameters are the contact
+ * diameters kappa_c D.  cfg: required, RCP_FP64.
+ *   x_out: host [N][d] final positions, diam_out: host [N] final contact
+ *   diameters (caller order); phi_out, iters_out (may be NULL): host [2C-1]
+ *   phi and Adam steps of the stages in order: pack, seat 1, release 1,
+ *   seat 2, release 2, ...
+ * Returns RCP_ERR_MAXITER if a stage does not reach the stopping criterion. */
+rcp_status rcp_cascade(const double* diameters, const int* cls, long long N, int d, const double* box,
+                       unsigned long long seed, const rcp_config* cfg, double* x_out, double* diam_out,
+                       double* phi_out, long long* iters_out);
+
 /* ---- batches: many independent packings in one graph of batched kernels ---- */
 typedef struct rcp_batch_ctx* rcp_batch;
 

@@ -35,6 +35,7 @@ struct DevBuf {
 
 struct rcp_ctx {
     long long N = 0;
+    long long n_mobile = 0;   // spheres Adam moves (N minus the frozen ones)
     rcp_config cfg;
     RcpConst c;
     unsigned long long seed = 0;
@@ -640,7 +641,7 @@ rcp_status capture_graph(rcp_ctx* h)
 void build_rungs(rcp_ctx* h)
 {
     const rcp_config& p = h->cfg;
-    double nt = (4000.0 * (double)p.Y + (double)p.X * std::sqrt((double)(h->N * (long long)h->c.dim))) - 2000.0;
+    double nt = (4000.0 * (double)p.Y + (double)p.X * std::sqrt((double)(h->n_mobile * (long long)h->c.dim))) - 2000.0;
     long long b0 = (long long)std::ceil(nt);
     if (b0 < p.n_min) b0 = p.n_min;
     long long bq = (long long)std::ceil(nt / 4.0);
@@ -773,6 +774,8 @@ rcp_status place_nonoverlapping(rcp_ctx* h, unsigned long long seed)
     h->placing = true;
     rcp_status st = [&]() -> rcp_status {
         CK(cudaMemsetAsync(placed, 0, (size_t)N, h->stream));
+        // frozen spheres are in place before any class is drawn
+        if (h->c.nfrozen > 0) CK(cudaMemsetAsync(placed, 1, (size_t)h->c.nfrozen, h->stream));
         CKS(build_a(h));   // the classes (they depend on D^0 and kappa_0 only)
         CK(cudaStreamSynchronize(h->stream));
         const int nlev = h->ctl_h->nlev;
@@ -817,22 +820,41 @@ rcp_status place_nonoverlapping(rcp_ctx* h, unsigned long long seed)
 }
 
 
-rcp_status rcp_create(const double* diameters, long long N, int d, const double* box, unsigned long long seed,
-                      const rcp_config* cfg, rcp_handle* out)
+}  // extern "C"
+
+namespace {
+
+// Creation of a packing of Nf frozen spheres (contact diameters fixed_d,
+// positions fixed_x [Nf][d]; internal indices 0..Nf-1) and Nm mobile ones
+// (relative diameters `diameters`; indices Nf..).  Nf = 0 is rcp_create.
+rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long Nf, const double* diameters,
+                       long long Nm, int d, const double* box, unsigned long long seed, const rcp_config* cfg,
+                       rcp_handle* out)
 {
     if (!out) return RCP_ERR_ARG;
     *out = nullptr;
-    if (!diameters || !box || N < 1) return RCP_ERR_ARG;
+    if (!diameters || !box || Nm < 1 || Nf < 0 || (Nf > 0 && (!fixed_d || !fixed_x))) return RCP_ERR_ARG;
     if (d != 2 && d != 3) return RCP_ERR_UNSUPPORTED;
-    if (N >= (1LL << 31)) return RCP_ERR_ARG;
+    if (Nf >= (1LL << 31) || Nm >= (1LL << 31) - Nf) return RCP_ERR_ARG;
+    if (Nf > 0 && cfg && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
+    const long long N = Nf + Nm;
+    for (long long i = 0; i < Nf; ++i) {
+        if (!(fixed_d[i] > 0.0) || !std::isfinite(fixed_d[i])) return RCP_ERR_ARG;
+        for (int a = 0; a < d; ++a)
+            if (!std::isfinite(fixed_x[(size_t)d * i + a])) return RCP_ERR_ARG;
+    }
     for (int a = 0; a < d; ++a)
         if (!(box[a] > 0.0) || !std::isfinite(box[a])) return RCP_ERR_ARG;
     // d = 2: disks held in the plane z = L_z / 2 of a box whose third edge is
     // the larger of the two (every z difference is exactly zero)
     const double box3[3] = {box[0], box[1], d == 3 ? box[2] : (box[0] > box[1] ? box[0] : box[1])};
     box = box3;
-    for (long long i = 0; i < N; ++i)
+    for (long long i = 0; i < Nm; ++i)
         if (!(diameters[i] > 0.0) || !std::isfinite(diameters[i])) return RCP_ERR_ARG;
+    // device encoding: -F for a frozen sphere, D^0 for a mobile one
+    std::vector<double> Dh((size_t)N);
+    for (long long i = 0; i < Nf; ++i) Dh[(size_t)i] = -fixed_d[i];
+    for (long long i = 0; i < Nm; ++i) Dh[(size_t)(Nf + i)] = diameters[i];
     rcp_ctx* h = new rcp_ctx();
     if (cfg) h->cfg = *cfg;
     else rcp_config_default(&h->cfg);
@@ -843,10 +865,12 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         return RCP_ERR_ARG;
     }
     h->N = N;
+    h->n_mobile = Nm;
     h->seed = seed;
     RcpConst& c = h->c;
     memset(&c, 0, sizeof(c));
     c.N = N;
+    c.nfrozen = Nf;
     c.Lmin = box[0];
     c.Lmax = box[0];
     for (int a = 0; a < 3; ++a) {
@@ -954,15 +978,25 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         init.shrink_bits = 0x7FF0000000000000ull;
         init.iter_limit = 0;
         CK(cudaMemcpyAsync(h->ctl, &init, sizeof(RcpCtl), cudaMemcpyHostToDevice, h->stream));
-        CK(cudaMemcpyAsync(h->D0, diameters, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->D0, Dh.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
         const unsigned int nb = rcp_ceil_div(N, 256);
         h->launches += 1;
         k_init_positions<<<nb, 256, 0, h->stream>>>(seed, N, c, h->D0, h->xA);
         CKL();
+        if (Nf > 0) {   // the frozen spheres where the caller holds them
+            CK(cudaMemcpyAsync(h->xtmp, fixed_x, sizeof(double) * d * (size_t)Nf, cudaMemcpyHostToDevice, h->stream));
+            h->launches += 1;
+            k_set_positions<<<rcp_ceil_div(Nf, 256), 256, 0, h->stream>>>(Nf, c, h->xtmp, h->D0, h->xA, nullptr);
+            CKL();
+        }
         CKS(tree_sum_D(h, 1, &h->ctl->SD));
         CKS(tree_sum_D(h, 3, &h->ctl->SD3));
         if (d == 2) CKS(tree_sum_D(h, 2, &h->ctl->SD2));
         CKS(tree_sum_D(h, 4, &h->ctl->SD4));
+        if (Nf > 0) {
+            CKS(tree_sum_D(h, -3, &h->ctl->SF3));
+            if (d == 2) CKS(tree_sum_D(h, -2, &h->ctl->SF2));
+        }
         h->launches += 1;
         k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.V, d);
         CKL();
@@ -988,6 +1022,109 @@ rcp_status rcp_create(const double* diameters, long long N, int d, const double*
         return st;
     }
     *out = h;
+    return RCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rcp_status rcp_create(const double* diameters, long long N, int d, const double* box, unsigned long long seed,
+                      const rcp_config* cfg, rcp_handle* out)
+{
+    return create_impl(nullptr, nullptr, 0, diameters, N, d, box, seed, cfg, out);
+}
+
+rcp_status rcp_create_seated(const double* fixed_d, const double* fixed_x, long long Nf, const double* diameters,
+                             long long N, int d, const double* box, unsigned long long seed, const rcp_config* cfg,
+                             rcp_handle* out)
+{
+    if (Nf < 1) return RCP_ERR_ARG;
+    if (out) *out = nullptr;
+    if (!cfg || cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
+    return create_impl(fixed_d, fixed_x, Nf, diameters, N, d, box, seed, cfg, out);
+}
+
+long long rcp_frozen(rcp_handle h) { return h ? h->c.nfrozen : 0; }
+
+// The sequential cascade (Sec. IV) through the calls above: stage 0 packs
+// class 0; stage s seats class s among the packed spheres (frozen at their
+// contact diameters, seed + s), runs it to the stop, shrinks it, then
+// releases all of them (a packing of the contact diameters, phi0 = the seated
+// phi, kappa set to 1, placement off) and runs and shrinks that.
+rcp_status rcp_cascade(const double* diameters, const int* cls, long long N, int d, const double* box,
+                       unsigned long long seed, const rcp_config* cfg, double* x_out, double* diam_out,
+                       double* phi_out, long long* iters_out)
+{
+    if (!diameters || !cls || !box || N < 1 || !x_out || !diam_out) return RCP_ERR_ARG;
+    if (!cfg || cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
+    int C = 0;
+    for (long long i = 0; i < N; ++i) {
+        if (cls[i] < 0) return RCP_ERR_ARG;
+        if (cls[i] + 1 > C) C = cls[i] + 1;
+    }
+    std::vector<std::vector<long long>> members((size_t)C);
+    for (long long i = 0; i < N; ++i) members[(size_t)cls[i]].push_back(i);
+    for (int s = 0; s < C; ++s)
+        if (members[(size_t)s].empty()) return RCP_ERR_ARG;
+    std::vector<long long> order;   // caller index of each packed sphere, stage order
+    std::vector<double> diam, xs;    // their contact diameters and positions
+    rcp_stop stop = {0, 0.0, 1};
+    int slot = 0;
+    auto finish = [&](rcp_handle h, const rcp_result& r, long long n) -> rcp_status {
+        if (!r.stopped) return RCP_ERR_MAXITER;
+        xs.assign((size_t)(n * d), 0.0);
+        rcp_status st = rcp_state(h, xs.data(), nullptr, nullptr, nullptr);
+        if (st != RCP_OK) return st;
+        if (phi_out) phi_out[slot] = r.phi;
+        if (iters_out) iters_out[slot] = r.iters;
+        ++slot;
+        return RCP_OK;
+    };
+    for (int s = 0; s < C; ++s) {
+        const std::vector<long long>& nw = members[(size_t)s];
+        std::vector<double> Dn(nw.size());
+        for (size_t t = 0; t < nw.size(); ++t) Dn[t] = diameters[nw[t]];
+        const long long nn = (long long)nw.size();
+        rcp_handle h = nullptr;
+        rcp_result r;
+        rcp_status st;
+        if (s == 0) {
+            st = rcp_create(Dn.data(), nn, d, box, seed, cfg, &h);
+            if (st == RCP_OK) st = rcp_run(h, &stop, &r);
+            if (st == RCP_OK) st = finish(h, r, nn);
+            rcp_destroy(h);
+            if (st != RCP_OK) return st;
+            order = nw;
+            diam.resize(Dn.size());
+            for (size_t t = 0; t < Dn.size(); ++t) diam[t] = r.kappa_c * Dn[t];
+            continue;
+        }
+        const long long nf = (long long)diam.size();
+        st = rcp_create_seated(diam.data(), xs.data(), nf, Dn.data(), nn, d, box, seed + (unsigned long long)s, cfg,
+                               &h);
+        if (st == RCP_OK) st = rcp_run(h, &stop, &r);
+        if (st == RCP_OK) st = finish(h, r, nf + nn);
+        rcp_destroy(h);
+        if (st != RCP_OK) return st;
+        for (size_t t = 0; t < Dn.size(); ++t) diam.push_back(r.kappa_c * Dn[t]);
+        order.insert(order.end(), nw.begin(), nw.end());
+        rcp_config rc = *cfg;
+        rc.phi0 = r.phi;
+        rc.placement = 0;
+        h = nullptr;
+        st = rcp_create(diam.data(), nf + nn, d, box, seed + (unsigned long long)s, &rc, &h);
+        if (st == RCP_OK) st = rcp_set_positions(h, xs.data(), 1.0, 0);
+        if (st == RCP_OK) st = rcp_run(h, &stop, &r);
+        if (st == RCP_OK) st = finish(h, r, nf + nn);
+        rcp_destroy(h);
+        if (st != RCP_OK) return st;
+        for (double& v : diam) v = r.kappa_c * v;
+    }
+    for (size_t t = 0; t < order.size(); ++t) {
+        diam_out[order[t]] = diam[t];
+        for (int a = 0; a < d; ++a) x_out[(size_t)d * order[t] + a] = xs[(size_t)d * t + a];
+    }
     return RCP_OK;
 }
 

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_rho(RcpCtl* ctl, RcpConst c, const doub
     double r = 0.0;
     if (i < c.N) {
         const double4_32a p = (ctl->parity ? xB : xA)[i];
-        r = (ctl->kappa_b * p.w) * (0.5 + c.skin_s) + ctl->sigma0;
+        r = size_at(p.w, ctl->kappa_b) * (0.5 + c.skin_s) + ctl->sigma0;   // frozen: fixed diameter
         rho[i] = r;
         xf[i] = make_float4((float)(p.x * c.invL[0]), (float)(p.y * c.invL[1]), (float)(p.z * c.invL[2]), (float)r);
     }
@@ -428,7 +428,10 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
         const float Eabs = (float)(5e-7 * c.Lmax);
         const float up = 1.0f + 2e-6f, dn = 1.0f - 2e-6f;
         const float u3[3] = {ui.x, ui.y, ui.z};
-        for (int k = 0; k <= li; ++k) {
+        // a placement candidate also meets frozen spheres of finer classes,
+        // which are placed before any class is
+        const int kend = (PLACE && c.nfrozen > 0) ? ctl->nlev - 1 : li;
+        for (int k = 0; k <= kend; ++k) {
             const double rk = ctl->rho_lvl[k];
             if (!(rk > 0.0)) continue;
             int lo[3];

@@ -63,7 +63,8 @@ struct RcpCtl {
     unsigned long long pairs;
     unsigned int n_long;      // rows longer than RCP_LONG_ROW
     // constants and one-off results
-    double SD, SD2, SD3, SD4;
+    double SD, SD2, SD3, SD4;   // moments of the mobile spheres' D^0
+    double SF2, SF3;            // sums of F^2 and F^3 over the frozen spheres
     unsigned long long shrink_bits;
     unsigned long long md64_bits;
     double kappa_c, phi;
@@ -92,6 +93,7 @@ struct RcpConst {
     int dim;                   // the caller's dimension: 3, or 2 (disks held in the plane z = L_z / 2)
     unsigned int long_row;     // rows longer than this get a warp (mixed)
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
+    long long nfrozen;         // frozen spheres (binary64 path only; 0 otherwise)
 };
 
 // Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
@@ -119,6 +121,14 @@ struct PackDev {
 };
 
 enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
+
+// ---- frozen spheres ----
+// A stage of the sequential cascade (Sec. IV) holds the coarser classes
+// fixed while a finer class is inflated among them.  A negative D0 = -F marks
+// such a frozen sphere: its contact diameter is F whatever kappa is, Adam
+// does not move it, and its coordinates carry no gradient.
+__device__ __forceinline__ double size_at(double D0, double kappa) { return D0 >= 0.0 ? kappa * D0 : -D0; }
+__device__ __forceinline__ double mobile_part(double D0) { return D0 > 0.0 ? D0 : 0.0; }
 
 // ---- small helpers ----
 #define RCP_KBUD_INF 0x7F800000u

@@ -133,14 +133,17 @@ __device__ __forceinline__ double block_max(double v, double* sh)
 }
 
 // Terms D, D^3 = (D D) D, D^4 = (D D)(D D) of the moment sums, one tree of
-// RCP_TREE consecutive terms per block.
+// RCP_TREE consecutive terms per block.  A positive power takes the mobile
+// spheres' D^0 (a frozen sphere's term is 0), a negative one the frozen
+// spheres' fixed diameters F (a mobile sphere's term is 0).
 __global__ void __launch_bounds__(RCP_TREE) k_tree_terms(const double* D0, long long N, int power, double* out)
 {
     __shared__ double sh[32];
     long long i = (long long)blockIdx.x * RCP_TREE + threadIdx.x;
     double v = 0.0;
     if (i < N) {
-        double D = D0[i];
+        double D = power > 0 ? mobile_part(D0[i]) : mobile_part(-D0[i]);
+        if (power < 0) power = -power;
         if (power == 1) v = D;
         else if (power == 2) v = D * D;
         else if (power == 3) v = (D * D) * D;
@@ -396,10 +399,11 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
             double dz = min_image(xi.z - xj.z, c.L[2], c.halfL[2]);
             double r2 = dx * dx + dy * dy + dz * dz;
             double r = sqrt(r2);
-            double dd = kappa * (0.5 * (xi.w + xj.w));
+            const bool both = xi.w > 0.0 && xj.w > 0.0;   // no frozen sphere in the pair
+            double dd = both ? kappa * (0.5 * (xi.w + xj.w)) : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
             double delta = 1.0 - r / dd;
             if (delta > 0.0) {
-                if (r > 0.0) {
+                if (r > 0.0 && xi.w > 0.0) {
                     double coef = (c.eps * delta) / (dd * r);
                     g0 = g0 - coef * dx;
                     g1 = g1 - coef * dy;
@@ -407,12 +411,17 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
                 }
                 if ((long long)j > i) {
                     e = e + (0.5 * c.eps) * (delta * delta);
-                    k = k + ((c.eps * delta) * (1.0 - delta)) / kappa;
+                    if (both)
+                        k = k + ((c.eps * delta) * (1.0 - delta)) / kappa;
+                    else   // d d / d kappa = (mobile D_i^0 + mobile D_j^0) / 2
+                        k = k + (((c.eps * delta) * (1.0 - delta)) * (0.5 * (mobile_part(xi.w) + mobile_part(xj.w)))) / dd;
                 }
                 if (delta > md) md = delta;
             }
         }
-        if (mode == RCP_MODE_ADAM) {
+        if (mode == RCP_MODE_ADAM && !(xi.w > 0.0)) {
+            xout[i] = xi;   // frozen: position and moments stay
+        } else if (mode == RCP_MODE_ADAM) {
             const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
             const double h1 = 1.0 - b1, h2 = 1.0 - b2;
             const double eta = ctl->eta_x;
@@ -598,7 +607,7 @@ __global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* 
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float bud = INFINITY;
-    if (i < c.N) {
+    if (i < c.N && (ctl->parity ? xB : xA)[i].w > 0.0) {   // frozen spheres stay
         double4_32a* x = ctl->parity ? xB : xA;
         const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
         const double h1 = 1.0 - b1, h2 = 1.0 - b2;
@@ -643,6 +652,7 @@ __global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, con
     if (i >= c.N) return;
     const double4_32a* x = ctl->parity ? xB : xA;
     const double4_32a p = x[i], b = xb[i];
+    if (!(p.w > 0.0)) return;   // a frozen sphere neither moves nor grows
     double dx = min_image(p.x - b.x, c.L[0], c.halfL[0]);
     double dy = min_image(p.y - b.y, c.L[1], c.halfL[1]);
     double dz = min_image(p.z - b.z, c.L[2], c.halfL[2]);
@@ -653,7 +663,10 @@ __global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, con
 
 // ---------------------------------------------------------------------------
 // Shrink to contact: min over listed pairs i < j of r_ij / d_ij^0 (order-free
-// minimum through the bit pattern of a non-negative double).
+// minimum through the bit pattern of a non-negative double).  A pair with one
+// frozen sphere (diameter F) touches at kappa = (r - F/2) / (D_a^0 / 2),
+// lowered by (1 - 2^-40) for the bits the subtraction may cancel and clamped
+// at 0; two frozen spheres set no bound.
 __global__ void __launch_bounds__(RCP_PAIR_THREADS)
 k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
          const unsigned int* rowptr, const unsigned int* col)
@@ -672,7 +685,17 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
             double dy = min_image(xi.y - xj.y, c.L[1], c.halfL[1]);
             double dz = min_image(xi.z - xj.z, c.L[2], c.halfL[2]);
             double r = sqrt(dx * dx + dy * dy + dz * dz);
-            double qq = r / (0.5 * (xi.w + xj.w));
+            double qq;
+            if (xi.w > 0.0 && xj.w > 0.0) {
+                qq = r / (0.5 * (xi.w + xj.w));
+            } else if (xi.w > 0.0 || xj.w > 0.0) {
+                const double Da = xi.w > 0.0 ? xi.w : xj.w;
+                const double F = xi.w > 0.0 ? -xj.w : -xi.w;
+                qq = ((r - 0.5 * F) / (0.5 * Da)) * (1.0 - 0x1.0p-40);
+                if (qq < 0.0) qq = 0.0;
+            } else {
+                continue;
+            }
             if (qq < q) q = qq;
         }
     }
@@ -683,7 +706,7 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
 
 // kappa_c = min(kappa, q_min) (1 - 2^-50): lowered by a few units in the
 // last place so that no pair overlaps when re-evaluated in binary64;
-// phi = (pi/6) kappa_c^3 sum D^3 / V.
+// phi = ((pi/6) kappa_c^3 sum D^3 + (pi/6) sum_frozen F^3) / V.
 __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c)
 {
     double q = bitsd(ctl->shrink_bits);
@@ -691,6 +714,6 @@ __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c)
     if (q < kc) kc = q;
     kc = kc * (1.0 - 0x1.0p-50);
     ctl->kappa_c = kc;
-    if (c.dim == 2) ctl->phi = (((RCP_PI / 4.0) * (kc * kc)) * ctl->SD2) / c.V;
-    else ctl->phi = (((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) / c.V;
+    if (c.dim == 2) ctl->phi = ((((RCP_PI / 4.0) * (kc * kc)) * ctl->SD2) + (RCP_PI / 4.0) * ctl->SF2) / c.V;
+    else ctl->phi = ((((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) + (RCP_PI / 6.0) * ctl->SF3) / c.V;
 }

@@ -25,7 +25,7 @@ EXPORTS = ["rcp_config_default", "rcp_create", "rcp_destroy", "rcp_set_stream", 
            "rcp_build_neighbors", "rcp_energy_grad", "rcp_energy_grad_at", "rcp_adam_step", "rcp_run", "rcp_profile", "rcp_shrink", "rcp_state",
            "rcp_load_state", "rcp_neighbors", "rcp_cell_keys", "rcp_size", "rcp_dim", "rcp_status_str", "rcp_last_error",
            "rcp_energy_grad_noalloc", "rcp_batch_create", "rcp_batch_run", "rcp_batch_tuning", "rcp_batch_destroy",
-           "rcp_batch_last_error"]
+           "rcp_batch_last_error", "rcp_create_seated", "rcp_frozen", "rcp_cascade"]
 
 
 class rcp_config(C.Structure):
@@ -102,12 +102,18 @@ def load(path: str | None = None) -> C.CDLL:
     L.rcp_size.restype = C.c_longlong
     L.rcp_dim.argtypes = [vp]
     L.rcp_dim.restype = C.c_int
+    L.rcp_create_seated.argtypes = [vp, vp, C.c_longlong, vp, C.c_longlong, ip, vp, C.c_ulonglong,
+                                    C.POINTER(rcp_config), C.POINTER(vp)]
+    L.rcp_frozen.argtypes = [vp]
+    L.rcp_frozen.restype = C.c_longlong
+    L.rcp_cascade.argtypes = [vp, vp, C.c_longlong, ip, vp, C.c_ulonglong, C.POINTER(rcp_config), vp, vp, vp, vp]
     L.rcp_status_str.argtypes = [ip]
     L.rcp_status_str.restype = C.c_char_p
     L.rcp_last_error.argtypes = [vp]
     L.rcp_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("rcp_size", "rcp_dim", "rcp_status_str", "rcp_last_error", "rcp_batch_last_error"):
+        if name not in ("rcp_size", "rcp_dim", "rcp_frozen", "rcp_status_str", "rcp_last_error",
+                        "rcp_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -145,6 +151,46 @@ def rcp_create(diameters, box=1.0, seed: int = 0, cfg: rcp_config | None = None,
     _check(load().rcp_create(D0.ctypes.data, D0.size, d, b.ctypes.data, seed,
                              C.byref(cfg) if cfg is not None else None, C.byref(h)))
     return h
+
+
+def rcp_create_seated(fixed_d, fixed_x, diameters, box=1.0, seed: int = 0, cfg: rcp_config | None = None,
+                      d: int = 3):
+    """Frozen spheres (contact diameters fixed_d, positions fixed_x [Nf, d])
+    first, then the mobile ones (relative diameters)."""
+    F = np.ascontiguousarray(fixed_d, dtype=np.float64).ravel()
+    X = np.ascontiguousarray(fixed_x, dtype=np.float64).reshape(F.size, d)
+    D0 = np.ascontiguousarray(diameters, dtype=np.float64).ravel()
+    b = np.full(d, float(box)) if np.isscalar(box) else np.ascontiguousarray(box, dtype=np.float64)
+    if cfg is None:
+        cfg = rcp_config_default()
+    h = C.c_void_p()
+    _check(load().rcp_create_seated(F.ctypes.data, X.ctypes.data, F.size, D0.ctypes.data, D0.size, d,
+                                    b.ctypes.data, seed, C.byref(cfg), C.byref(h)))
+    return h
+
+
+def rcp_frozen(h) -> int:
+    return int(load().rcp_frozen(h))
+
+
+def rcp_cascade(diameters, cls, box=1.0, seed: int = 0, cfg: rcp_config | None = None, d: int = 3):
+    """The sequential cascade.  Returns (positions [N, d], contact diameters
+    [N], phi of each stage [2C-1], Adam steps of each stage [2C-1])."""
+    D0 = np.ascontiguousarray(diameters, dtype=np.float64).ravel()
+    k = np.ascontiguousarray(cls, dtype=np.int32).ravel()
+    if k.size != D0.size or k.size == 0:
+        raise ValueError("one class per sphere")
+    nst = 2 * (int(k.max()) + 1) - 1
+    b = np.full(d, float(box)) if np.isscalar(box) else np.ascontiguousarray(box, dtype=np.float64)
+    if cfg is None:
+        cfg = rcp_config_default()
+    x = np.zeros((D0.size, d))
+    dm = np.zeros(D0.size)
+    ph = np.zeros(max(nst, 1))
+    it = np.zeros(max(nst, 1), dtype=np.int64)
+    _check(load().rcp_cascade(D0.ctypes.data, k.ctypes.data, D0.size, d, b.ctypes.data, seed, C.byref(cfg),
+                              x.ctypes.data, dm.ctypes.data, ph.ctypes.data, it.ctypes.data))
+    return x, dm, ph, it
 
 
 def rcp_destroy(h):
@@ -300,11 +346,18 @@ class RunSummary:
 class Packing:
     """One packing on the GPU (owns an rcp handle)."""
 
-    def __init__(self, diameters, box=1.0, seed: int = 0, precision: int = RCP_FP64, d: int = 3, **cfg):
+    def __init__(self, diameters, box=1.0, seed: int = 0, precision: int = RCP_FP64, d: int = 3,
+                 fixed_d=None, fixed_x=None, **cfg):
+        """fixed_d / fixed_x (optional): frozen spheres placed before the
+        mobile ones (rcp_create_seated)."""
         self.cfg = rcp_config_default(precision=precision, **cfg)
-        self.n = int(np.size(diameters))
         self.d = int(d)
-        self.h = rcp_create(diameters, box, seed, self.cfg, d=self.d)
+        if fixed_d is None:
+            self.n = int(np.size(diameters))
+            self.h = rcp_create(diameters, box, seed, self.cfg, d=self.d)
+        else:
+            self.n = int(np.size(fixed_d)) + int(np.size(diameters))
+            self.h = rcp_create_seated(fixed_d, fixed_x, diameters, box, seed, self.cfg, d=self.d)
 
     def close(self):
         if self.h:

@@ -51,3 +51,24 @@ def test_create_rejects_bad_input_before_touching_the_gpu(lib):
     with pytest.raises(rcp.RcpError) as e:
         rcp.rcp_create(np.ones(4), np.ones(4), 0, d=4)   # d is 2 or 3
     assert e.value.status == 9
+
+
+def test_seated_and_cascade_reject_bad_input_before_touching_the_gpu(lib):
+    from paper_2608_12235_b300 import rcp
+    import numpy as np
+    mixed = rcp.rcp_config_default(precision=rcp.RCP_MIXED)
+    with pytest.raises(rcp.RcpError) as e:   # frozen spheres: binary64 path only
+        rcp.rcp_create_seated([1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0, mixed)
+    assert e.value.status == 9
+    with pytest.raises(rcp.RcpError) as e:   # a frozen diameter must be positive
+        rcp.rcp_create_seated([-1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0)
+    assert e.value.status == 1
+    with pytest.raises(rcp.RcpError) as e:   # a frozen position must be finite
+        rcp.rcp_create_seated([1.0], [[0.5, np.nan, 0.5]], [1.0], 1.0, 0)
+    assert e.value.status == 1
+    with pytest.raises(rcp.RcpError) as e:   # class 1 is empty
+        rcp.rcp_cascade([1.0, 1.0], [0, 2])
+    assert e.value.status == 1
+    with pytest.raises(rcp.RcpError) as e:
+        rcp.rcp_cascade([1.0, 1.0], [0, 1], cfg=mixed)
+    assert e.value.status == 9
