@@ -12,6 +12,7 @@ paper it follows.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -46,7 +47,7 @@ class Params(C.Structure):
                 ("skin_abs", C.c_double), ("lr_x", C.c_double), ("lr_kappa", C.c_double),
                 ("delta_star0", C.c_double), ("tol", C.c_double), ("Y", C.c_int), ("X", C.c_int),
                 ("n_min", C.c_long), ("n_down", C.c_int), ("n_cycles", C.c_int),
-                ("max_iters", C.c_long), ("kappa_init", C.c_double)]
+                ("max_iters", C.c_long), ("kappa_init", C.c_double), ("walls", C.c_int)]
 
 
 class Result(C.Structure):
@@ -60,6 +61,8 @@ def lib():
     if _lib is None:
         build()
         L = C.CDLL(_LIB)
+        L.orc_set_walls.argtypes = [C.c_int]
+        L.orc_get_walls.restype = C.c_int
         L.orc_splitmix64_at.restype = C.c_uint64
         L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_init_positions.argtypes = [C.c_uint64, C.c_long, C.c_int, _dp, _dp]
@@ -130,6 +133,19 @@ def f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+@contextlib.contextmanager
+def walls(mask: int):
+    """Flat hard walls (bit a: walls at 0 and L_a bound axis a) for the calls
+    inside the block (orc_set_walls); the previous mask is restored."""
+    L = lib()
+    before = L.orc_get_walls()
+    L.orc_set_walls(int(mask))
+    try:
+        yield
+    finally:
+        L.orc_set_walls(before)
+
+
 # ---------------------------------------------------------------- primitives
 def splitmix64_at(seed: int, k: int) -> int:
     return int(lib().orc_splitmix64_at(seed, k))
@@ -141,7 +157,7 @@ def init_positions(seed: int, n: int, L=1.0, d: int = 3) -> np.ndarray:
     return x.reshape(n, d)
 
 
-def place(seed: int, D0, kappa: float, L=1.0, d: int = 3, max_rounds: int = 10000, x_frozen=None):
+def place(seed: int, D0, kappa: float, L=1.0, d: int = 3, max_rounds: int = 10000, x_frozen=None, wall_mask=0):
     """Non-overlapping placement by rounds of random sequential addition
     (orc_place).  Frozen spheres (D0 < 0) stay where x_frozen [n, d] has them.
     Returns (positions [n, d], round of each sphere, rounds or -1)."""
@@ -149,7 +165,8 @@ def place(seed: int, D0, kappa: float, L=1.0, d: int = 3, max_rounds: int = 1000
     n = D0.size
     x = np.zeros(n * d) if x_frozen is None else f64(x_frozen).ravel().copy()
     rounds = np.zeros(n, dtype=np.int32)
-    r = lib().orc_place(seed, n, d, _box(L, d), D0, kappa, max_rounds, x, rounds)
+    with walls(wall_mask):
+        r = lib().orc_place(seed, n, d, _box(L, d), D0, kappa, max_rounds, x, rounds)
     return x.reshape(n, d), rounds, int(r)
 
 
@@ -202,7 +219,7 @@ def cell_keys(x, D0, L, kappa_b, s, sigma0, d=3, occ=1.0):
     return key
 
 
-def _list(fn, x, D0, L, kappa_b, s, sigma0, d):
+def _list(fn, x, D0, L, kappa_b, s, sigma0, d, wall_mask=0):
     x = f64(x).ravel()
     D0 = f64(D0)
     n = D0.size
@@ -210,20 +227,21 @@ def _list(fn, x, D0, L, kappa_b, s, sigma0, d):
     cap = 32 * n + 64
     while True:
         col = np.zeros(cap, dtype=np.int32)
-        P = fn(x, D0, n, d, _box(L, d), kappa_b, s, sigma0, rowptr, col, cap)
+        with walls(wall_mask):
+            P = fn(x, D0, n, d, _box(L, d), kappa_b, s, sigma0, rowptr, col, cap)
         if P <= cap:
             return rowptr, col[:P].copy()
         cap = P
 
 
-def list_brute(x, D0, L, kappa_b, s, sigma0, d=3):
+def list_brute(x, D0, L, kappa_b, s, sigma0, d=3, wall_mask=0):
     """The listed set by definition (O(N^2)); CSR with ascending columns."""
-    return _list(lib().orc_list_brute, x, D0, L, kappa_b, s, sigma0, d)
+    return _list(lib().orc_list_brute, x, D0, L, kappa_b, s, sigma0, d, wall_mask)
 
 
-def list_grid(x, D0, L, kappa_b, s, sigma0, d=3):
+def list_grid(x, D0, L, kappa_b, s, sigma0, d=3, wall_mask=0):
     """The same set found through the size-class cell search."""
-    return _list(lib().orc_list_grid, x, D0, L, kappa_b, s, sigma0, d)
+    return _list(lib().orc_list_grid, x, D0, L, kappa_b, s, sigma0, d, wall_mask)
 
 
 def row_brute(x, D0, L, kappa_b, s, sigma0, i, d=3):
@@ -235,7 +253,7 @@ def row_brute(x, D0, L, kappa_b, s, sigma0, i, d=3):
     return col[:P].copy()
 
 
-def energy_grad(x, D0, L, kappa, mu, eps=1.0, d=3, rowptr=None, col=None):
+def energy_grad(x, D0, L, kappa, mu, eps=1.0, d=3, rowptr=None, col=None, wall_mask=0):
     """Eq. energy, its gradient w.r.t. every coordinate and kappa, and the largest
     fractional overlap.  Brute force over all pairs unless a CSR list is given."""
     x = f64(x).ravel()
@@ -243,12 +261,13 @@ def energy_grad(x, D0, L, kappa, mu, eps=1.0, d=3, rowptr=None, col=None):
     n = D0.size
     E, dk, md = np.zeros(1), np.zeros(1), np.zeros(1)
     g = np.zeros(n * d)
-    if rowptr is None:
-        lib().orc_energy_grad_brute(x, D0, n, d, _box(L, d), kappa, mu, eps, E, g, dk, md)
-    else:
-        lib().orc_energy_grad_list(x, D0, n, d, _box(L, d), kappa, mu, eps,
-                                   np.ascontiguousarray(rowptr, dtype=np.int64),
-                                   np.ascontiguousarray(col, dtype=np.int32), E, g, dk, md)
+    with walls(wall_mask):
+        if rowptr is None:
+            lib().orc_energy_grad_brute(x, D0, n, d, _box(L, d), kappa, mu, eps, E, g, dk, md)
+        else:
+            lib().orc_energy_grad_list(x, D0, n, d, _box(L, d), kappa, mu, eps,
+                                       np.ascontiguousarray(rowptr, dtype=np.int64),
+                                       np.ascontiguousarray(col, dtype=np.int32), E, g, dk, md)
     return float(E[0]), g.reshape(n, d), float(dk[0]), float(md[0])
 
 
@@ -269,12 +288,13 @@ def wrap(x: float, L: float) -> float:
     return float(lib().orc_wrap(x, L))
 
 
-def shrink_kappa(x, D0, L, kappa, rowptr, col, d=3) -> float:
+def shrink_kappa(x, D0, L, kappa, rowptr, col, d=3, wall_mask=0) -> float:
     x = f64(x).ravel()
     D0 = f64(D0)
-    return float(lib().orc_shrink_kappa(x, D0, D0.size, d, _box(L, d), kappa,
-                                        np.ascontiguousarray(rowptr, dtype=np.int64),
-                                        np.ascontiguousarray(col, dtype=np.int32)))
+    with walls(wall_mask):
+        return float(lib().orc_shrink_kappa(x, D0, D0.size, d, _box(L, d), kappa,
+                                            np.ascontiguousarray(rowptr, dtype=np.int64),
+                                            np.ascontiguousarray(col, dtype=np.int32)))
 
 
 def phi(D0, L, kappa, d=3) -> float:
@@ -326,7 +346,8 @@ def run(D0, seed=0, x0=None, trace_len=0, **params) -> RunResult:
 
 
 # ---------------------------------------------------------------- the cascade
-def seated_state(fixed_d, fixed_x, D0, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, phi0=0.05):
+def seated_state(fixed_d, fixed_x, D0, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, phi0=0.05,
+                 wall_mask=0):
     """Initial state of a seated packing (Sec. IV: a finer class seated into
     the voids of coarser spheres held fixed).  Spheres 0..nf-1 are frozen, with
     contact diameters fixed_d and positions fixed_x (wrapped into the box);
@@ -342,10 +363,10 @@ def seated_state(fixed_d, fixed_x, D0, seed=0, L=1.0, d=3, placement=0, place_ro
     fx = f64(fixed_x).reshape(nf, d)
     for i in range(nf):
         for a in range(d):
-            x[i, a] = wrap(fx[i, a], box[a])
+            x[i, a] = fx[i, a] if (wall_mask >> a) & 1 else wrap(fx[i, a], box[a])
     if placement:
         k0 = kappa0(Dall, L, phi0, d)
-        x, _, r = place(seed, Dall, k0, L, d, place_rounds, x_frozen=x)
+        x, _, r = place(seed, Dall, k0, L, d, place_rounds, x_frozen=x, wall_mask=wall_mask)
         if r < 0:
             raise RuntimeError("placement did not finish")
     return Dall, x
@@ -368,6 +389,7 @@ def cascade(D0, cls, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, **para
     n = D0.size
     nclass = int(cls.max()) + 1
     phi0 = params.pop("phi0", 0.05)
+    wall_mask = params.get("walls", 0)
     order = []          # caller indices of the packed spheres, in stage order
     diam = None         # their contact diameters
     xs = None           # their positions
@@ -377,7 +399,7 @@ def cascade(D0, cls, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, **para
         if s_ == 0:
             if placement:
                 k0 = kappa0(D0[new], L, phi0, d)
-                x0, _, r = place(seed, D0[new], k0, L, d, place_rounds)
+                x0, _, r = place(seed, D0[new], k0, L, d, place_rounds, wall_mask=wall_mask)
                 if r < 0:
                     raise RuntimeError("placement did not finish")
             else:
@@ -388,7 +410,7 @@ def cascade(D0, cls, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, **para
             xs = res.x
             log.append((0, "pack", res.phi, res.iters))
             continue
-        Dall, x0 = seated_state(diam, xs, D0[new], seed + s_, L, d, placement, place_rounds, phi0)
+        Dall, x0 = seated_state(diam, xs, D0[new], seed + s_, L, d, placement, place_rounds, phi0, wall_mask)
         res = run(Dall, seed=seed + s_, x0=x0, d=d, L=L, phi0=phi0, **params)
         log.append((s_, "seat", res.phi, res.iters))
         nf = diam.size

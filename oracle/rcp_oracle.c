@@ -36,6 +36,13 @@
  *     the moments that scale the schedule sum over the mobile spheres only.
  *     The whole encoding is a reading; the paper describes the protocol, not
  *     its arithmetic.
+ *   - flat hard walls (Sec. II: each axis periodic or bounded by a wall):
+ *     axis a with bit a of the wall mask set has walls at 0 and L_a; it takes
+ *     no minimum image and no wrap.  A sphere meets a wall when the distance
+ *     h from its centre to the wall is below its contact radius rad = kappa
+ *     D^0 / 2 (F/2 frozen); delta = 1 - h/rad is the pair rule against its
+ *     mirror image, and the term eps/2 delta^2 joins its row after the pair
+ *     fold (axes in order, the wall at 0 before the wall at L_a).  Readings.
  */
 #include "rcp_oracle.h"
 #include <math.h>
@@ -45,6 +52,16 @@
 #define ORC_PI 3.141592653589793
 #define ORC_KMAX 32
 #define ORC_NMAX (1L << 19)
+
+/* Wall mask of the boundary in force (bit a: flat walls bound axis a).  A
+ * module setting rather than an argument of every geometric function;
+ * orc_run sets it from its parameters for the run and restores it. */
+static int g_walls = 0;
+
+void orc_set_walls(int mask) { g_walls = mask; }
+int orc_get_walls(void) { return g_walls; }
+
+static int walled(int a) { return (g_walls >> a) & 1; }
 
 /* Contact diameter of a sphere at scale kappa: kappa D^0 for a mobile sphere,
  * the fixed -D0 for a frozen one (D0 < 0). */
@@ -102,7 +119,8 @@ void orc_init_positions(uint64_t seed, long n, int d, const double* L, double* x
  * tested against every sphere.  attempt[i] (optional) receives the round in
  * which sphere i was placed.  Returns the largest number of rounds a class
  * took, or -1 if a class still has spheres unplaced after max_rounds (those
- * keep their last candidates).  Frozen spheres (D0 < 0) count as placed from
+ * keep their last candidates).  With flat walls a candidate is also rejected
+ * when it meets one (distance to the wall below rho_i).  Frozen spheres (D0 < 0) count as placed from
  * the start, at the positions x holds on entry; they never draw. */
 int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, double kappa, int max_rounds,
               double* x, int* attempt)
@@ -144,6 +162,8 @@ int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, d
             for (long i = 0; i < n; ++i) {
                 if (cls[i] != k || placed[i]) continue;
                 keep[i] = 1;
+                for (int a = 0; a < d; ++a)   /* a candidate must not meet a wall either */
+                    if (walled(a) && (cand[d * i + a] < rad[i] || L[a] - cand[d * i + a] < rad[i])) keep[i] = 0;
                 for (long j = 0; j < n && keep[i]; ++j) {
                     if (j == i) continue;
                     if (placed[j]) {
@@ -261,15 +281,16 @@ double orc_rho(double D0, double kappa_b, double s, double sigma0)
     return size_at(D0, kappa_b) * (0.5 + s) + sigma0;
 }
 
-/* Minimum-image displacement x_i - x_j on every axis, squared distance
- * accumulated left to right. */
+/* Minimum-image displacement x_i - x_j on every periodic axis (the plain
+ * difference on a walled one), squared distance accumulated left to right. */
 static double min_image(const double* xi, const double* xj, int d, const double* L, double* dx)
 {
     double r2 = 0.0;
     for (int a = 0; a < d; ++a) {
         double t = xi[a] - xj[a];
         double h = 0.5 * L[a];
-        if (t > h) t = t - L[a];
+        if (walled(a)) { /* bounded axis: the plain difference */ }
+        else if (t > h) t = t - L[a];
         else if (t < -h) t = t + L[a];
         dx[a] = t;
         r2 = r2 + t * t;
@@ -505,7 +526,13 @@ long orc_list_grid_occ(const double* x, const double* D0, long n, int d, const d
                 long nn = ng[k][a];
                 long l = (long)floor(((x[d * i + a] - R) / L[a]) * (double)nn);
                 long h = (long)floor(((x[d * i + a] + R) / L[a]) * (double)nn);
-                if (h - l + 1 >= nn) { lo[a] = 0; cnt[a] = nn; }
+                if (walled(a)) {   /* no wrap: clamp the window; edge cells hold what lies beyond */
+                    if (l < 0) l = 0;
+                    if (l > nn - 1) l = nn - 1;
+                    if (h < 0) h = 0;
+                    if (h > nn - 1) h = nn - 1;
+                    lo[a] = l; cnt[a] = h - l + 1;
+                } else if (h - l + 1 >= nn) { lo[a] = 0; cnt[a] = nn; }
                 else { lo[a] = l; cnt[a] = h - l + 1; }
             }
             for (long cz = 0; cz < cnt[2]; ++cz)
@@ -580,6 +607,34 @@ static void row_add(rowacc* a, long i, long j, const double* x, const double* D0
     if (delta > a->md) a->md = delta;
 }
 
+/* Row i's wall terms, after its pairs: for every walled axis a, the wall at 0
+ * (h = x_a) then the wall at L_a (h = L_a - x_a).  rad = kappa D^0/2 (F/2
+ * frozen), delta = 1 - h/rad; when delta > 0:
+ *   d E / d x_a = -+ eps delta / rad (mobile rows; the wall at 0 pushes to +x_a),
+ *   e_i += eps/2 delta^2,  k_i += eps delta (1 - delta)/kappa (mobile),
+ * the latter from d delta / d kappa = (h/rad)/kappa. */
+static void row_walls(rowacc* acc, long i, const double* x, const double* D0, int d, const double* L, double kappa,
+                      double eps)
+{
+    if (!g_walls) return;
+    double rad = D0[i] > 0.0 ? kappa * (0.5 * D0[i]) : 0.5 * (-D0[i]);
+    for (int a = 0; a < d; ++a) {
+        if (!walled(a)) continue;
+        for (int side = 0; side < 2; ++side) {
+            double h = side == 0 ? x[d * i + a] : L[a] - x[d * i + a];
+            double delta = 1.0 - h / rad;
+            if (!(delta > 0.0)) continue;
+            if (D0[i] > 0.0) {
+                double f = (eps * delta) / rad;
+                acc->g[a] = side == 0 ? acc->g[a] - f : acc->g[a] + f;
+                acc->k = acc->k + ((eps * delta) * (1.0 - delta)) / kappa;
+            }
+            acc->e = acc->e + (0.5 * eps) * (delta * delta);
+            if (delta > acc->md) acc->md = delta;
+        }
+    }
+}
+
 static void finish_sums(const double* e, const double* k, const double* D0, long n,
                         double kappa, double mu, double* E, double* dEdk)
 {
@@ -605,6 +660,7 @@ void orc_energy_grad_brute(const double* x, const double* D0, long n, int d, con
         rowacc a;
         row_begin(&a);
         for (long j = 0; j < n; ++j) if (j != i) row_add(&a, i, j, x, D0, d, L, kappa, eps);
+        row_walls(&a, i, x, D0, d, L, kappa, eps);
         if (g) for (int c = 0; c < d; ++c) g[d * i + c] = a.g[c];
         e[i] = a.e;
         k[i] = a.k;
@@ -630,6 +686,7 @@ void orc_energy_grad_list(const double* x, const double* D0, long n, int d, cons
         rowacc a;
         row_begin(&a);
         for (long t = rowptr[i]; t < rowptr[i + 1]; ++t) row_add(&a, i, col[t], x, D0, d, L, kappa, eps);
+        row_walls(&a, i, x, D0, d, L, kappa, eps);
         if (g) for (int c = 0; c < d; ++c) g[d * i + c] = a.g[c];
         e[i] = a.e;
         k[i] = a.k;
@@ -649,6 +706,7 @@ void orc_row_grad(const double* x, const double* D0, long n, int d, const double
     rowacc a;
     row_begin(&a);
     for (long j = 0; j < n; ++j) if (j != i) row_add(&a, i, j, x, D0, d, L, kappa, eps);
+    row_walls(&a, i, x, D0, d, L, kappa, eps);
     for (int c = 0; c < d; ++c) g_i[c] = a.g[c];
     *e_i = a.e;
     *k_i = a.k;
@@ -686,7 +744,8 @@ void orc_adam_update(double* p, double* m, double* v, const double* g, long n,
  * A pair with one frozen sphere (fixed diameter F) touches at
  * kappa = (r - F/2) / (D_a^0 / 2); the subtraction can cancel bits, so that
  * quotient is lowered by (1 - 2^-40) first, and clamped at 0.  Two frozen
- * spheres do not depend on kappa and set no bound. */
+ * spheres do not depend on kappa and set no bound.  A mobile sphere at
+ * distance h from a wall touches it at kappa = 2h / D^0 (clamped at 0). */
 double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const double* L,
                         double kappa, const long* rowptr, const int* col)
 {
@@ -709,6 +768,19 @@ double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const 
                 continue;
             }
             if (q < kc) kc = q;
+        }
+    if (g_walls)
+        for (long i = 0; i < n; ++i) {
+            if (!(D0[i] > 0.0)) continue;
+            for (int a = 0; a < d; ++a) {
+                if (!walled(a)) continue;
+                for (int side = 0; side < 2; ++side) {
+                    double h = side == 0 ? x[d * i + a] : L[a] - x[d * i + a];
+                    double q = (2.0 * h) / D0[i];
+                    if (q < 0.0) q = 0.0;
+                    if (q < kc) kc = q;
+                }
+            }
         }
     return kc * (1.0 - 0x1.0p-50);
 }
@@ -849,6 +921,8 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
     int d = p->d;
     const double* L = p->L;
     if (n < 1 || (d != 2 && d != 3)) return 1;
+    int walls_before = g_walls;
+    g_walls = p->walls;
     long nd = n * d;
     double* x = (double*)malloc(sizeof(double) * (size_t)nd);
     double* m = (double*)calloc((size_t)nd, sizeof(double));
@@ -871,8 +945,8 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
     if (p->kappa_init > 0.0) kappa = p->kappa_init;   /* sigma0 stays that of kappa_0 */
     double mk = 0.0, vk = 0.0, b1 = 1.0, b2 = 1.0;
     double s = p->skin_s, th = p->skin_theta;
-    double Lmin = L[0];
-    for (int a = 1; a < d; ++a) if (L[a] < Lmin) Lmin = L[a];
+    double Lmin = INFINITY;   /* the periodic-image rule concerns periodic axes only */
+    for (int a = 0; a < d; ++a) if (!walled(a) && L[a] < Lmin) Lmin = L[a];
 
     long n_mobile = 0;
     for (long i = 0; i < n; ++i) n_mobile += D0[i] > 0.0;
@@ -912,7 +986,8 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
             b2 = b2 * p->beta2;
             adam_positions(x, m, v, g, D0, n, d, eta_x, p, b1, b2);
             for (long i = 0; i < n; ++i)
-                for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
+                for (int a = 0; a < d; ++a)
+                    if (!walled(a)) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
             orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);
             ++it;
             need = need || skin_spent(x, xb, D0, n, d, L, kappa, kb, s, th, sigma0);
@@ -933,6 +1008,7 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
         memcpy(x_io, x, sizeof(double) * (size_t)nd);
     }
 done:
+    g_walls = walls_before;
     free(x); free(m); free(v); free(g); free(xb); free(rowptr); free(col);
     return status;
 }

@@ -46,6 +46,8 @@ typedef struct {
     long   max_iters;    /* safety cap on the total iteration count */
     double kappa_init;   /* > 0: start the run at this kappa instead of kappa_0
                             (sigma0 is still that of kappa_0); 0: kappa_0 */
+    int    walls;        /* bit a set: flat hard walls at 0 and L_a bound axis a
+                            (no minimum image, no wrap); 0: periodic box */
 } orc_params;
 
 typedef struct {
@@ -62,6 +64,12 @@ typedef struct {
 /* Frozen spheres (stages of the sequential cascade, Sec. IV): wherever a
  * function takes D0, an entry D0[i] < 0 marks sphere i as frozen, with fixed
  * contact diameter -D0[i] and a position that the run does not move. */
+
+/* Flat hard walls: the wall mask in force for every geometric function
+ * below (bit a: axis a bounded by walls at 0 and L_a).  orc_run uses its
+ * parameter's mask for the run. */
+void   orc_set_walls(int mask);
+int    orc_get_walls(void);
 
 /* ---- input-side primitives ---- */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
