@@ -93,6 +93,17 @@ typedef struct {
                                round 0 being the uniform draw */
     int       place_rounds; /* most placement rounds before rcp_create gives up
                                with RCP_ERR_CAPACITY (10000) */
+    int       walls;        /* boundary (Sec. II: each axis periodic or bounded by a
+                               hard wall): bit a set bounds axis a by flat walls at 0
+                               and L_a -- no minimum image and no wrap there, and a
+                               sphere closer than its contact radius rad = kappa
+                               D^0/2 to a wall overlaps it by delta = 1 - h/rad (h
+                               the distance to the wall), adding eps/2 delta^2 to
+                               Eq. energy; shrink to contact also stops at the first
+                               wall contact and placement keeps spheres off the
+                               walls.  Positions on walled axes should stay within
+                               one box edge of the box.  Only the bits of the d
+                               axes; binary64 path only (0: periodic box) */
 } rcp_config;
 
 /* When rcp_run returns early. */

@@ -837,6 +837,8 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     if (d != 2 && d != 3) return RCP_ERR_UNSUPPORTED;
     if (Nf >= (1LL << 31) || Nm >= (1LL << 31) - Nf) return RCP_ERR_ARG;
     if (Nf > 0 && cfg && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
+    if (cfg && (cfg->walls & ~((1 << d) - 1))) return RCP_ERR_ARG;   // one bit per axis of the caller
+    if (cfg && cfg->walls && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     const long long N = Nf + Nm;
     for (long long i = 0; i < Nf; ++i) {
         if (!(fixed_d[i] > 0.0) || !std::isfinite(fixed_d[i])) return RCP_ERR_ARG;
@@ -889,6 +891,11 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         if (box[a] > c.Lmax) c.Lmax = box[a];
     }
     c.V = d == 2 ? box[0] * box[1] : (box[0] * box[1]) * box[2];   // area when d = 2
+    c.walls = h->cfg.walls;
+    // the periodic-image rule concerns the periodic axes of the caller only
+    c.Lmin = INFINITY;
+    for (int a = 0; a < d; ++a)
+        if (!((c.walls >> a) & 1) && box[a] < c.Lmin) c.Lmin = box[a];
     c.dim = d;
     c.eps = h->cfg.eps;
     c.beta1 = h->cfg.beta1;

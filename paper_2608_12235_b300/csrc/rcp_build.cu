@@ -431,6 +431,14 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
         // a placement candidate also meets frozen spheres of finer classes,
         // which are placed before any class is
         const int kend = (PLACE && c.nfrozen > 0) ? ctl->nlev - 1 : li;
+        if (PLACE && c.walls) {   // a candidate must keep off the walls too (distance below rho_i)
+            const double4_32a xi = x[i];
+            for (int a = 0; a < 3; ++a) {
+                if (!((c.walls >> a) & 1)) continue;
+                const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
+                if (xa < ri || c.L[a] - xa < ri) reject[i] = 1;
+            }
+        }
         for (int k = 0; k <= kend; ++k) {
             const double rk = ctl->rho_lvl[k];
             if (!(rk > 0.0)) continue;
@@ -442,9 +450,17 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
                 // binary32 errors of u and of the product below
                 const float Ru = (float)(((ri + rk) * c.invL[a]) * (1.0 + 1e-6) + 2e-6);
                 const float fn = (float)ng[a];
-                const int l = (int)floorf((u3[a] - Ru) * fn);
-                const int h = (int)floorf((u3[a] + Ru) * fn);
-                if (h - l + 1 >= (int)ng[a]) {
+                int l = (int)floorf((u3[a] - Ru) * fn);
+                int h = (int)floorf((u3[a] + Ru) * fn);
+                if ((c.walls >> a) & 1) {
+                    // walled axis, no wrap: clamp the window (the edge cells
+                    // also hold the spheres beyond the walls)
+                    const int top = (int)ng[a] - 1;
+                    l = l < 0 ? 0 : (l > top ? top : l);
+                    h = h < 0 ? 0 : (h > top ? top : h);
+                    lo[a] = l;
+                    nc[a] = (unsigned int)(h - l + 1);
+                } else if (h - l + 1 >= (int)ng[a]) {
                     lo[a] = 0;
                     nc[a] = ng[a];
                 } else {
@@ -463,9 +479,9 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
                         const uint2 range = row[xx];
                         for (unsigned int t = range.x; t < range.y; ++t) {
                             const float4 uj = xsf[t];
-                            const float dx = wrap_unit(ui.x - uj.x) * L0;
-                            const float dy = wrap_unit(ui.y - uj.y) * L1;
-                            const float dz = wrap_unit(ui.z - uj.z) * L2;
+                            const float dx = ((c.walls & 1) ? ui.x - uj.x : wrap_unit(ui.x - uj.x)) * L0;
+                            const float dy = ((c.walls & 2) ? ui.y - uj.y : wrap_unit(ui.y - uj.y)) * L1;
+                            const float dz = ((c.walls & 4) ? ui.z - uj.z : wrap_unit(ui.z - uj.z)) * L2;
                             const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
                             const float cut = ui.w + uj.w;
                             const float hi = (cut * up + Eabs) * up;
@@ -477,9 +493,9 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
                             if (!in) {
                                 // the band: exact binary64 predicate
                                 const double4_32a xi = x[i], xj = x[j];
-                                double ex = min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
-                                double ey = min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
-                                double ez = min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
+                                double ex = (c.walls & 1) ? xi.x - xj.x : min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
+                                double ey = (c.walls & 2) ? xi.y - xj.y : min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
+                                double ez = (c.walls & 4) ? xi.z - xj.z : min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
                                 double d2 = ex * ex + ey * ey + ez * ez;
                                 double cc = ri + rho[j];
                                 in = d2 < cc * cc;

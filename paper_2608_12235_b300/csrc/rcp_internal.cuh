@@ -94,6 +94,7 @@ struct RcpConst {
     unsigned int long_row;     // rows longer than this get a warp (mixed)
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
     long long nfrozen;         // frozen spheres (binary64 path only; 0 otherwise)
+    int walls;                 // bit a: flat walls at 0 and L_a bound axis a (binary64 path only)
 };
 
 // Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a

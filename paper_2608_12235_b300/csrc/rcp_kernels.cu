@@ -41,6 +41,49 @@ __device__ __forceinline__ double min_image(double t, double L, double h)
     return t;
 }
 
+// Component a of x_i - x_j: minimum image on a periodic axis, the plain
+// difference on an axis bounded by flat walls (bit a of c.walls).
+__device__ __forceinline__ double axis_diff(const RcpConst& c, int a, double t)
+{
+    return ((c.walls >> a) & 1) ? t : min_image(t, c.L[a], c.halfL[a]);
+}
+
+// Coordinate a after a step: wrapped on a periodic axis, kept on a walled one.
+__device__ __forceinline__ double axis_wrap(const RcpConst& c, int a, double x)
+{
+    return ((c.walls >> a) & 1) ? x : wrap_step(x, c.L[a]);
+}
+
+// Flat hard walls at 0 and L_a on every axis a whose bit is set in c.walls
+// (Sec. II).  Sphere i (contact radius rad = kappa D^0/2, F/2 frozen) meets
+// the wall at distance h when h < rad; with delta = 1 - h/rad its row takes
+// eps/2 delta^2, eps delta (1 - delta)/kappa (mobile) and -+ eps delta / rad
+// on dE/dx_a (mobile; the wall at 0 pushes towards +x_a).  Axes in order, the
+// wall at 0 before the wall at L_a, after the row's pairs.
+__device__ __forceinline__ void wall_terms(const RcpConst& c, double kappa, const double4_32a& xi, double& g0,
+                                           double& g1, double& g2, double& e, double& k, double& md)
+{
+    const bool mob = xi.w > 0.0;
+    const double rad = mob ? kappa * (0.5 * xi.w) : 0.5 * (-xi.w);
+    for (int a = 0; a < 3; ++a) {
+        if (!((c.walls >> a) & 1)) continue;
+        const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
+        for (int side = 0; side < 2; ++side) {
+            const double h = side == 0 ? xa : c.L[a] - xa;
+            const double delta = 1.0 - h / rad;
+            if (!(delta > 0.0)) continue;
+            if (mob) {
+                const double f = (c.eps * delta) / rad;
+                double& ga = a == 0 ? g0 : (a == 1 ? g1 : g2);
+                ga = side == 0 ? ga - f : ga + f;
+                k = k + ((c.eps * delta) * (1.0 - delta)) / kappa;
+            }
+            e = e + (0.5 * c.eps) * (delta * delta);
+            if (delta > md) md = delta;
+        }
+    }
+}
+
 __global__ void k_init_positions(unsigned long long seed, long long N, RcpConst c, const double* D0, double4_32a* x)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,6 +314,10 @@ __global__ void k_set_positions(long long N, RcpConst c, const double* xin, cons
             continue;
         }
         double v = xin[c.dim * u + a];
+        if ((c.walls >> a) & 1) {   // walled axis: the caller's coordinate as it is
+            p[a] = v;
+            continue;
+        }
         if (v < 0.0 || v >= c.L[a]) v = v - c.L[a] * floor(v / c.L[a]);
         p[a] = wrap_step(v, c.L[a]);
     }
@@ -332,9 +379,9 @@ __device__ __forceinline__ double adam_coord(double p, double g, double& m, doub
 __device__ __forceinline__ void skin_budget64(RcpCtl* ctl, const RcpConst& c, double px, double py, double pz,
                                               double D0, double4_32a b, float& bud)
 {
-    double dx = min_image(px - b.x, c.L[0], c.halfL[0]);
-    double dy = min_image(py - b.y, c.L[1], c.halfL[1]);
-    double dz = min_image(pz - b.z, c.L[2], c.halfL[2]);
+    double dx = axis_diff(c, 0, px - b.x);
+    double dy = axis_diff(c, 1, py - b.y);
+    double dz = axis_diff(c, 2, pz - b.z);
     const double disp = sqrt(dx * dx + dy * dy + dz * dz) * (1.0 + 1e-9);
     const double sig = c.skin_theta * (c.skin_s * ctl->kappa_b * D0 + ctl->sigma0) * (1.0 - 1e-9);
     const double bi = 2.0 * (sig - disp) / D0;
@@ -394,9 +441,9 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
         for (unsigned int t = rowptr[i]; t < t1; ++t) {
             const unsigned int j = col[t];
             const double4_32a xj = xin[j];
-            double dx = min_image(xi.x - xj.x, c.L[0], c.halfL[0]);
-            double dy = min_image(xi.y - xj.y, c.L[1], c.halfL[1]);
-            double dz = min_image(xi.z - xj.z, c.L[2], c.halfL[2]);
+            double dx = axis_diff(c, 0, xi.x - xj.x);
+            double dy = axis_diff(c, 1, xi.y - xj.y);
+            double dz = axis_diff(c, 2, xi.z - xj.z);
             double r2 = dx * dx + dy * dy + dz * dz;
             double r = sqrt(r2);
             const bool both = xi.w > 0.0 && xj.w > 0.0;   // no frozen sphere in the pair
@@ -419,6 +466,7 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
                 if (delta > md) md = delta;
             }
         }
+        if (c.walls) wall_terms(c, kappa, xi, g0, g1, g2, e, k, md);
         if (mode == RCP_MODE_ADAM && !(xi.w > 0.0)) {
             xout[i] = xi;   // frozen: position and moments stay
         } else if (mode == RCP_MODE_ADAM) {
@@ -427,9 +475,9 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
             const double eta = ctl->eta_x;
             double m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
             double v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
-            double p0 = wrap_step(adam_coord(xi.x, g0, m0, v0, eta, c, h1, h2), c.L[0]);
-            double p1 = wrap_step(adam_coord(xi.y, g1, m1, v1, eta, c, h1, h2), c.L[1]);
-            double p2 = wrap_step(adam_coord(xi.z, g2, m2, v2, eta, c, h1, h2), c.L[2]);
+            double p0 = axis_wrap(c, 0, adam_coord(xi.x, g0, m0, v0, eta, c, h1, h2));
+            double p1 = axis_wrap(c, 1, adam_coord(xi.y, g1, m1, v1, eta, c, h1, h2));
+            double p2 = axis_wrap(c, 2, adam_coord(xi.z, g2, m2, v2, eta, c, h1, h2));
             m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
             v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
             xout[i] = make_double4_32a(p0, p1, p2, xi.w);
@@ -614,9 +662,9 @@ __global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* 
         double4_32a p = x[i];
         double m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
         double v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
-        double p0 = wrap_step(adam_coord(p.x, g[3 * i], m0, v0, eta_x, c, h1, h2), c.L[0]);
-        double p1 = wrap_step(adam_coord(p.y, g[3 * i + 1], m1, v1, eta_x, c, h1, h2), c.L[1]);
-        double p2 = wrap_step(adam_coord(p.z, g[3 * i + 2], m2, v2, eta_x, c, h1, h2), c.L[2]);
+        double p0 = axis_wrap(c, 0, adam_coord(p.x, g[3 * i], m0, v0, eta_x, c, h1, h2));
+        double p1 = axis_wrap(c, 1, adam_coord(p.y, g[3 * i + 1], m1, v1, eta_x, c, h1, h2));
+        double p2 = axis_wrap(c, 2, adam_coord(p.z, g[3 * i + 2], m2, v2, eta_x, c, h1, h2));
         m[3 * i] = m0; m[3 * i + 1] = m1; m[3 * i + 2] = m2;
         v[3 * i] = v0; v[3 * i + 1] = v1; v[3 * i + 2] = v2;
         x[i] = make_double4_32a(p0, p1, p2, p.w);
@@ -653,9 +701,9 @@ __global__ void k_disp_check(RcpCtl* ctl, RcpConst c, const double4_32a* xA, con
     const double4_32a* x = ctl->parity ? xB : xA;
     const double4_32a p = x[i], b = xb[i];
     if (!(p.w > 0.0)) return;   // a frozen sphere neither moves nor grows
-    double dx = min_image(p.x - b.x, c.L[0], c.halfL[0]);
-    double dy = min_image(p.y - b.y, c.L[1], c.halfL[1]);
-    double dz = min_image(p.z - b.z, c.L[2], c.halfL[2]);
+    double dx = axis_diff(c, 0, p.x - b.x);
+    double dy = axis_diff(c, 1, p.y - b.y);
+    double dz = axis_diff(c, 2, p.z - b.z);
     const double disp = sqrt(dx * dx + dy * dy + dz * dz) * (1.0 + 1e-9);
     const double sig = c.skin_theta * (c.skin_s * ctl->kappa_b * p.w + ctl->sigma0) * (1.0 - 1e-9);
     if (disp + (ctl->kappa - ctl->kappa_b) * p.w * 0.5 * (1.0 + 1e-9) > sig) ctl->need_rebuild = 1;
@@ -681,9 +729,9 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
             const unsigned int j = col[t];
             if ((long long)j <= i) continue;
             const double4_32a xj = x[j];
-            double dx = min_image(xi.x - xj.x, c.L[0], c.halfL[0]);
-            double dy = min_image(xi.y - xj.y, c.L[1], c.halfL[1]);
-            double dz = min_image(xi.z - xj.z, c.L[2], c.halfL[2]);
+            double dx = axis_diff(c, 0, xi.x - xj.x);
+            double dy = axis_diff(c, 1, xi.y - xj.y);
+            double dz = axis_diff(c, 2, xi.z - xj.z);
             double r = sqrt(dx * dx + dy * dy + dz * dz);
             double qq;
             if (xi.w > 0.0 && xj.w > 0.0) {
@@ -698,6 +746,17 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
             }
             if (qq < q) q = qq;
         }
+        if (c.walls && xi.w > 0.0)   // a mobile sphere touches a wall at kappa = 2h / D^0
+            for (int a = 0; a < 3; ++a) {
+                if (!((c.walls >> a) & 1)) continue;
+                const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
+                for (int side = 0; side < 2; ++side) {
+                    const double h = side == 0 ? xa : c.L[a] - xa;
+                    double qq = (2.0 * h) / xi.w;
+                    if (qq < 0.0) qq = 0.0;
+                    if (qq < q) q = qq;
+                }
+            }
     }
     // block minimum through max of the negated value
     double bm = -block_max(-q, sh);

@@ -72,3 +72,14 @@ def test_seated_and_cascade_reject_bad_input_before_touching_the_gpu(lib):
     with pytest.raises(rcp.RcpError) as e:
         rcp.rcp_cascade([1.0, 1.0], [0, 1], cfg=mixed)
     assert e.value.status == 9
+
+
+def test_walls_are_checked_before_touching_the_gpu(lib):
+    from paper_2608_12235_b300 import rcp
+    import numpy as np
+    with pytest.raises(rcp.RcpError) as e:   # walls: binary64 path only
+        rcp.rcp_create(np.ones(4), 1.0, 0, rcp.rcp_config_default(precision=rcp.RCP_MIXED, walls=1))
+    assert e.value.status == 9
+    with pytest.raises(rcp.RcpError) as e:   # no z axis when d = 2
+        rcp.rcp_create(np.ones(4), 1.0, 0, rcp.rcp_config_default(walls=4), d=2)
+    assert e.value.status == 1

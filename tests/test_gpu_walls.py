@@ -1,0 +1,95 @@
+"""Flat hard walls (Sec. II): the binary64 CUDA path against the oracle, bit
+for bit, on the same seeded inputs -- lists with spheres on and beyond the
+walls, energy and gradient, placement, whole runs in d = 3 and d = 2, and a
+seated stage inside walls.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_12235_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rcp():
+    import torch
+    assert torch.cuda.is_available(), "the CUDA path needs a GPU"
+    from paper_2608_12235_b300 import build, rcp as R
+    build.build()
+    R.load()
+    return R
+
+
+def _sigma0(orc, D0, kappa0, cfg):
+    m = orc.moments(D0)
+    return cfg.skin_abs * ((cfg.lr_x * kappa0) * (m[2] / m[1]))
+
+
+def _state(orc, n, mask, d, seed):
+    rng = np.random.default_rng(seed)
+    D0 = inputs.lognormal(n, 0.5, 10.0)
+    x = rng.uniform(0.0, 1.0, (n, d))
+    for a in range(d):
+        if (mask >> a) & 1:
+            x[:, a] = rng.uniform(-0.01, 1.01, n)   # some spheres beyond the walls
+    return D0, x
+
+
+@pytest.mark.parametrize("mask,d", [(0b001, 3), (0b101, 3), (0b111, 3), (0b01, 2), (0b11, 2)])
+def test_walled_list_and_energy_bitexact(rcp, orc, mask, d):
+    n = 3000 if d == 3 else 1500
+    D0, x = _state(orc, n, mask, d, seed=mask + 10 * d)
+    p = rcp.Packing(D0, box=1.0, seed=1, d=d, walls=mask)
+    k = orc.kappa0(D0, 1.0, 0.4, d=d)
+    p.set_positions(x, k)
+    rp, col = p.neighbors()
+    s0 = _sigma0(orc, D0, orc.kappa0(D0, 1.0, 0.05, d=d), p.cfg)
+    orp, ocol = orc.list_brute(x, D0, 1.0, k, p.cfg.skin_s, s0, d=d, wall_mask=mask)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    for mu in (0.0, 0.01):
+        E, g, dk, md = p.energy_grad(mu)
+        oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, mu, d=d, wall_mask=mask)
+        assert omd > 0.0
+        assert E == oE and dk == odk and md == omd
+        assert np.array_equal(g, og)
+    # positions on walled axes are kept as given, not wrapped
+    assert np.array_equal(p.positions(), x)
+    p.close()
+
+
+def test_walled_placement_bitexact(rcp, orc):
+    D0 = inputs.lognormal(2000, 0.5, 10.0)
+    p = rcp.Packing(D0, box=1.0, seed=6, placement=1, phi0=0.2, walls=0b111)
+    k = orc.kappa0(D0, 1.0, 0.2)
+    x, _, R = orc.place(6, D0, k, wall_mask=0b111)
+    assert R >= 1
+    assert np.array_equal(p.positions(), x)
+    p.close()
+
+
+@pytest.mark.parametrize("mask,d", [(0b111, 3), (0b001, 3), (0b11, 2)])
+def test_walled_run_bitexact(rcp, orc, mask, d):
+    D0 = inputs.lognormal(600, 0.5, 10.0)
+    ref = orc.run(D0, seed=2, d=d, walls=mask)
+    p = rcp.Packing(D0, box=1.0, seed=2, d=d, walls=mask)
+    r = p.run()
+    assert r.stopped and ref.stopped and r.iters == ref.iters
+    assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
+    assert np.array_equal(p.positions(), ref.x)
+    p.close()
+
+
+def test_seated_stage_inside_walls_bitexact(rcp, orc):
+    g = (np.arange(2) + 0.25) * 4.0
+    X = np.array([[a, b, c] for a in g for b in g for c in g])
+    F = np.full(len(X), 1.6)
+    D = np.linspace(0.6, 1.0, 200)
+    Dall, x0 = orc.seated_state(F, X, D, seed=4, L=8.0, placement=1, wall_mask=0b011)
+    ref = orc.run(Dall, seed=4, x0=x0, L=8.0, walls=0b011)
+    p = rcp.Packing(D, box=8.0, seed=4, fixed_d=F, fixed_x=X, placement=1, walls=0b011)
+    r = p.run()
+    assert r.stopped and ref.stopped and r.iters == ref.iters
+    assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
+    assert np.array_equal(p.positions(), ref.x)
+    p.close()
