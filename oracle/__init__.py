@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("skin_abs", C.c_double), ("lr_x", C.c_double), ("lr_kappa", C.c_double),
                 ("delta_star0", C.c_double), ("tol", C.c_double), ("Y", C.c_int), ("X", C.c_int),
                 ("n_min", C.c_long), ("n_down", C.c_int), ("n_cycles", C.c_int),
-                ("max_iters", C.c_long), ("kappa_init", C.c_double), ("walls", C.c_int)]
+                ("max_iters", C.c_long), ("kappa_init", C.c_double), ("walls", C.c_int),
+                ("container", C.c_int)]
 
 
 class Result(C.Structure):
@@ -63,6 +64,8 @@ def lib():
         L = C.CDLL(_LIB)
         L.orc_set_walls.argtypes = [C.c_int]
         L.orc_get_walls.restype = C.c_int
+        L.orc_set_container.argtypes = [C.c_int]
+        L.orc_get_container.restype = C.c_int
         L.orc_splitmix64_at.restype = C.c_uint64
         L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_init_positions.argtypes = [C.c_uint64, C.c_long, C.c_int, _dp, _dp]
@@ -134,16 +137,23 @@ def f64(a):
 
 
 @contextlib.contextmanager
-def walls(mask: int):
-    """Flat hard walls (bit a: walls at 0 and L_a bound axis a) for the calls
-    inside the block (orc_set_walls); the previous mask is restored."""
+def walls(mask: int, container: int | None = None):
+    """Flat hard walls (bit a: walls at 0 and L_a bound axis a) and, when
+    given, the curved container (0 none, 1 ball / disk, 2 cylinder about z) for
+    the calls inside the block; the previous settings are restored.  A bare
+    mask may also be a (mask, container) pair."""
+    if isinstance(mask, tuple):
+        mask, container = mask
     L = lib()
-    before = L.orc_get_walls()
+    before = (L.orc_get_walls(), L.orc_get_container())
     L.orc_set_walls(int(mask))
+    if container is not None:
+        L.orc_set_container(int(container))
     try:
         yield
     finally:
-        L.orc_set_walls(before)
+        L.orc_set_walls(before[0])
+        L.orc_set_container(before[1])
 
 
 # ---------------------------------------------------------------- primitives

@@ -43,6 +43,13 @@
  *     D^0 / 2 (F/2 frozen); delta = 1 - h/rad is the pair rule against its
  *     mirror image, and the term eps/2 delta^2 joins its row after the pair
  *     fold (axes in order, the wall at 0 before the wall at L_a).  Readings.
+ *   - curved hard walls (Sec. II, Fig. 2: circular, cylindrical and spherical
+ *     domains): a container of radius R = min over its axes of L_a/2 about the
+ *     box centre -- a ball over every axis (a disk when d = 2) or a cylinder
+ *     about the z axis (circle in x, y).  Its axes are bounded (no minimum
+ *     image, no wrap); h = R - |x - c| over them, delta = 1 - h/rad as for a
+ *     flat wall, the term after the flat walls'; kappa_0 and phi take the
+ *     container's volume.  Readings.
  */
 #include "rcp_oracle.h"
 #include <math.h>
@@ -61,7 +68,42 @@ static int g_walls = 0;
 void orc_set_walls(int mask) { g_walls = mask; }
 int orc_get_walls(void) { return g_walls; }
 
-static int walled(int a) { return (g_walls >> a) & 1; }
+/* Curved container (0 none, 1 ball over every axis / disk when d = 2,
+ * 2 cylinder about z), a module setting like the wall mask. */
+static int g_container = 0;
+
+void orc_set_container(int type) { g_container = type; }
+int orc_get_container(void) { return g_container; }
+
+/* Axis a lies in the container's cross-section. */
+static int in_container(int a, int d) { return g_container == 1 ? a < d : (g_container == 2 ? a < 2 : 0); }
+
+/* Bounded axis: flat walls or the container; no minimum image, no wrap. */
+static int walled(int a) { return ((g_walls >> a) & 1) || in_container(a, 3); }
+
+/* Flat wall terms only on the axes of the wall mask. */
+static int flat_wall(int a) { return (g_walls >> a) & 1; }
+
+/* Container radius: half the smallest box edge over its axes. */
+static double container_R(int d, const double* L)
+{
+    double R = INFINITY;
+    for (int a = 0; a < d; ++a)
+        if (in_container(a, d) && 0.5 * L[a] < R) R = 0.5 * L[a];
+    return R;
+}
+
+/* Distance from x to the container's axis or centre over its axes, and the
+ * offsets x_a - L_a/2. */
+static double container_dist(const double* x, int d, const double* L, double* off)
+{
+    double s2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+        off[a] = in_container(a, d) ? x[a] - 0.5 * L[a] : 0.0;
+        s2 = s2 + off[a] * off[a];
+    }
+    return sqrt(s2);
+}
 
 /* Contact diameter of a sphere at scale kappa: kappa D^0 for a mobile sphere,
  * the fixed -D0 for a frozen one (D0 < 0). */
@@ -163,7 +205,11 @@ int orc_place(uint64_t seed, long n, int d, const double* L, const double* D0, d
                 if (cls[i] != k || placed[i]) continue;
                 keep[i] = 1;
                 for (int a = 0; a < d; ++a)   /* a candidate must not meet a wall either */
-                    if (walled(a) && (cand[d * i + a] < rad[i] || L[a] - cand[d * i + a] < rad[i])) keep[i] = 0;
+                    if (flat_wall(a) && (cand[d * i + a] < rad[i] || L[a] - cand[d * i + a] < rad[i])) keep[i] = 0;
+                if (g_container) {
+                    double off[3];
+                    if (container_R(d, L) - container_dist(&cand[d * i], d, L, off) < rad[i]) keep[i] = 0;
+                }
                 for (long j = 0; j < n && keep[i]; ++j) {
                     if (j == i) continue;
                     if (placed[j]) {
@@ -247,12 +293,21 @@ static double box_volume(int d, const double* L)
     return d == 2 ? L[0] * L[1] : (L[0] * L[1]) * L[2];
 }
 
+/* Volume (area when d = 2) the spheres fill: the container's, else the box's. */
+static double solid_volume(int d, const double* L)
+{
+    double R = container_R(d, L);
+    if (g_container == 1) return d == 2 ? (ORC_PI * R) * R : (((4.0 / 3.0) * ORC_PI) * ((R * R) * R));
+    if (g_container == 2) return ((ORC_PI * R) * R) * L[2];
+    return box_volume(d, L);
+}
+
 /* kappa such that the solid-volume fraction of {kappa D_i^0} equals phi0
  * (mobile spheres only: a frozen sphere's term is 0). */
 double orc_kappa0(const double* D0, long n, int d, const double* L, double phi0)
 {
     double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double V = box_volume(d, L), k;
+    double V = solid_volume(d, L), k;
     if (d == 2) {
         for (long i = 0; i < n; ++i) { double D = mobile_part(D0[i]); t[i] = D * D; }
         k = sqrt((phi0 * V) / ((ORC_PI / 4.0) * orc_tree_sum(t, n)));
@@ -607,19 +662,21 @@ static void row_add(rowacc* a, long i, long j, const double* x, const double* D0
     if (delta > a->md) a->md = delta;
 }
 
-/* Row i's wall terms, after its pairs: for every walled axis a, the wall at 0
- * (h = x_a) then the wall at L_a (h = L_a - x_a).  rad = kappa D^0/2 (F/2
+/* Row i's wall terms, after its pairs: for every axis a of the flat-wall
+ * mask, the wall at 0 (h = x_a) then the wall at L_a (h = L_a - x_a); then the
+ * curved container, h = R - |x - c| over its axes.  rad = kappa D^0/2 (F/2
  * frozen), delta = 1 - h/rad; when delta > 0:
- *   d E / d x_a = -+ eps delta / rad (mobile rows; the wall at 0 pushes to +x_a),
+ *   d E / d x_a = eps delta / rad * (- d h / d x_a)   (mobile rows: -+1 for the
+ *   flat walls, (x_a - c_a)/|x - c| for the container, nothing at its centre),
  *   e_i += eps/2 delta^2,  k_i += eps delta (1 - delta)/kappa (mobile),
  * the latter from d delta / d kappa = (h/rad)/kappa. */
 static void row_walls(rowacc* acc, long i, const double* x, const double* D0, int d, const double* L, double kappa,
                       double eps)
 {
-    if (!g_walls) return;
+    if (!g_walls && !g_container) return;
     double rad = D0[i] > 0.0 ? kappa * (0.5 * D0[i]) : 0.5 * (-D0[i]);
     for (int a = 0; a < d; ++a) {
-        if (!walled(a)) continue;
+        if (!flat_wall(a)) continue;
         for (int side = 0; side < 2; ++side) {
             double h = side == 0 ? x[d * i + a] : L[a] - x[d * i + a];
             double delta = 1.0 - h / rad;
@@ -627,6 +684,25 @@ static void row_walls(rowacc* acc, long i, const double* x, const double* D0, in
             if (D0[i] > 0.0) {
                 double f = (eps * delta) / rad;
                 acc->g[a] = side == 0 ? acc->g[a] - f : acc->g[a] + f;
+                acc->k = acc->k + ((eps * delta) * (1.0 - delta)) / kappa;
+            }
+            acc->e = acc->e + (0.5 * eps) * (delta * delta);
+            if (delta > acc->md) acc->md = delta;
+        }
+    }
+    if (g_container) {
+        /* curved wall: h = R - |x - c|; d h / d x_a = -(x_a - c_a)/|x - c| */
+        double off[3];
+        double rc = container_dist(&x[d * i], d, L, off);
+        double h = container_R(d, L) - rc;
+        double delta = 1.0 - h / rad;
+        if (delta > 0.0) {
+            if (D0[i] > 0.0) {
+                if (rc > 0.0) {
+                    double f = ((eps * delta) / rad) / rc;
+                    for (int a = 0; a < d; ++a)
+                        if (in_container(a, d)) acc->g[a] = acc->g[a] + f * off[a];
+                }
                 acc->k = acc->k + ((eps * delta) * (1.0 - delta)) / kappa;
             }
             acc->e = acc->e + (0.5 * eps) * (delta * delta);
@@ -769,11 +845,18 @@ double orc_shrink_kappa(const double* x, const double* D0, long n, int d, const 
             }
             if (q < kc) kc = q;
         }
-    if (g_walls)
+    if (g_walls || g_container)
         for (long i = 0; i < n; ++i) {
             if (!(D0[i] > 0.0)) continue;
+            if (g_container) {
+                double off[3];
+                double h = container_R(d, L) - container_dist(&x[d * i], d, L, off);
+                double q = (2.0 * h) / D0[i];
+                if (q < 0.0) q = 0.0;
+                if (q < kc) kc = q;
+            }
             for (int a = 0; a < d; ++a) {
-                if (!walled(a)) continue;
+                if (!flat_wall(a)) continue;
                 for (int side = 0; side < 2; ++side) {
                     double h = side == 0 ? x[d * i + a] : L[a] - x[d * i + a];
                     double q = (2.0 * h) / D0[i];
@@ -792,7 +875,7 @@ double orc_phi(const double* D0, long n, int d, const double* L, double kappa)
 {
     double* t = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double* f = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double V = box_volume(d, L), phi;
+    double V = solid_volume(d, L), phi;
     if (d == 2) {
         for (long i = 0; i < n; ++i) {
             double D = mobile_part(D0[i]), F = mobile_part(-D0[i]);
@@ -921,8 +1004,9 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
     int d = p->d;
     const double* L = p->L;
     if (n < 1 || (d != 2 && d != 3)) return 1;
-    int walls_before = g_walls;
+    int walls_before = g_walls, container_before = g_container;
     g_walls = p->walls;
+    g_container = p->container;
     long nd = n * d;
     double* x = (double*)malloc(sizeof(double) * (size_t)nd);
     double* m = (double*)calloc((size_t)nd, sizeof(double));
@@ -1009,6 +1093,7 @@ int orc_run(const orc_params* p, const double* D0, long n, uint64_t seed,
     }
 done:
     g_walls = walls_before;
+    g_container = container_before;
     free(x); free(m); free(v); free(g); free(xb); free(rowptr); free(col);
     return status;
 }

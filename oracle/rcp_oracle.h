@@ -48,6 +48,8 @@ typedef struct {
                             (sigma0 is still that of kappa_0); 0: kappa_0 */
     int    walls;        /* bit a set: flat hard walls at 0 and L_a bound axis a
                             (no minimum image, no wrap); 0: periodic box */
+    int    container;    /* curved wall: 0 none, 1 ball (disk when d = 2), 2 cylinder
+                            about z; radius min L_a/2 over its axes, box centre */
 } orc_params;
 
 typedef struct {
@@ -70,6 +72,8 @@ typedef struct {
  * parameter's mask for the run. */
 void   orc_set_walls(int mask);
 int    orc_get_walls(void);
+void   orc_set_container(int type);   /* 0 none, 1 ball / disk, 2 cylinder about z */
+int    orc_get_container(void);
 
 /* ---- input-side primitives ---- */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
