@@ -228,6 +228,62 @@ def bench_autograd(rcp, torch, reps: int = 20):
             "fwd_bwd_per_s_mixed": out["mixed"]}
 
 
+def bench_rows(rcp, torch):
+    """The widened rows on the binary64 path, each beside the oracle (as it
+    stands, one host thread) on the same workload:
+      cascade: three classes, diameters 3 : 1.5 : 1, 160 / 480 / 800 spheres,
+               box 15, seed 3 -- the whole rcp_cascade (five stages) against
+               oracle.cascade, with the stage phi compared;
+      walls / container: lognormal N = 2e5 (sigma_ln 0.5, S = 10) at phi 0.5
+               from uniform positions -- 20 iterations launched one by one
+               (rcp_profile) with a periodic box, flat walls on every axis and
+               a ball container, and 3 oracle iterations of each."""
+    import oracle
+    out = {}
+    D0 = np.concatenate([np.full(160, 3.0), np.full(480, 1.5), np.full(800, 1.0)])
+    cls = np.concatenate([np.zeros(160, int), np.ones(480, int), np.full(800, 2)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, dm, phi, iters = rcp.rcp_cascade(D0, cls, box=15.0, seed=3)
+    gpu_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    xo, do, log = oracle.cascade(D0, cls, seed=3, L=15.0)
+    cpu_s = time.perf_counter() - t0
+    out["cascade"] = {"workload": "3 classes 3:1.5:1, 160/480/800 spheres, box 15", "stages": len(phi),
+                      "phi": [float(v) for v in phi], "adam_steps": int(iters.sum()),
+                      "gpu_s": gpu_s, "gpu_steps_per_s": float(iters.sum()) / gpu_s,
+                      "oracle_s": cpu_s, "speedup": cpu_s / gpu_s,
+                      "bit_identical": bool(np.array_equal(x, xo) and np.array_equal(dm, do)
+                                            and list(phi) == [f for _, _, f, _ in log])}
+    from paper_2608_12235_b300 import inputs
+    D = inputs.lognormal(200_000, 0.5, 10.0)
+    xs = oracle.init_positions(0, D.size)
+    rows = {}
+    for name, walls, cont in (("periodic", 0, 0), ("walls_xyz", 7, 0), ("ball", 0, 1)):
+        p = rcp.Packing(D, box=1.0, seed=0, walls=walls, container=cont)
+        with oracle.walls(walls, cont):
+            k = oracle.kappa0(D, 1.0, 0.5)
+        p.set_positions(xs, k)
+        rcp.rcp_profile(p.h, 3)
+        ms_pair, ms_iter, n_pair = rcp.rcp_profile(p.h, 20)
+        ms_pair, ms_iter = ms_pair / max(n_pair, 1), ms_iter / 20.0
+        p.close()
+        xc = xs.copy()
+        with oracle.walls(walls, cont):
+            k0 = oracle.kappa0(D, 1.0, 0.05)
+            m = oracle.moments(D)
+            dref = m[2] / m[1]
+            t0 = time.perf_counter()
+            oracle.sample_iterations(D, xc, k, 0.0, 1e-3 * k * dref, 1e-3 * k, 100.0 * (1e-3 * k0) * dref, 3,
+                                     skin_s=0.02)
+            dt = time.perf_counter() - t0
+        rows[name] = {"ms_pair": ms_pair, "ms_iter": ms_iter, "oracle_iters_per_s": 3.0 / dt}
+    for name in ("walls_xyz", "ball"):
+        rows[name]["pair_time_vs_periodic"] = rows[name]["ms_pair"] / rows["periodic"]["ms_pair"]
+    out["boundaries"] = {"workload": "lognormal-n2e5-s10 phi 0.5 uniform", **rows}
+    return out
+
+
 def run_reference(args, w):
     """--impl reference: the CPU oracle on the same workload and metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -264,10 +320,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and autograd measurements")
     ap.add_argument("--batch-iters", type=int, default=300)
+    ap.add_argument("--rows", action="store_true",
+                    help="measure the widened rows (cascade, walls, container) instead; one JSON line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.rows:
+        import torch
+        from paper_2608_12235_b300 import rcp
+        rcp.load()
+        clk = Clocks(0)
+        res = bench_rows(rcp, torch)
+        print(json.dumps({"metric": "widened rows on the binary64 path (GPU beside the oracle)",
+                          "data": "synthetic", **res, "clocks": clk.stop()}))
+        return
 
     import torch
     import torch.distributed as dist

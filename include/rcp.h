@@ -104,6 +104,16 @@ typedef struct {
                                walls.  Positions on walled axes should stay within
                                one box edge of the box.  Only the bits of the d
                                axes; binary64 path only (0: periodic box) */
+    int       container;    /* curved hard wall (Sec. II, Fig. 2): 0 none; 1 a ball
+                               over every axis (a disk when d = 2); 2 a cylinder
+                               about the z axis (d = 3).  Radius R = min L_a/2 over
+                               its axes, centre at the box centre; its axes take no
+                               minimum image or wrap; a sphere with h = R - |x - c|
+                               below its contact radius overlaps the wall by
+                               delta = 1 - h/rad as for a flat wall; kappa_0 and
+                               phi use the container's volume.  Start from
+                               placement = 1 (a uniform draw over the box leaves
+                               spheres outside).  Binary64 path only */
 } rcp_config;
 
 /* When rcp_run returns early. */

@@ -1141,7 +1141,8 @@ long orc_sample_iterations(const orc_params* p, const double* D0, long n, double
         b2 = b2 * p->beta2;
         adam_positions(x, m, v, g, D0, n, d, eta_x, p, b1, b2);
         for (long i = 0; i < n; ++i)
-            for (int a = 0; a < d; ++a) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
+            for (int a = 0; a < d; ++a)
+                if (!walled(a)) x[d * i + a] = orc_wrap(x[d * i + a], L[a]);
         orc_adam_update(&kappa, &mk, &vk, &dEdk, 1, eta_k, p->beta1, p->beta2, p->adam_eps, b1, b2);
         need = need || skin_spent(x, xb, D0, n, d, L, kappa, kb, s, th, sigma0);
     }

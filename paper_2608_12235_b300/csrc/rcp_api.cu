@@ -839,6 +839,8 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     if (Nf > 0 && cfg && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     if (cfg && (cfg->walls & ~((1 << d) - 1))) return RCP_ERR_ARG;   // one bit per axis of the caller
     if (cfg && cfg->walls && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
+    if (cfg && (cfg->container < 0 || cfg->container > 2 || (cfg->container == 2 && d != 3))) return RCP_ERR_ARG;
+    if (cfg && cfg->container && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     const long long N = Nf + Nm;
     for (long long i = 0; i < Nf; ++i) {
         if (!(fixed_d[i] > 0.0) || !std::isfinite(fixed_d[i])) return RCP_ERR_ARG;
@@ -892,10 +894,21 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     }
     c.V = d == 2 ? box[0] * box[1] : (box[0] * box[1]) * box[2];   // area when d = 2
     c.walls = h->cfg.walls;
+    c.container = h->cfg.container;
+    // the container: a ball over the caller's axes (a disk when d = 2) or a
+    // cylinder about z, radius min L_a / 2 over its axes, about the centre
+    c.caxes = c.container == 1 ? (1 << d) - 1 : (c.container == 2 ? 3 : 0);
+    c.bounded = c.walls | c.caxes;
+    c.Rc = INFINITY;
+    for (int a = 0; a < d; ++a)
+        if (((c.caxes >> a) & 1) && 0.5 * box[a] < c.Rc) c.Rc = 0.5 * box[a];
+    if (c.container == 1) c.Vs = d == 2 ? (RCP_PI * c.Rc) * c.Rc : (((4.0 / 3.0) * RCP_PI) * ((c.Rc * c.Rc) * c.Rc));
+    else if (c.container == 2) c.Vs = ((RCP_PI * c.Rc) * c.Rc) * box[2];
+    else c.Vs = c.V;
     // the periodic-image rule concerns the periodic axes of the caller only
     c.Lmin = INFINITY;
     for (int a = 0; a < d; ++a)
-        if (!((c.walls >> a) & 1) && box[a] < c.Lmin) c.Lmin = box[a];
+        if (!((c.bounded >> a) & 1) && box[a] < c.Lmin) c.Lmin = box[a];
     c.dim = d;
     c.eps = h->cfg.eps;
     c.beta1 = h->cfg.beta1;
@@ -1005,7 +1018,7 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
             if (d == 2) CKS(tree_sum_D(h, -2, &h->ctl->SF2));
         }
         h->launches += 1;
-        k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.V, d);
+        k_kappa0<<<1, 1, 0, h->stream>>>(h->ctl, h->cfg.phi0, c.Vs, d);
         CKL();
         CKS(sync_ctl(h));
         h->SD = h->ctl_h->SD;

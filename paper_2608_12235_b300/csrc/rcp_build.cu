@@ -431,12 +431,21 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
         // a placement candidate also meets frozen spheres of finer classes,
         // which are placed before any class is
         const int kend = (PLACE && c.nfrozen > 0) ? ctl->nlev - 1 : li;
-        if (PLACE && c.walls) {   // a candidate must keep off the walls too (distance below rho_i)
+        if (PLACE && (c.walls | c.container)) {   // a candidate must keep off the walls too (distance below rho_i)
             const double4_32a xi = x[i];
             for (int a = 0; a < 3; ++a) {
                 if (!((c.walls >> a) & 1)) continue;
                 const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
                 if (xa < ri || c.L[a] - xa < ri) reject[i] = 1;
+            }
+            if (c.container) {   // distance to the curved wall R - |x - c| over its axes
+                double s2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    if (!((c.caxes >> a) & 1)) continue;
+                    const double o = (a == 0 ? xi.x : (a == 1 ? xi.y : xi.z)) - c.halfL[a];
+                    s2 = s2 + o * o;
+                }
+                if (c.Rc - sqrt(s2) < ri) reject[i] = 1;
             }
         }
         for (int k = 0; k <= kend; ++k) {
@@ -452,8 +461,8 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
                 const float fn = (float)ng[a];
                 int l = (int)floorf((u3[a] - Ru) * fn);
                 int h = (int)floorf((u3[a] + Ru) * fn);
-                if ((c.walls >> a) & 1) {
-                    // walled axis, no wrap: clamp the window (the edge cells
+                if ((c.bounded >> a) & 1) {
+                    // bounded axis, no wrap: clamp the window (the edge cells
                     // also hold the spheres beyond the walls)
                     const int top = (int)ng[a] - 1;
                     l = l < 0 ? 0 : (l > top ? top : l);
@@ -479,9 +488,9 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
                         const uint2 range = row[xx];
                         for (unsigned int t = range.x; t < range.y; ++t) {
                             const float4 uj = xsf[t];
-                            const float dx = ((c.walls & 1) ? ui.x - uj.x : wrap_unit(ui.x - uj.x)) * L0;
-                            const float dy = ((c.walls & 2) ? ui.y - uj.y : wrap_unit(ui.y - uj.y)) * L1;
-                            const float dz = ((c.walls & 4) ? ui.z - uj.z : wrap_unit(ui.z - uj.z)) * L2;
+                            const float dx = ((c.bounded & 1) ? ui.x - uj.x : wrap_unit(ui.x - uj.x)) * L0;
+                            const float dy = ((c.bounded & 2) ? ui.y - uj.y : wrap_unit(ui.y - uj.y)) * L1;
+                            const float dz = ((c.bounded & 4) ? ui.z - uj.z : wrap_unit(ui.z - uj.z)) * L2;
                             const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
                             const float cut = ui.w + uj.w;
                             const float hi = (cut * up + Eabs) * up;
@@ -493,9 +502,9 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
                             if (!in) {
                                 // the band: exact binary64 predicate
                                 const double4_32a xi = x[i], xj = x[j];
-                                double ex = (c.walls & 1) ? xi.x - xj.x : min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
-                                double ey = (c.walls & 2) ? xi.y - xj.y : min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
-                                double ez = (c.walls & 4) ? xi.z - xj.z : min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
+                                double ex = (c.bounded & 1) ? xi.x - xj.x : min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
+                                double ey = (c.bounded & 2) ? xi.y - xj.y : min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
+                                double ez = (c.bounded & 4) ? xi.z - xj.z : min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
                                 double d2 = ex * ex + ey * ey + ez * ez;
                                 double cc = ri + rho[j];
                                 in = d2 < cc * cc;

@@ -95,6 +95,11 @@ struct RcpConst {
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
     long long nfrozen;         // frozen spheres (binary64 path only; 0 otherwise)
     int walls;                 // bit a: flat walls at 0 and L_a bound axis a (binary64 path only)
+    int container;             // curved wall: 0 none, 1 ball (disk when d = 2), 2 cylinder about z
+    int caxes;                 // the container's axes (bit a)
+    int bounded;               // axes without minimum image or wrap: flat walls and the container's
+    double Rc;                 // container radius: min L_a / 2 over its axes (centre L / 2)
+    double Vs;                 // volume the spheres fill (kappa_0, phi): the container's, else V
 };
 
 // Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
@@ -122,6 +127,8 @@ struct PackDev {
 };
 
 enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
+
+#define RCP_PI 3.141592653589793
 
 // ---- frozen spheres ----
 // A stage of the sequential cascade (Sec. IV) holds the coarser classes

@@ -12,7 +12,6 @@
 // of which non-overlapping pairs happen to be listed.
 #include "rcp_internal.cuh"
 
-#define RCP_PI 3.141592653589793
 
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea & Flood 2014): output k of the stream seeded with
@@ -42,16 +41,30 @@ __device__ __forceinline__ double min_image(double t, double L, double h)
 }
 
 // Component a of x_i - x_j: minimum image on a periodic axis, the plain
-// difference on an axis bounded by flat walls (bit a of c.walls).
+// difference on an axis bounded by flat walls or the container (c.bounded).
 __device__ __forceinline__ double axis_diff(const RcpConst& c, int a, double t)
 {
-    return ((c.walls >> a) & 1) ? t : min_image(t, c.L[a], c.halfL[a]);
+    return ((c.bounded >> a) & 1) ? t : min_image(t, c.L[a], c.halfL[a]);
 }
 
-// Coordinate a after a step: wrapped on a periodic axis, kept on a walled one.
+// Coordinate a after a step: wrapped on a periodic axis, kept on a bounded one.
 __device__ __forceinline__ double axis_wrap(const RcpConst& c, int a, double x)
 {
-    return ((c.walls >> a) & 1) ? x : wrap_step(x, c.L[a]);
+    return ((c.bounded >> a) & 1) ? x : wrap_step(x, c.L[a]);
+}
+
+// Distance from a sphere's centre to the container's centre (ball) or axis
+// (cylinder), with the offsets x_a - L_a/2 over the container's axes (0 on
+// the others); summed over the axes in order.
+__device__ __forceinline__ double container_dist(const RcpConst& c, const double4_32a& xi, double off[3])
+{
+    double s2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
+        off[a] = ((c.caxes >> a) & 1) ? xa - c.halfL[a] : 0.0;
+        if ((c.caxes >> a) & 1) s2 = s2 + off[a] * off[a];
+    }
+    return sqrt(s2);
 }
 
 // Flat hard walls at 0 and L_a on every axis a whose bit is set in c.walls
@@ -76,6 +89,26 @@ __device__ __forceinline__ void wall_terms(const RcpConst& c, double kappa, cons
                 const double f = (c.eps * delta) / rad;
                 double& ga = a == 0 ? g0 : (a == 1 ? g1 : g2);
                 ga = side == 0 ? ga - f : ga + f;
+                k = k + ((c.eps * delta) * (1.0 - delta)) / kappa;
+            }
+            e = e + (0.5 * c.eps) * (delta * delta);
+            if (delta > md) md = delta;
+        }
+    }
+    if (c.container) {
+        // the curved wall: h = R - |x - c|, d h / d x_a = -(x_a - c_a) / |x - c|
+        double off[3];
+        const double rc = container_dist(c, xi, off);
+        const double h = c.Rc - rc;
+        const double delta = 1.0 - h / rad;
+        if (delta > 0.0) {
+            if (mob) {
+                if (rc > 0.0) {
+                    const double f = ((c.eps * delta) / rad) / rc;
+                    if (c.caxes & 1) g0 = g0 + f * off[0];
+                    if (c.caxes & 2) g1 = g1 + f * off[1];
+                    if (c.caxes & 4) g2 = g2 + f * off[2];
+                }
                 k = k + ((c.eps * delta) * (1.0 - delta)) / kappa;
             }
             e = e + (0.5 * c.eps) * (delta * delta);
@@ -314,7 +347,7 @@ __global__ void k_set_positions(long long N, RcpConst c, const double* xin, cons
             continue;
         }
         double v = xin[c.dim * u + a];
-        if ((c.walls >> a) & 1) {   // walled axis: the caller's coordinate as it is
+        if ((c.bounded >> a) & 1) {   // bounded axis: the caller's coordinate as it is
             p[a] = v;
             continue;
         }
@@ -466,7 +499,7 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
                 if (delta > md) md = delta;
             }
         }
-        if (c.walls) wall_terms(c, kappa, xi, g0, g1, g2, e, k, md);
+        if (c.walls | c.container) wall_terms(c, kappa, xi, g0, g1, g2, e, k, md);
         if (mode == RCP_MODE_ADAM && !(xi.w > 0.0)) {
             xout[i] = xi;   // frozen: position and moments stay
         } else if (mode == RCP_MODE_ADAM) {
@@ -746,7 +779,14 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
             }
             if (qq < q) q = qq;
         }
-        if (c.walls && xi.w > 0.0)   // a mobile sphere touches a wall at kappa = 2h / D^0
+        if ((c.walls | c.container) && xi.w > 0.0) {   // a mobile sphere touches a wall at kappa = 2h / D^0
+            if (c.container) {
+                double off[3];
+                const double h = c.Rc - container_dist(c, xi, off);
+                double qq = (2.0 * h) / xi.w;
+                if (qq < 0.0) qq = 0.0;
+                if (qq < q) q = qq;
+            }
             for (int a = 0; a < 3; ++a) {
                 if (!((c.walls >> a) & 1)) continue;
                 const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
@@ -757,6 +797,7 @@ k_shrink(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                     if (qq < q) q = qq;
                 }
             }
+        }
     }
     // block minimum through max of the negated value
     double bm = -block_max(-q, sh);
@@ -773,6 +814,6 @@ __global__ void k_shrink_final(RcpCtl* ctl, RcpConst c)
     if (q < kc) kc = q;
     kc = kc * (1.0 - 0x1.0p-50);
     ctl->kappa_c = kc;
-    if (c.dim == 2) ctl->phi = ((((RCP_PI / 4.0) * (kc * kc)) * ctl->SD2) + (RCP_PI / 4.0) * ctl->SF2) / c.V;
-    else ctl->phi = ((((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) + (RCP_PI / 6.0) * ctl->SF3) / c.V;
+    if (c.dim == 2) ctl->phi = ((((RCP_PI / 4.0) * (kc * kc)) * ctl->SD2) + (RCP_PI / 4.0) * ctl->SF2) / c.Vs;
+    else ctl->phi = ((((RCP_PI / 6.0) * ((kc * kc) * kc)) * ctl->SD3) + (RCP_PI / 6.0) * ctl->SF3) / c.Vs;
 }

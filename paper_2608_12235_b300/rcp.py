@@ -35,7 +35,8 @@ class rcp_config(C.Structure):
                 ("lr_kappa", C.c_double), ("delta_star0", C.c_double), ("tol", C.c_double), ("Y", C.c_int),
                 ("X", C.c_int), ("n_min", C.c_longlong), ("n_down", C.c_int), ("n_cycles", C.c_int),
                 ("max_iters", C.c_longlong), ("chunk", C.c_int), ("cell_occupancy", C.c_double),
-                ("placement", C.c_int), ("place_rounds", C.c_int), ("walls", C.c_int)]
+                ("placement", C.c_int), ("place_rounds", C.c_int), ("walls", C.c_int),
+                ("container", C.c_int)]
 
 
 class rcp_stop(C.Structure):

@@ -83,3 +83,14 @@ def test_walls_are_checked_before_touching_the_gpu(lib):
     with pytest.raises(rcp.RcpError) as e:   # no z axis when d = 2
         rcp.rcp_create(np.ones(4), 1.0, 0, rcp.rcp_config_default(walls=4), d=2)
     assert e.value.status == 1
+
+
+def test_container_is_checked_before_touching_the_gpu(lib):
+    from paper_2608_12235_b300 import rcp
+    import numpy as np
+    for cfg, d, want in [(rcp.rcp_config_default(container=3), 3, 1),
+                         (rcp.rcp_config_default(container=2), 2, 1),   # a cylinder needs z
+                         (rcp.rcp_config_default(container=1, precision=rcp.RCP_MIXED), 3, 9)]:
+        with pytest.raises(rcp.RcpError) as e:
+            rcp.rcp_create(np.ones(4), 1.0, 0, cfg, d=d)
+        assert e.value.status == want

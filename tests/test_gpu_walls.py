@@ -93,3 +93,47 @@ def test_seated_stage_inside_walls_bitexact(rcp, orc):
     assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
     assert np.array_equal(p.positions(), ref.x)
     p.close()
+
+
+# ------------------------------------------------------------------ curved walls
+@pytest.mark.parametrize("container,d", [(1, 3), (2, 3), (1, 2)])
+def test_container_list_and_energy_bitexact(rcp, orc, container, d):
+    n = 3000 if d == 3 else 1500
+    rng = np.random.default_rng(container + 7 * d)
+    D0 = inputs.lognormal(n, 0.5, 10.0)
+    x = rng.uniform(0.0, 1.0, (n, d))
+    cax = list(range(d)) if container == 1 else [0, 1]
+    x[:, cax] = rng.uniform(-0.01, 1.01, (n, len(cax)))
+    p = rcp.Packing(D0, box=1.0, seed=1, d=d, container=container)
+    with orc.walls(0, container):
+        k = orc.kappa0(D0, 1.0, 0.3, d=d)
+        k0 = orc.kappa0(D0, 1.0, 0.05, d=d)
+    p.set_positions(x, k)
+    rp, col = p.neighbors()
+    s0 = _sigma0(orc, D0, k0, p.cfg)
+    orp, ocol = orc.list_brute(x, D0, 1.0, k, p.cfg.skin_s, s0, d=d, wall_mask=(0, container))
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    E, g, dk, md = p.energy_grad(0.01)
+    oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, 0.01, d=d, wall_mask=(0, container))
+    assert omd > 0.0
+    assert E == oE and dk == odk and md == omd
+    assert np.array_equal(g, og)
+    p.close()
+
+
+@pytest.mark.parametrize("container,d", [(1, 3), (2, 3), (1, 2)])
+def test_container_run_from_placement_bitexact(rcp, orc, container, d):
+    """The container from App. A's dilute start: placement inside it, then the
+    whole protocol and the shrink, against the oracle."""
+    D0 = inputs.lognormal(500, 0.5, 10.0)
+    with orc.walls(0, container):
+        k0 = orc.kappa0(D0, 1.0, 0.05, d=d)
+    x0, _, _ = orc.place(5, D0, k0, 1.0, d, wall_mask=(0, container))
+    ref = orc.run(D0, seed=5, x0=x0, d=d, container=container)
+    p = rcp.Packing(D0, box=1.0, seed=5, d=d, container=container, placement=1)
+    assert np.array_equal(p.positions(), x0)
+    r = p.run()
+    assert r.stopped and ref.stopped and r.iters == ref.iters
+    assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
+    assert np.array_equal(p.positions(), ref.x)
+    p.close()
