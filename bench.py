@@ -228,7 +228,7 @@ def bench_autograd(rcp, torch, reps: int = 20):
             "fwd_bwd_per_s_mixed": out["mixed"]}
 
 
-def bench_rows(rcp, torch):
+def bench_rows(rcp, torch, large: bool = False):
     """The widened rows on the binary64 path, each beside the oracle (as it
     stands, one host thread) on the same workload:
       cascade: three classes, diameters 3 : 1.5 : 1, 160 / 480 / 800 spheres,
@@ -281,6 +281,26 @@ def bench_rows(rcp, torch):
     for name in ("walls_xyz", "ball"):
         rows[name]["pair_time_vs_periodic"] = rows[name]["ms_pair"] / rows["periodic"]["ms_pair"]
     out["boundaries"] = {"workload": "lognormal-n2e5-s10 phi 0.5 uniform", **rows}
+    if large:
+        # the same grading scaled 70x (about 1e5 spheres, box 15 * 70^(1/3));
+        # the oracle only for a bounded sample: 200 iterations of stage 0
+        f = 70
+        Lb = 15.0 * f ** (1.0 / 3.0)
+        D0 = np.concatenate([np.full(160 * f, 3.0), np.full(480 * f, 1.5), np.full(800 * f, 1.0)])
+        cls = np.concatenate([np.zeros(160 * f, int), np.ones(480 * f, int), np.full(800 * f, 2)])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, dm, phi, iters = rcp.rcp_cascade(D0, cls, box=Lb, seed=3)
+        gpu_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = oracle.run(D0[cls == 0], seed=3, L=Lb, max_iters=200)
+        cpu_s = time.perf_counter() - t0
+        out["cascade_large"] = {"workload": f"3 classes 3:1.5:1, {160 * f}/{480 * f}/{800 * f} spheres, box {Lb:.2f}",
+                                "phi": [float(v) for v in phi], "adam_steps": int(iters.sum()),
+                                "adam_steps_per_stage": [int(v) for v in iters], "gpu_s": gpu_s,
+                                "gpu_steps_per_s": float(iters.sum()) / gpu_s,
+                                "oracle_sample": f"200 iterations of stage 0 ({160 * f} spheres)",
+                                "oracle_stage0_iters_per_s": r.iters / cpu_s}
     return out
 
 
@@ -322,6 +342,7 @@ def main():
     ap.add_argument("--batch-iters", type=int, default=300)
     ap.add_argument("--rows", action="store_true",
                     help="measure the widened rows (cascade, walls, container) instead; one JSON line")
+    ap.add_argument("--rows-large", action="store_true", help="with --rows: also a ~1e5-sphere cascade")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -331,7 +352,7 @@ def main():
         from paper_2608_12235_b300 import rcp
         rcp.load()
         clk = Clocks(0)
-        res = bench_rows(rcp, torch)
+        res = bench_rows(rcp, torch, large=args.rows_large)
         print(json.dumps({"metric": "widened rows on the binary64 path (GPU beside the oracle)",
                           "data": "synthetic", **res, "clocks": clk.stop()}))
         return
