@@ -137,3 +137,27 @@ def test_container_run_from_placement_bitexact(rcp, orc, container, d):
     assert r.kappa_c == ref.kappa_c and r.phi == ref.phi
     assert np.array_equal(p.positions(), ref.x)
     p.close()
+
+
+def test_batch_of_bounded_and_seated_packings_runs_as_solo(rcp):
+    """Walled, contained and seated packings advanced by the batched kernels
+    stop at the same iteration, kappa_c and phi as when each runs alone."""
+    g = (np.arange(2) + 0.25) * 4.0
+    X = np.array([[a, b, c] for a in g for b in g for c in g])
+    F = np.full(len(X), 1.6)
+
+    def make():
+        return [rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=1, walls=0b111),
+                rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=2, container=1, placement=1),
+                rcp.Packing(np.linspace(0.6, 1.0, 200), box=8.0, seed=4, fixed_d=F, fixed_x=X, placement=1)]
+    solo = make()
+    ref = [p.run() for p in solo]
+    packs = make()
+    b = rcp.Batch(packs)
+    res = b.run()
+    for r, q, p, s in zip(res, ref, packs, solo):
+        assert r.stopped and r.iters == q.iters and r.phi == q.phi and r.kappa_c == q.kappa_c
+        assert np.array_equal(p.positions(), s.positions())
+    b.close()
+    for p in solo + packs:
+        p.close()
