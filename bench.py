@@ -281,6 +281,21 @@ def bench_rows(rcp, torch, large: bool = False):
     for name in ("walls_xyz", "ball"):
         rows[name]["pair_time_vs_periodic"] = rows[name]["ms_pair"] / rows["periodic"]["ms_pair"]
     out["boundaries"] = {"workload": "lognormal-n2e5-s10 phi 0.5 uniform", **rows}
+    # per-iteration cost of whole runs at small N, binary64 beside mixed: what
+    # bounds the cascade's stages
+    small = {}
+    for name, D, L in (("n160-d3-box15", np.full(160, 3.0), 15.0), ("n1440-d1-box10", np.full(1440, 1.0), 10.0),
+                       ("n20000-d1-box24", np.full(20000, 1.0), 24.0)):
+        for prec in (rcp.RCP_FP64, rcp.RCP_MIXED):
+            p = rcp.Packing(D, box=L, seed=3, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = p.run()
+            dt = time.perf_counter() - t0
+            p.close()
+            small[f"{name}-{'fp64' if prec == rcp.RCP_FP64 else 'mixed'}"] = {
+                "iters": r.iters, "rebuilds": r.rebuilds, "us_per_iter": dt / r.iters * 1e6}
+    out["small_n_runs"] = small
     if large:
         # the same grading scaled 70x (about 1e5 spheres, box 15 * 70^(1/3));
         # the oracle only for a bounded sample: 200 iterations of stage 0
