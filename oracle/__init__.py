@@ -356,6 +356,17 @@ def run(D0, seed=0, x0=None, trace_len=0, **params) -> RunResult:
 
 
 # ---------------------------------------------------------------- the cascade
+def _boundary(wall_mask):
+    """(flat-wall mask, container) from a mask or a (mask, container) pair."""
+    return tuple(wall_mask) if isinstance(wall_mask, tuple) else (int(wall_mask), 0)
+
+
+def _bounded_axes(bd, d):
+    """Axes without minimum image or wrap: the flat walls' and the container's."""
+    mask, container = bd
+    return mask | ((1 << d) - 1 if container == 1 else (3 if container == 2 else 0))
+
+
 def seated_state(fixed_d, fixed_x, D0, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, phi0=0.05,
                  wall_mask=0):
     """Initial state of a seated packing (Sec. IV: a finer class seated into
@@ -371,12 +382,15 @@ def seated_state(fixed_d, fixed_x, D0, seed=0, L=1.0, d=3, placement=0, place_ro
     box = _box(L, d)
     x = init_positions(seed, n, L, d)
     fx = f64(fixed_x).reshape(nf, d)
+    bd = _boundary(wall_mask)
+    bounded = _bounded_axes(bd, d)
     for i in range(nf):
         for a in range(d):
-            x[i, a] = fx[i, a] if (wall_mask >> a) & 1 else wrap(fx[i, a], box[a])
+            x[i, a] = fx[i, a] if (bounded >> a) & 1 else wrap(fx[i, a], box[a])
     if placement:
-        k0 = kappa0(Dall, L, phi0, d)
-        x, _, r = place(seed, Dall, k0, L, d, place_rounds, x_frozen=x, wall_mask=wall_mask)
+        with walls(*bd):
+            k0 = kappa0(Dall, L, phi0, d)
+        x, _, r = place(seed, Dall, k0, L, d, place_rounds, x_frozen=x, wall_mask=bd)
         if r < 0:
             raise RuntimeError("placement did not finish")
     return Dall, x
@@ -399,7 +413,7 @@ def cascade(D0, cls, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, **para
     n = D0.size
     nclass = int(cls.max()) + 1
     phi0 = params.pop("phi0", 0.05)
-    wall_mask = params.get("walls", 0)
+    wall_mask = (params.get("walls", 0), params.get("container", 0))
     order = []          # caller indices of the packed spheres, in stage order
     diam = None         # their contact diameters
     xs = None           # their positions
@@ -408,7 +422,8 @@ def cascade(D0, cls, seed=0, L=1.0, d=3, placement=0, place_rounds=10000, **para
         new = np.flatnonzero(cls == s_)
         if s_ == 0:
             if placement:
-                k0 = kappa0(D0[new], L, phi0, d)
+                with walls(*wall_mask):
+                    k0 = kappa0(D0[new], L, phi0, d)
                 x0, _, r = place(seed, D0[new], k0, L, d, place_rounds, wall_mask=wall_mask)
                 if r < 0:
                     raise RuntimeError("placement did not finish")

@@ -163,3 +163,25 @@ def test_cascade_climbs_stage_by_stage(orc):
     assert np.ptp(diam[:nc]) == 0.0 and np.ptp(diam[nc:]) == 0.0
     assert _min_gap(x, diam, 12.0) >= 0.0
     assert phi[2] == pytest.approx((math.pi / 6) * (diam ** 3).sum() / 12.0 ** 3, rel=1e-12)
+
+
+def test_seated_run_inside_walls_and_a_container(orc):
+    """Frozen spheres inside a walled box and inside a ball: the mobile ones
+    end inside the boundary, the frozen ones unmoved, nothing overlaps."""
+    F = np.full(8, 1.6)
+    g = (np.arange(2) + 0.25) * 4.0
+    X = np.array([[a, b, c] for a in g for b in g for c in g])
+    D = np.linspace(0.6, 1.0, 150)
+    for walls, container, Xf in ((0b011, 0, X), (0, 1, 4.0 + 0.45 * (X - 4.0))):
+        Dall, x0 = orc.seated_state(F, Xf, D, seed=4, L=8.0, placement=1, wall_mask=(walls, container))
+        res = orc.run(Dall, seed=4, x0=x0, L=8.0, walls=walls, container=container)
+        assert res.stopped and np.array_equal(res.x[:8], Xf)
+        E, g_, dk, md = orc.energy_grad(res.x, Dall, 8.0, res.kappa_c, 0.0, wall_mask=(walls, container))
+        assert md == 0.0
+        rad = 0.5 * res.kappa_c * D
+        xm = res.x[8:]
+        if walls:
+            for a in (0, 1):
+                assert (xm[:, a] >= rad).all() and (8.0 - xm[:, a] >= rad).all()
+        else:
+            assert (np.sqrt(((xm - 4.0) ** 2).sum(axis=1)) + rad <= 4.0).all()
