@@ -122,3 +122,16 @@ def test_cascade_three_classes_bitexact(rcp, orc):
     assert list(phi) == [f for _, _, f, _ in log]
     assert list(iters) == [t for _, _, _, t in log]
     assert np.array_equal(dm, do) and np.array_equal(x, xo)
+
+
+def test_cascade_in_a_ball_bitexact(rcp, orc):
+    """A two-class cascade inside a ball container (every axis bounded, so
+    no periodic-image limit on the coarse class), placement on."""
+    D0 = np.concatenate([np.full(24, 4.0), np.full(120, 1.0)])
+    cls = np.concatenate([np.zeros(24, int), np.ones(120, int)])
+    xo, do, log = orc.cascade(D0, cls, seed=5, L=14.0, placement=1, container=1)
+    cfg = rcp.rcp_config_default(placement=1, container=1)
+    x, dm, phi, iters = rcp.rcp_cascade(D0, cls, box=14.0, seed=5, cfg=cfg)
+    assert list(phi) == [f for _, _, f, _ in log]
+    assert list(iters) == [t for _, _, _, t in log]
+    assert np.array_equal(dm, do) and np.array_equal(x, xo)
