@@ -58,6 +58,8 @@ struct rcp_ctx {
     MixRec* rb = nullptr;   // records at the last build
     double* g = nullptr;      // [3N] gradient output / input buffer
     double* part_e = nullptr; // block partials
+    double* row_e = nullptr;  // binary64 warp-per-row kernel: e_i and k_i of every row
+    double* row_k = nullptr;
     double* part_k = nullptr;
     double* part_e2 = nullptr;
     double* part_k2 = nullptr;
@@ -528,13 +530,17 @@ unsigned int launch_blocks(const rcp_ctx* h)
     return pair_blocks(h);
 }
 
-// Reduce the pair kernel's block partials to <= 8192 entries; returns the
-// buffers and count to hand to k_kappa_step.
-void prereduce(rcp_ctx* h, const double** pe, const double** pk, long long* nb)
+// Binary64 packings up to RCP_WARP_ROW_MAX_N spheres take a warp per row
+// (k_pair64_warp), which leaves one e_i and k_i per row instead of block
+// partials.
+bool warp_rows(const rcp_ctx* h) { return h->c.canon && h->row_e != nullptr; }
+
+// Reduce the pair kernel's partials a, b (n of each) to <= 8192 entries by
+// tree passes over aligned groups (the canonical order); returns the buffers
+// and count to hand to k_kappa_step.
+void prereduce(rcp_ctx* h, const double* a, const double* b, long long n, const double** pe, const double** pk,
+               long long* nb)
 {
-    const double* a = h->part_e;
-    const double* b = h->part_k;
-    long long n = launch_blocks(h);
     bool flip = false;
     while (n > 8192) {
         unsigned int g = rcp_ceil_div(n, RCP_TREE);
@@ -569,19 +575,24 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
         k_pair_mixed<<<nb + h->c.long_blocks, RCP_PAIR_THREADS, 0, h->stream>>>(
             h->ctl, h->c, h->m32, h->v32, h->rA, h->rB, h->rowptr, h->col, h->long_rows, h->rb, h->part_e, h->part_k,
             mode, h->g);
+    } else if (warp_rows(h)) {
+        k_pair64_warp<<<rcp_ceil_div(h->N * 32, RCP_WARP_ROW_THREADS), RCP_WARP_ROW_THREADS, 0, h->stream>>>(
+            h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr, h->col, h->xb, h->row_e, h->row_k, mode, h->g);
     } else {
         k_pair64<<<nb, RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr,
                                                           h->col, h->xb, h->part_e, h->part_k, mode, h->g);
     }
     if (ev) cudaEventRecord(ev[1], h->stream);
+    const bool wr = warp_rows(h);
+    const long long n0 = wr ? h->N : (long long)launch_blocks(h);
     const double* pe;
     const double* pk;
     long long n;
-    prereduce(h, &pe, &pk, &n);
+    prereduce(h, wr ? h->row_e : h->part_e, wr ? h->row_k : h->part_k, n0, &pe, &pk, &n);
     k_kappa_step<<<1, 1024, kappa_smem(n), h->stream>>>(h->ctl, h->c, pe, pk, n, mode);
     if (ev) cudaEventRecord(ev[2], h->stream);
     int passes = 0;
-    for (long long m = launch_blocks(h); m > 8192; m = (m + RCP_TREE - 1) / RCP_TREE) ++passes;
+    for (long long m = n0; m > 8192; m = (m + RCP_TREE - 1) / RCP_TREE) ++passes;
     return 2 + passes;
 }
 
@@ -738,7 +749,7 @@ rcp_status rcp_destroy(rcp_handle h)
     void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
                     h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->cells, h->cnt,
                     h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->hist, h->scan_tmp, h->perm, h->perm_alt, h->D0_alt, h->rho_alt,
-                    h->lvl_alt};
+                    h->lvl_alt, h->row_e, h->row_k};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->ctl_h) cudaFreeHost(h->ctl_h);
@@ -956,6 +967,10 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         } else {
             CKS(dalloc(h, &h->m64, 3 * n));
             CKS(dalloc(h, &h->v64, 3 * n));
+            if (N <= RCP_WARP_ROW_MAX_N) {
+                CKS(dalloc(h, &h->row_e, n));
+                CKS(dalloc(h, &h->row_k, n));
+            }
             CK(cudaMemsetAsync(h->m64, 0, sizeof(double) * 3 * n, h->stream));
             CK(cudaMemsetAsync(h->v64, 0, sizeof(double) * 3 * n, h->stream));
         }

@@ -19,6 +19,9 @@
 #define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
 #define RCP_LONG_ROW 32        // default: rows longer than this get a warp in the mixed pair kernel
 #define RCP_LONG_BLOCKS_MAX 592  // most blocks (8 warps each) that loop over the long rows
+#define RCP_WARP_ROW_THREADS 128   // binary64 warp-per-row kernel: 4 rows per block
+#define RCP_WARP_ROW_MAX_N 4096    // binary64 packings up to this size take a warp per row (measured
+                                   // crossover: 2.5x faster at N = 1440, 2.8x slower at N = 2e4)
 
 // Device-resident control block of one packing.  Kernels read the optimiser
 // scalars and the current rung's values from here, so one captured graph
@@ -230,6 +233,9 @@ struct BatchStat {
 __global__ void k_batch_set(const PackDev* P, const RungSet* rs, int B);
 __global__ void k_batch_status(const PackDev* P, BatchStat* out, int B);
 __global__ void k_pair64_batch(const PackDev* P, const unsigned int* bstart, int B, int mode);
+__global__ void k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+                              const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
+                              double* row_e, double* row_k, int mode, double* g_out);
 __global__ void k_kappa_step_batch(const PackDev* P, int mode);
 __global__ void k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode);
 __global__ void k_tree_pass2(const double* ina, const double* inb, long long n, double* outa, double* outb);

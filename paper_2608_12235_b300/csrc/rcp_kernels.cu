@@ -540,6 +540,124 @@ k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, d
     pair64_body(ctl, c, xA, xB, m, v, rowptr, col, xb, part_e, part_k, mode, g_out, blockIdx.x);
 }
 
+// Binary64 pair kernel for small N: one warp per row.  With a thread per
+// row, a small packing occupies a few SMs while each thread walks its row
+// through a serial chain of binary64 square roots and divisions (slow on
+// B300).  Here the lanes compute the terms of up to 32 partners at once and
+// lane 0 folds them in the row's order -- the same products and the same
+// left folds as pair64_body, so the sums are bit-identical -- then the wall
+// terms.  e_i and k_i go to row_e/row_k[i] for the canonical tree over the
+// rows; lanes 0-2 take the Adam step of one coordinate each.
+__global__ void __launch_bounds__(RCP_WARP_ROW_THREADS)
+k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+              const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb, double* row_e,
+              double* row_k, int mode, double* g_out)
+{
+    __shared__ double sh[RCP_WARP_ROW_THREADS / 32];
+    if (ctl->halted) return;
+    const unsigned int FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int parity = ctl->parity;
+    const double4_32a* __restrict__ xin = parity ? xB : xA;
+    double4_32a* __restrict__ xout = parity ? xA : xB;
+    const double kappa = ctl->kappa;
+    const long long i = ((long long)blockIdx.x * RCP_WARP_ROW_THREADS + threadIdx.x) >> 5;   // warp-uniform
+    double md = 0.0;
+    float bud = INFINITY;
+    if (i < c.N) {
+        const double4_32a xi = xin[i];
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0, e = 0.0, k = 0.0;   // the fold, the same in every lane
+        const unsigned int t0 = rowptr[i], t1 = rowptr[i + 1];
+        for (unsigned int base = t0; base < t1; base += 32) {
+            const unsigned int t = base + (unsigned int)lane;
+            bool hit = false, grad = false, upper = false;
+            double tx = 0.0, ty = 0.0, tz = 0.0, te = 0.0, tk = 0.0;
+            if (t < t1) {
+                const unsigned int j = col[t];
+                const double4_32a xj = xin[j];
+                double dx = axis_diff(c, 0, xi.x - xj.x);
+                double dy = axis_diff(c, 1, xi.y - xj.y);
+                double dz = axis_diff(c, 2, xi.z - xj.z);
+                double r2 = dx * dx + dy * dy + dz * dz;
+                double r = sqrt(r2);
+                const bool both = xi.w > 0.0 && xj.w > 0.0;
+                double dd = both ? kappa * (0.5 * (xi.w + xj.w)) : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
+                double delta = 1.0 - r / dd;
+                if (delta > 0.0) {
+                    hit = true;
+                    if (r > 0.0 && xi.w > 0.0) {
+                        grad = true;
+                        double coef = (c.eps * delta) / (dd * r);
+                        tx = coef * dx;
+                        ty = coef * dy;
+                        tz = coef * dz;
+                    }
+                    if ((long long)j > i) {
+                        upper = true;
+                        te = (0.5 * c.eps) * (delta * delta);
+                        if (both)
+                            tk = ((c.eps * delta) * (1.0 - delta)) / kappa;
+                        else
+                            tk = (((c.eps * delta) * (1.0 - delta)) * (0.5 * (mobile_part(xi.w) + mobile_part(xj.w)))) / dd;
+                    }
+                    if (delta > md) md = delta;
+                }
+            }
+            const unsigned int gm = __ballot_sync(FULL, grad), um = __ballot_sync(FULL, upper);
+            unsigned int hm = __ballot_sync(FULL, hit);
+            while (hm) {   // partners in the row's order (lowest lane first)
+                const int l = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const double ax = __shfl_sync(FULL, tx, l), ay = __shfl_sync(FULL, ty, l);
+                const double az = __shfl_sync(FULL, tz, l), ae = __shfl_sync(FULL, te, l);
+                const double ak = __shfl_sync(FULL, tk, l);
+                if ((gm >> l) & 1u) {
+                    g0 = g0 - ax;
+                    g1 = g1 - ay;
+                    g2 = g2 - az;
+                }
+                if ((um >> l) & 1u) {
+                    e = e + ae;
+                    k = k + ak;
+                }
+            }
+        }
+        if (c.walls | c.container) wall_terms(c, kappa, xi, g0, g1, g2, e, k, md);   // identical in every lane
+        if (lane == 0) {
+            row_e[i] = e;
+            row_k[i] = k;
+        }
+        if (mode == RCP_MODE_ADAM && !(xi.w > 0.0)) {
+            if (lane == 0) xout[i] = xi;   // frozen: position and moments stay
+        } else if (mode == RCP_MODE_ADAM) {
+            const double b1 = ctl->b1 * c.beta1, b2 = ctl->b2 * c.beta2;
+            const double h1 = 1.0 - b1, h2 = 1.0 - b2;
+            const double eta = ctl->eta_x;
+            double pa = 0.0;
+            if (lane < 3) {
+                const double ga = lane == 0 ? g0 : (lane == 1 ? g1 : g2);
+                const double xa = lane == 0 ? xi.x : (lane == 1 ? xi.y : xi.z);
+                double ma = m[3 * i + lane], va = v[3 * i + lane];
+                pa = axis_wrap(c, lane, adam_coord(xa, ga, ma, va, eta, c, h1, h2));
+                m[3 * i + lane] = ma;
+                v[3 * i + lane] = va;
+            }
+            const double p0 = __shfl_sync(FULL, pa, 0), p1 = __shfl_sync(FULL, pa, 1), p2 = __shfl_sync(FULL, pa, 2);
+            if (lane == 0) {
+                xout[i] = make_double4_32a(p0, p1, p2, xi.w);
+                skin_budget64(ctl, c, p0, p1, p2, xi.w, xb[i], bud);
+            }
+        } else if (lane == 0) {
+            g_out[3 * i] = g0;
+            g_out[3 * i + 1] = g1;
+            g_out[3 * i + 2] = g2;
+        }
+    }
+    if (mode == RCP_MODE_ADAM) push_budget(ctl, bud);
+    const double bm = block_max(md, sh);
+    if (threadIdx.x == 0 && bm > 0.0) atomicMax(&ctl->maxdelta_bits, dbits(bm));
+}
+
 // Packing of a block in a batched launch: the last p with bstart[p] <= block.
 __device__ __forceinline__ int batch_pack(const unsigned int* bstart, int B, unsigned int block)
 {
