@@ -185,3 +185,33 @@ def test_seated_run_inside_walls_and_a_container(orc):
                 assert (xm[:, a] >= rad).all() and (8.0 - xm[:, a] >= rad).all()
         else:
             assert (np.sqrt(((xm - 4.0) ** 2).sum(axis=1)) + rad <= 4.0).all()
+
+
+def test_placement_sees_frozen_spheres_of_a_finer_class(orc):
+    """Frozen spheres far smaller than the mobile ones (a finer size class)
+    still keep every placed candidate off them."""
+    g = (np.arange(4) + 0.25) * 2.0
+    X = np.array([[a, b, c] for a in g for b in g for c in g])
+    F = np.full(len(X), 0.3)
+    D = np.full(40, 1.0)
+    Dall, x = orc.seated_state(F, X, D, seed=2, L=8.0, placement=1, phi0=0.1)
+    k0 = orc.kappa0(Dall, 8.0, 0.1)
+    lvl, _ = orc.levels(Dall, k0, 0.0, 0.0)
+    assert lvl[:len(X)].min() > lvl[len(X):].max()      # the frozen ones are in a finer class
+    diam = np.where(Dall < 0, -Dall, k0 * Dall)
+    assert _min_gap(x, diam, 8.0) >= 0.0
+
+
+def test_two_dimensional_cascade_climbs(orc):
+    """Disks: two classes at diameter ratio 4; the seated stage packs denser
+    than the coarse class alone and nothing overlaps at the end."""
+    D0 = np.concatenate([np.full(40, 4.0), np.full(300, 1.0)])
+    cls = np.concatenate([np.zeros(40, int), np.ones(300, int)])
+    x, diam, log = orc.cascade(D0, cls, seed=3, L=30.0, d=2, placement=1)
+    phi = [f for _, _, f, _ in log]
+    assert phi[1] > phi[0] + 0.02 and phi[2] > phi[1] - 2e-3
+    n = len(diam)
+    dx = x[:, None, :] - x[None, :, :]
+    dx -= 30.0 * np.round(dx / 30.0)
+    r = np.sqrt((dx ** 2).sum(-1)) + np.eye(n) * 100
+    assert (r / (0.5 * (diam[:, None] + diam[None, :])) - 1).min() >= 0.0
