@@ -215,3 +215,14 @@ def test_two_dimensional_cascade_climbs(orc):
     dx -= 30.0 * np.round(dx / 30.0)
     r = np.sqrt((dx ** 2).sum(-1)) + np.eye(n) * 100
     assert (r / (0.5 * (diam[:, None] + diam[None, :])) - 1).min() >= 0.0
+
+
+def test_release_starts_at_the_given_kappa(orc):
+    """kappa_init (the cascade's release) replaces kappa_0 as the first
+    iterate while the skin keeps kappa_0's scale."""
+    D0 = np.linspace(0.7, 1.0, 60)
+    x0 = orc.init_positions(2, 60)
+    r = orc.run(D0, seed=2, x0=x0, kappa_init=0.123, max_iters=3, trace_len=3)
+    assert r.trace[0, 2] == 0.123
+    r0 = orc.run(D0, seed=2, x0=x0, max_iters=3, trace_len=3)
+    assert r0.trace[0, 2] == orc.kappa0(D0, 1.0, 0.05)

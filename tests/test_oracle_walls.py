@@ -257,3 +257,14 @@ def test_container_placement_keeps_candidates_inside(orc):
     assert R >= 1
     rc = np.sqrt(((x - 0.5) ** 2).sum(axis=1))
     assert (rc + 0.5 * k * D0 <= 0.5).all()
+
+
+def test_run_restores_the_boundary_setting(orc):
+    """orc_run takes its boundary from its parameters and leaves the module
+    setting as it found it."""
+    D0 = np.linspace(0.7, 1.0, 50)
+    with orc.walls(5, 2):
+        orc.run(D0, seed=1, max_iters=50, walls=0, container=0)
+        L = orc.lib()
+        assert L.orc_get_walls() == 5 and L.orc_get_container() == 2
+    assert orc.lib().orc_get_walls() == 0 and orc.lib().orc_get_container() == 0
