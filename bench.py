@@ -338,7 +338,10 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iters/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "N": w["N"], "S": w["S"]},
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"], "precision": "f64",
+                       "iters_per_step": 1, "skin_abs": args.skin_abs, "skin_s": args.skin_s,
+                       "phi_at_timing": 0.5, "l2": "working set larger than L2 (host caches)"},
             "cpu_baseline": {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
