@@ -29,9 +29,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "lognormal-n1e6-s5e5": dict(kind="lognormal", N=1_000_000, p=2.0, S=5e5),
-    "powerlaw-n1e5-s20": dict(kind="power_law", N=100_000, p=-3.0, S=20.0),
-    "lognormal-n1e3-s10": dict(kind="lognormal", N=1000, p=0.5, S=10.0),
+    # phi_window: the packing fraction of the benchmark's timed window, at
+    # which the oracle's sample is taken
+    "lognormal-n1e6-s5e5": dict(kind="lognormal", N=1_000_000, p=2.0, S=5e5, phi_window=0.62),
+    "powerlaw-n1e5-s20": dict(kind="power_law", N=100_000, p=-3.0, S=20.0, phi_window=0.62),
+    "lognormal-n1e3-s10": dict(kind="lognormal", N=1000, p=0.5, S=10.0, phi_window=0.62),
 }
 METRIC = "inflation iters/s and pair-evals/s at N=1e6, S=5e5 (mixed vs FP64, same φ)"
 
@@ -69,7 +71,8 @@ def pair_traffic(args, Pn):
     is now (sha256 prefix over csrc/*.cu and csrc/*.cuh in name order; the
     data layout the kernel sees comes from the build kernels too) -- or on a
     later source the summary lists under traffic_valid_for, each with the
-    reason the pair kernel, its launch and its inputs are unchanged -- else
+    reason the pair kernel, its launch and its inputs are unchanged -- and
+    for a state whose listed entries are within 3 % of the capture's, else
     None."""
     import hashlib
     import re
@@ -85,8 +88,10 @@ def pair_traffic(args, Pn):
         pairs = int(re.search(r"traffic_pairs: (\d+)", text).group(1))
     except Exception:
         return None, None
+    # the counters hold for a state whose list has nearly the capture's
+    # entry count (the kernel's traffic follows the entries it walks)
     same_state = (args.workload == "lognormal-n1e6-s5e5" and args.skin_abs == 100.0 and args.skin_s == 0.02
-                  and args.densify + (args.warmup + args.steps) * args.iters_per_step == 8300)
+                  and abs(Pn - pairs) <= 0.03 * pairs)
     if not any(sha.startswith(w) for w in want) or not same_state:
         return None, None
     return float(traffic), pairs
@@ -132,25 +137,35 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(D0, iters, phi=0.5, seed=0, skin_abs=100.0, skin_s=0.02):
-    """The oracle as it stands, single thread, on a bounded sample of the same
-    workload (same skin settings): `iters` protocol iterations (one list build
-    included) from uniform positions at packing fraction `phi`."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(D0, iters, phi, seed=0, skin_abs=100.0, skin_s=0.02, threads=1):
+    """The oracle as it stands on a bounded sample of the workload: `iters`
+    protocol iterations (one list build included) from uniform positions at
+    packing fraction `phi`, at the first rung's values (mu, learning rates
+    and skin from kappa_0, as the GPU window that the benchmark times), with
+    `threads` host threads.  Constants are the oracle's own defaults; nothing
+    of the CUDA library is loaded."""
     import oracle
-    from paper_2608_12235_b300 import rcp
-    cfg = rcp.rcp_config_default()
+    p = oracle.default_params()
     x = oracle.init_positions(seed, D0.size)
     k = oracle.kappa0(D0, 1.0, phi)
-    k0 = oracle.kappa0(D0, 1.0, cfg.phi0)
+    k0 = oracle.kappa0(D0, 1.0, p.phi0)
     m = oracle.moments(D0)
     Dref = m[2] / m[1]
-    sigma0 = skin_abs * ((cfg.lr_x * k0) * Dref)
+    eta_x0 = (p.lr_x * k0) * Dref
+    sigma0 = skin_abs * eta_x0
     Neff = m[1] / (Dref ** 3)
-    mu = (((3.0 * cfg.delta_star0) * cfg.eps) * Neff) / (k * m[0])
-    t0 = time.perf_counter()
-    builds = oracle.sample_iterations(D0, x, k, mu, (cfg.lr_x * k) * Dref, cfg.lr_kappa * k, sigma0, iters,
-                                      skin_s=skin_s)
-    dt = time.perf_counter() - t0
+    mu0 = (((3.0 * p.delta_star0) * p.eps) * Neff) / (k0 * m[0])
+    with oracle.threads(threads):
+        t0 = time.perf_counter()
+        builds = oracle.sample_iterations(D0, x, k, mu0, eta_x0, p.lr_kappa * k0, sigma0, iters, skin_s=skin_s)
+        dt = time.perf_counter() - t0
     return iters / dt, dt, builds
 
 
@@ -325,24 +340,73 @@ def bench_rows(rcp, torch, large: bool = False):
     return out
 
 
+def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0):
+    """Mixed precision beside binary64, each run to App. A's stopping
+    criterion (max delta < 5e-4) and shrunk to contact (Sec. II), per seed:
+    final phi, iterations, wall time and the device memory the handle holds
+    (free memory before creation minus free memory after the run)."""
+    out = {}
+    for name in workloads:
+        w = WORKLOADS[name]
+        D0 = diameters(w)
+        rows = []
+        for seed in seeds:
+            row = {"seed": seed}
+            for prec, tag in ((rcp.RCP_MIXED, "mixed"), (rcp.RCP_FP64, "fp64")):
+                torch.cuda.synchronize()
+                free0 = torch.cuda.mem_get_info()[0]
+                p = rcp.Packing(D0, box=1.0, seed=seed, precision=prec)
+                t0 = time.perf_counter()
+                r = p.run(max_seconds=max_fp64_s if (tag == "fp64" and max_fp64_s > 0) else 0.0)
+                dt = time.perf_counter() - t0
+                free1 = torch.cuda.mem_get_info()[0]
+                p.close()
+                row[tag] = {"phi": r.phi, "stopped": r.stopped, "iters": r.iters, "rebuilds": r.rebuilds,
+                            "seconds": dt, "iters_per_s": r.iters / dt, "kappa_c": r.kappa_c,
+                            "max_delta": r.max_delta, "device_bytes": int(free0 - free1)}
+            if row["mixed"]["stopped"] and row["fp64"]["stopped"]:
+                row["dphi"] = row["mixed"]["phi"] - row["fp64"]["phi"]
+            rows.append(row)
+            print(json.dumps({"workload": name, **row}), file=sys.stderr, flush=True)
+        d = [r["dphi"] for r in rows if "dphi" in r]
+        out[name] = {"runs": rows, "mean_dphi": float(np.mean(d)) if d else None,
+                     "mean_abs_dphi": float(np.mean(np.abs(d))) if d else None,
+                     "max_abs_dphi": float(np.max(np.abs(d))) if d else None,
+                     "seed_scatter_fp64": float(np.std([r["fp64"]["phi"] for r in rows], ddof=1))
+                     if len(rows) > 1 else None}
+    return out
+
+
+def config_of(args, w, phi, precision, state, iters_per_step):
+    """The workload's `config`, the same keys in both arms."""
+    return {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"], "precision": precision,
+            "iters_per_step": iters_per_step, "skin_abs": args.skin_abs, "skin_s": args.skin_s,
+            "rung": 0, "phi_at_timing": round(phi, 4), "state": state,
+            "l2": "working set larger than L2 (>250 MB on the device; host caches)"}
+
+
 def run_reference(args, w):
-    """--impl reference: the CPU oracle on the same workload and metric."""
+    """--impl reference: the CPU oracle, as it stands, on all host cores, on
+    the same workload, metric and rung as the GPU arm.  It starts from uniform
+    positions at the packing fraction of the GPU's timed window (the oracle
+    cannot follow the 6000-iteration densification within minutes)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     D0 = diameters(w)
-    cpu_baseline(D0, max(1, args.warmup), skin_abs=args.skin_abs, skin_s=args.skin_s)
-    rate, dt, builds = cpu_baseline(D0, max(1, args.steps), skin_abs=args.skin_abs, skin_s=args.skin_s)
-    sample = (f"{args.steps} protocol iterations (one neighbour-list build, {builds} builds in all) from uniform "
-              f"positions at phi=0.5, N={w['N']}, single thread")
+    cores = host_cores()
+    phi = w["phi_window"]
+    cpu_baseline(D0, max(1, args.warmup), phi, skin_abs=args.skin_abs, skin_s=args.skin_s, threads=cores)
+    rate, dt, builds = cpu_baseline(D0, max(1, args.steps), phi, skin_abs=args.skin_abs, skin_s=args.skin_s,
+                                    threads=cores)
+    sample = (f"{args.steps} protocol iterations ({builds} neighbour-list builds, the first one included) from "
+              f"uniform positions at phi={phi}, N={w['N']}, first-rung values, {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iters/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"], "precision": "f64",
-                       "iters_per_step": 1, "skin_abs": args.skin_abs, "skin_s": args.skin_s,
-                       "phi_at_timing": 0.5, "l2": "working set larger than L2 (host caches)"},
-            "cpu_baseline": {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": config_of(args, w, phi, "f64", f"uniform positions at phi {phi} (seed 0)", 1),
+            "cpu_baseline": {"value": rate, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -367,10 +431,22 @@ def main():
     ap.add_argument("--rows", action="store_true",
                     help="measure the widened rows (cascade, walls, container) instead; one JSON line")
     ap.add_argument("--rows-large", action="store_true", help="with --rows: also a ~1e5-sphere cascade")
+    ap.add_argument("--phi-parity", default="",
+                    help="comma-separated workloads: mixed beside binary64 runs to the stop; one JSON line")
+    ap.add_argument("--phi-seeds", default="0,1,2,3,4")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.phi_parity:
+        import torch
+        from paper_2608_12235_b300 import rcp
+        rcp.load()
+        clk = Clocks(0)
+        res = phi_parity(rcp, torch, args.phi_parity.split(","), [int(v) for v in args.phi_seeds.split(",")])
+        print(json.dumps({"metric": "final phi, mixed precision beside binary64, runs to the stopping criterion",
+                          "data": "synthetic", **res, "clocks": clk.stop()}))
+        return
     if args.rows:
         import torch
         from paper_2608_12235_b300 import rcp
@@ -491,20 +567,28 @@ def main():
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, builds = cpu_baseline(D0, args.cpu_iters, skin_abs=args.skin_abs, skin_s=args.skin_s)
-        cpu = {"value": rate, "unit": "iters/s", "cores": 1, "kind": "oracle",
+        # the oracle at the packing fraction of the timed window, all host
+        # cores, and a shorter sample on one core
+        cores = host_cores()
+        phi_c = w["phi_window"]
+        rate, dt, builds = cpu_baseline(D0, args.cpu_iters, phi_c, skin_abs=args.skin_abs, skin_s=args.skin_s,
+                                        threads=cores)
+        it1 = max(1, args.cpu_iters // 2)
+        rate1, dt1, _ = cpu_baseline(D0, it1, phi_c, skin_abs=args.skin_abs, skin_s=args.skin_s, threads=1)
+        cpu = {"value": rate, "unit": "iters/s", "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_iters} protocol iterations incl. one neighbour-list build from uniform "
-                         f"positions at phi=0.5, N={w['N']} ({dt:.1f} s)"}
+                         f"positions at phi={phi_c}, first-rung values, N={w['N']}, {cores} threads ({dt:.1f} s)",
+               "single_thread": {"value": rate1, "cores": 1,
+                                 "sample": f"{it1} iterations, the same start ({dt1:.1f} s)"}}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 pair math, f64 state and reductions", "data": "synthetic",
-            "config": {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"],
-                       "precision": "mixed", "iters_per_step": ips, "densify_iters": args.densify,
-                       "skin_abs": args.skin_abs, "skin_s": args.skin_s,
-                       "phi_at_timing": round(phi_now, 4), "l2": "working set larger than L2 (>250 MB)"},
+            "config": config_of(args, w, phi_now, "mixed",
+                                f"protocol trajectory from phi0 = 0.05 (seed {rank}) after "
+                                f"{args.densify + args.warmup * ips} iterations", ips),
             "pair_evals_per_s": pair_evals,
             "fp64": {"value": value64, "unit": "iters/s", "speedup_mixed_over_fp64": value / value64},
             "rebuilds_in_timed_region": rebuilds - (rebuild0 or 0), "listed_pairs": Pn,

@@ -34,7 +34,7 @@ _up = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
 def build(force: bool = False) -> str:
     """Compile the oracle into ``librcp_oracle.so`` beside its source."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
     return _LIB
@@ -62,6 +62,8 @@ def lib():
     if _lib is None:
         build()
         L = C.CDLL(_LIB)
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
         L.orc_set_walls.argtypes = [C.c_int]
         L.orc_get_walls.restype = C.c_int
         L.orc_set_container.argtypes = [C.c_int]
@@ -121,6 +123,26 @@ def lib():
                               C.POINTER(Result), C.c_void_p, C.c_long]
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's row loop and Adam step (1 by default); results
+    do not depend on it."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+@contextlib.contextmanager
+def threads(n: int):
+    old = get_threads()
+    set_threads(n)
+    try:
+        yield
+    finally:
+        set_threads(old)
 
 
 def _box(L, d=3):

@@ -56,6 +56,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Threads for the row loop of orc_energy_grad_list and the coordinate loop
+ * of the Adam step (OpenMP; 1 unless orc_set_threads asks for more).  Each
+ * row's fold and each coordinate's update are independent and every global
+ * sum keeps its fixed tree over the particle index, so no result depends on
+ * the thread count. */
+static int g_threads = 1;
+void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int orc_get_threads(void) { return g_threads; }
+
 #define ORC_PI 3.141592653589793
 #define ORC_KMAX 32
 #define ORC_NMAX (1L << 19)
@@ -758,6 +767,7 @@ void orc_energy_grad_list(const double* x, const double* D0, long n, int d, cons
     double* e = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double* k = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double md = 0.0;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 4096) reduction(max : md)
     for (long i = 0; i < n; ++i) {
         rowacc a;
         row_begin(&a);
@@ -976,6 +986,7 @@ static int build_rungs(const orc_params* p, long n, rung* R, int cap)
 static void adam_positions(double* x, double* m, double* v, const double* g, const double* D0, long n, int d,
                            double eta, const orc_params* p, double b1, double b2)
 {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (long i = 0; i < n; ++i)
         if (D0[i] > 0.0)
             orc_adam_update(&x[d * i], &m[d * i], &v[d * i], &g[d * i], d, eta, p->beta1, p->beta2, p->adam_eps, b1,

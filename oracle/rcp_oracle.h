@@ -75,6 +75,12 @@ int    orc_get_walls(void);
 void   orc_set_container(int type);   /* 0 none, 1 ball / disk, 2 cylinder about z */
 int    orc_get_container(void);
 
+/* Threads of the row loop of the evaluation and of the Adam step (OpenMP;
+ * 1 by default).  Results do not depend on it: rows are independent and
+ * every global sum keeps its fixed tree. */
+void   orc_set_threads(int n);
+int    orc_get_threads(void);
+
 /* ---- input-side primitives ---- */
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k);
 void   orc_init_positions(uint64_t seed, long n, int d, const double* L, double* x);

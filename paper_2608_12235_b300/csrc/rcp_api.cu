@@ -1292,7 +1292,7 @@ rcp_status rcp_adam_step(rcp_handle h, const double* grad_x, double dE_dkappa, d
         k_adam_mixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->m32, h->v32, gin,
                                                                   h->rb, lr_x);
     else
-        k_adam64<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->g,
+        k_adam64<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, gin,
                                                                h->xb, lr_x);
     CKL();
     h->launches += 1;

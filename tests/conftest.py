@@ -1,6 +1,7 @@
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -18,3 +19,66 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def row_term_scale(orc, x, D0, L, kappa, d=3, eps=1.0, band=1e-8):
+    """Scales of the element-wise gradient tolerance of the mixed path, from
+    the inputs alone (binary64, no value of the CUDA path):
+
+      s_i = sum over the overlapping partners j of sphere i of the magnitude
+            eps delta_ij / d_ij of its term of dE/dx_i;
+      a_i = sum over the partners with |delta_ij| < band of eps 2 band / d_ij.
+
+    The mixed path forms each pair term in binary32 from exactly represented
+    displacements (a few roundings of 2^-24 each), so every term is within
+    about 5e-7 of itself and a row's gradient component within that fraction
+    of s_i (plus the compensated sum's own error): s_i is the floor where the
+    terms of a row cancel (a sphere pushed evenly from all sides), which no
+    bound relative to the small net gradient covers.  The mixed overlap also
+    carries an absolute error (56-bit fixed-point positions, about 3e-11 of
+    the smallest contact distance at S = 5e5, and the float-float d^2 - r^2):
+    a pair within `band` of contact may count on one side and not on the
+    other, which a_i allows for."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, d)
+    D0 = np.asarray(D0, dtype=np.float64)
+    n = D0.size
+    # the pairs with r < d (1 + 2 band): interaction radius kappa D (1/2 + band)
+    rp, col = orc.list_grid(x, D0, L, kappa, band, 0.0, d=d)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    dx = x[rows] - x[col]
+    dx -= L * np.rint(dx / L)
+    r = np.sqrt(np.sum(dx * dx, axis=1))
+    dd = kappa * 0.5 * (D0[rows] + D0[col])
+    delta = 1.0 - r / dd
+    t = np.where(delta > 0.0, eps * delta / dd, 0.0)
+    a = np.where(np.abs(delta) < band, eps * 2.0 * band / dd, 0.0)
+    return np.bincount(rows, weights=t, minlength=n), np.bincount(rows, weights=a, minlength=n)
+
+
+def assert_grad_close(g, og, scale, rel=1e-5, floor=1e-6, what=""):
+    """Element-wise: |g - og| <= rel |og| + floor s_i + a_i, with (s, a) from
+    row_term_scale.  Returns the largest ratio of an error to its bound
+    (<= 1 passes)."""
+    s, a = scale
+    og = np.asarray(og)
+    g = np.asarray(g).reshape(og.shape)
+    bound = rel * np.abs(og) + (floor * np.asarray(s) + np.asarray(a))[:, None]
+    err = np.abs(g - og)
+    safe = np.where(bound > 0.0, bound, 1.0)
+    ratio = np.where(bound > 0.0, err / safe, np.where(err > 0.0, np.inf, 0.0))
+    worst = float(ratio.max()) if ratio.size else 0.0
+    if worst > 1.0:
+        i = int(np.unravel_index(np.argmax(ratio), ratio.shape)[0])
+        raise AssertionError(f"{what} gradient row {i}: got {g[i]}, oracle {og[i]}, s_i {s[i]:.3e}, "
+                             f"a_i {a[i]:.3e}, error/bound {worst:.3g}")
+    return worst
+
+
+@pytest.fixture(scope="session")
+def grad_check():
+    return assert_grad_close
+
+
+@pytest.fixture(scope="session")
+def term_scale(orc):
+    return lambda *a, **k: row_term_scale(orc, *a, **k)

@@ -2,8 +2,10 @@
 
 Bar: integer work (cell keys, neighbour lists) bit-exact; the binary64 path
 bit-exact as well (same operations in the same order, IEEE-correct on both
-sides); the mixed path within 1e-5 relative on energy, gradient norm and
-dE/dkappa.
+sides); the mixed path within 1e-5 relative on energy, dE/dkappa and the
+largest overlap, and element by element on the gradient within 1e-5 relative
+plus an absolute floor of 1e-6 of the row's summed term magnitudes (see
+row_term_scale in conftest.py for why that floor).
 """
 import numpy as np
 import pytest
@@ -137,6 +139,34 @@ def test_adam_step_fp64_bitexact(rcp, orc):
     p.close()
 
 
+@pytest.mark.parametrize("d,mask", [(2, 0), (3, 0b101), (2, 0b01)])
+def test_adam_step_fp64_bitexact_disks_and_walls(rcp, orc, d, mask):
+    """The standalone Adam step with the caller's [N][d] gradient: disks (the
+    internal layout has three columns) and walled axes (no wrap there)."""
+    n = 700
+    D0 = inputs.lognormal(n, 0.5, 10.0)
+    x = orc.init_positions(8, n, 1.0, d=d)
+    k = orc.kappa0(D0, 1.0, 0.4, d=d)
+    p = _mk(rcp, D0, seed=8, d=d, walls=mask)
+    p.set_positions(x, k)
+    rng = np.random.default_rng(d + 10 * mask)
+    xo, mo, vo = x.ravel().copy(), np.zeros(x.size), np.zeros(x.size)
+    periodic = np.array([not ((mask >> (a % d)) & 1) for a in range(x.size)])
+    b1 = b2 = 1.0
+    for t in range(4):
+        g = rng.standard_normal(x.shape) * 10.0 ** rng.uniform(-4, 2)
+        p.adam_step(g, 0.0, 1e-3, 0.0)
+        b1 *= 0.9
+        b2 *= 0.999
+        orc.adam_update(xo, mo, vo, g, 1e-3, b1, b2)
+        xo = np.array([orc.wrap(a, 1.0) if per else a for a, per in zip(xo, periodic)])
+    xs, ms, vs, s = p.state()
+    assert xs.shape == (n, d)
+    assert np.array_equal(xs.ravel(), xo) and np.array_equal(ms.ravel(), mo) and np.array_equal(vs.ravel(), vo)
+    assert s.t == 4
+    p.close()
+
+
 def test_shrink_fp64_bitexact(rcp, orc):
     D0, x, k = _states(orc)[1]
     p = _mk(rcp, D0)
@@ -228,7 +258,7 @@ def test_chunk_size_does_not_change_the_trajectory(rcp):
 
 
 # ------------------------------------------------------------------ mixed precision
-def test_energy_grad_mixed_within_tolerance(rcp, orc):
+def test_energy_grad_mixed_within_tolerance(rcp, orc, term_scale, grad_check):
     for D0, x, k in _states(orc):
         p = _mk(rcp, D0, precision=rcp.RCP_MIXED)
         p.set_positions(x, k)
@@ -236,9 +266,10 @@ def test_energy_grad_mixed_within_tolerance(rcp, orc):
         E, g, dk, md = p.energy_grad(mu)
         oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, mu)
         assert abs(E - oE) <= 1e-5 * abs(oE)
-        assert np.linalg.norm(g - og) <= 1e-5 * np.linalg.norm(og)
         assert abs(dk - odk) <= 1e-5 * abs(odk)
-        assert abs(md - omd) <= 1e-5 * omd + 1e-6
+        assert abs(md - omd) <= 1e-5 * omd
+        w = grad_check(g, og, term_scale(x, D0, 1.0, k), what="mixed")
+        print(f"N={D0.size} worst gradient error / bound {w:.3g}")
         p.close()
 
 
@@ -276,7 +307,7 @@ def test_mixed_state_follows_the_caller_order(rcp, orc):
     p.close()
 
 
-def test_energy_grad_mixed_near_contact(rcp, orc):
+def test_energy_grad_mixed_near_contact(rcp, orc, term_scale, grad_check):
     """Small overlaps (delta ~ 1e-3, a relaxed packing inflated by 0.2 %): the
     regime where a plain binary32 d - r would cancel."""
     D0 = inputs.lognormal(400, 0.5, 10.0)
@@ -293,8 +324,9 @@ def test_energy_grad_mixed_near_contact(rcp, orc):
               f"relg={np.linalg.norm(g - og) / np.linalg.norm(og):.2e} relmd={abs(md - omd) / omd:.2e}")
         assert abs(E - oE) <= 1e-5 * abs(oE)
         assert abs(dk - odk) <= 1e-5 * abs(odk)
-        assert np.linalg.norm(g - og) <= 1e-5 * np.linalg.norm(og)
         assert abs(md - omd) <= 1e-5 * omd
+        w = grad_check(g, og, term_scale(x, D0, 1.0, k), what="mixed near contact")
+        print(f"worst gradient error / bound {w:.3g}")
     p.close()
 
 
@@ -365,7 +397,7 @@ def test_two_dimensional_initial_state_and_kappa0_bitexact(rcp, orc):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_two_dimensional_list_and_energy(rcp, orc, precision):
+def test_two_dimensional_list_and_energy(rcp, orc, precision, term_scale, grad_check):
     n = 1200
     D0 = inputs.lognormal(n, 1.0, 30.0)
     prec = rcp.RCP_FP64 if precision == "fp64" else rcp.RCP_MIXED
@@ -384,7 +416,8 @@ def test_two_dimensional_list_and_energy(rcp, orc, precision):
         assert E == oE and dk == odk and md == omd and np.array_equal(g, og)
     else:
         assert abs(E - oE) <= 1e-5 * abs(oE) and abs(dk - odk) <= 1e-5 * abs(odk)
-        assert np.linalg.norm(g - og) <= 1e-5 * np.linalg.norm(og)
+        assert abs(md - omd) <= 1e-5 * omd
+        grad_check(g, og, term_scale(x, D0, 1.0, k, d=2), what="mixed d = 2")
     p.close()
 
 

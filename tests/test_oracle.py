@@ -508,3 +508,24 @@ def test_two_dimensional_run_reaches_the_criterion(orc):
     assert (r2 >= c * c * (1 - 1e-12)).all()
     assert r.phi == pytest.approx(math.pi / 4 * r.kappa_c ** 2 * np.sum(D0 ** 2), rel=1e-12)
     assert 0.8 < r.phi < 0.9
+
+
+def test_thread_count_does_not_change_the_oracle(orc):
+    """The all-core oracle (OpenMP over rows and coordinates) gives the same
+    bits as one thread: rows are independent folds and the global sums keep
+    their fixed tree over the particle index."""
+    D0 = inputs.lognormal(4000, 1.0, 30.0)
+    x = orc.init_positions(3, D0.size)
+    k = orc.kappa0(D0, 1.0, 0.55)
+    rp, col = orc.list_grid(x, D0, 1.0, k, 0.1, 0.0)
+    outs, xs = [], []
+    for t in (1, 4):
+        with orc.threads(t):
+            outs.append(orc.energy_grad(x, D0, 1.0, k, 0.01, rowptr=rp, col=col))
+            xt = x.copy()
+            orc.sample_iterations(D0, xt, k, 0.01, 1e-4, 1e-4, 1e-3, 5)
+            xs.append(xt)
+    (E1, g1, k1, m1), (E4, g4, k4, m4) = outs
+    assert E1 == E4 and k1 == k4 and m1 == m4 and np.array_equal(g1, g4)
+    assert np.array_equal(xs[0], xs[1])
+    assert orc.get_threads() == 1
