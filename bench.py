@@ -377,6 +377,29 @@ def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0):
     return out
 
 
+def profile_window(args, w):
+    """A bounded window of the workload for ncu (--profile-from-start off)."""
+    import torch
+    from paper_2608_12235_b300 import rcp
+    rcp.load()
+    D0 = diameters(w)
+    p = rcp.Packing(D0, box=1.0, seed=0, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs, skin_s=args.skin_s)
+    r = p.run(max_iters=args.densify, shrink=False)
+    rcp.rcp_build_neighbors(p.h)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    if args.profile_window == "pair":
+        rcp.rcp_profile(p.h, 2)
+    elif args.profile_window == "build":
+        rcp.rcp_build_neighbors(p.h)
+    else:
+        p.run(max_iters=100, shrink=False)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(f"window done: iters={r.iters} pairs={r.pairs}")
+    p.close()
+
+
 def config_of(args, w, phi, precision, state, iters_per_step):
     """The workload's `config`, the same keys in both arms."""
     return {"workload": args.workload, "N": w["N"], "S": w["S"], "sigma_ln": w["p"], "precision": precision,
@@ -431,6 +454,11 @@ def main():
     ap.add_argument("--rows", action="store_true",
                     help="measure the widened rows (cascade, walls, container) instead; one JSON line")
     ap.add_argument("--rows-large", action="store_true", help="with --rows: also a ~1e5-sphere cascade")
+    ap.add_argument("--profile-window", choices=["pair", "build", "iters"], default=None,
+                    help="densify the workload (mixed) outside the profiled range, then bracket with "
+                         "cudaProfilerStart/Stop two iterations launched one by one (pair), one neighbour "
+                         "rebuild (build) or 100 graph-driven iterations (iters), for ncu --profile-from-start "
+                         "off; prints no benchmark line")
     ap.add_argument("--phi-parity", default="",
                     help="comma-separated workloads: mixed beside binary64 runs to the stop; one JSON line")
     ap.add_argument("--phi-seeds", default="0,1,2,3,4")
@@ -438,6 +466,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.profile_window:
+        return profile_window(args, w)
     if args.phi_parity:
         import torch
         from paper_2608_12235_b300 import rcp

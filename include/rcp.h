@@ -13,14 +13,15 @@
  *   - the return value is an rcp_status; RCP_OK on success.  On failure a
  *     message is kept in the handle (rcp_last_error) and no output is written
  *     unless stated;
- *   - positions are row-major [N][3] doubles in the caller's particle order;
+ *   - positions are row-major [N][d] doubles in the caller's particle order;
  *   - work is issued on the handle's CUDA stream (rcp_set_stream); calls that
  *     return host data synchronise that stream before returning;
  *   - `on_device` = 1 means the pointer arguments of that call are device
  *     pointers on the handle's device (outputs are then written
  *     asynchronously on the handle's stream); 0 means host pointers;
- *   - d must be 3: the kernels are written for three dimensions (the paper's
- *     quantitative results are 3D periodic, Sec. II).
+ *   - d is 3 or 2 (disks; the paper's quantitative results are 3D, Sec. II
+ *     shows disks among its domains); other d return RCP_ERR_UNSUPPORTED.
+ *     Positions, gradients and moments then have two columns at the boundary.
  */
 #ifndef RCP_H
 #define RCP_H
@@ -42,7 +43,7 @@ typedef enum {
     RCP_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
     RCP_ERR_MAXITER = 7,     /* the iteration cap was reached before the stopping criterion */
     RCP_ERR_CUDA = 8,        /* a CUDA runtime call failed (message has its text) */
-    RCP_ERR_UNSUPPORTED = 9  /* valid but not implemented here (e.g. d != 3) */
+    RCP_ERR_UNSUPPORTED = 9  /* valid but not implemented here (e.g. d other than 2 or 3) */
 } rcp_status;
 
 typedef enum {
@@ -356,11 +357,15 @@ const char* rcp_batch_last_error(rcp_batch b);
  * the allocator while another library holds it).  No handle is involved and
  * no cudaMalloc, cudaFree or allocating library routine is called.
  *
- * Computes, from caller-owned DEVICE buffers, exactly what rcp_energy_grad
- * computes in RCP_FP64 mode: Eq. energy E, grad_x[N][3] = dE/dx_i, dE/dkappa
- * and max(0, max delta_ij), over the CSR list rowptr[N+1] / col[P]
- * (unsigned 32-bit, ascending columns per row; it must contain every
- * overlapping pair, as rcp_neighbors' list does).
+ * Computes, from caller-owned DEVICE buffers, what rcp_energy_grad computes
+ * in RCP_FP64 mode for a periodic d = 3 box without walls, container or
+ * frozen spheres (the only case it covers): Eq. energy E, grad_x[N][3] =
+ * dE/dx_i, dE/dkappa and max(0, max delta_ij), bit for bit, over the CSR
+ * list rowptr[N+1] / col[P] (unsigned 32-bit, ascending columns per row).
+ * The list must be a full (symmetric) list holding every overlapping pair in
+ * both rows -- j in row i and i in row j -- as rcp_neighbors' list does: a
+ * row's energy share counts its partners j > i, its gradient all partners,
+ * so a half list gives wrong gradients without an error.
  *   x: [N][3] positions inside the box; D0: [N] relative diameters;
  *   box: HOST array of 3 box edges; kappa > 0; mu and eps as in Eq. energy;
  *   E, dE_dkappa, max_delta: device pointers to one double each (may be NULL);

@@ -1,7 +1,7 @@
 // rcp_api.cu -- the C ABI (include/rcp.h): handle life cycle, the
 // neighbour-structure build, evaluation, the standalone Adam step, and the
-// host-side schedule controller that replays a captured CUDA graph of
-// `chunk` iterations per launch.
+// host-side schedule controller that launches a captured CUDA graph whose
+// device-side loop runs `chunk` iterations per body pass until one halts.
 //
 // Scalar schedule values (mu, learning rates, rung budgets) are computed on
 // the host from device-reduced sums, in the same binary64 expressions as the
@@ -348,7 +348,7 @@ rcp_status ensure_pair_capacity(rcp_ctx* h, unsigned long long P)
 // The build runs in three phases separated by host reads, so that several
 // packings can be built concurrently on their own streams (the batch):
 //   A: class sizes and grids (ctl copied to the host);
-//   B: keys, sort, hash, search (entry count copied to the host);
+//   B: keys, sort, cell table, search (entry count copied to the host);
 //   C: pair sort, CSR, long-row list, snapshot.
 rcp_status build_a(rcp_ctx* h)
 {
@@ -471,7 +471,8 @@ rcp_status build_c(rcp_ctx* h)
         CK(cudaStreamSynchronize(h->stream));
         P = h->ctl_h->pair_cursor;
     }
-    if (P >= (1ull << 32)) return fail(h, RCP_ERR_CAPACITY, "more than 2^32 listed pairs");
+    // the pair kernels step 32-bit entry indices up to 64 past the last entry
+    if (P >= (1ull << 32) - 1024) return fail(h, RCP_ERR_CAPACITY, "more than 2^32 - 1024 listed pairs");
     // row and column fields are adjacent: 8-bit digits over all 2 nbits bits
     std::vector<int> ps = field_shifts(0, 2 * nbits);
     const unsigned long long* spairs = nullptr;
@@ -497,6 +498,7 @@ rcp_status build_c(rcp_ctx* h)
 // Rows longer than c.long_row, compacted (used by the mixed pair kernel).
 rcp_status relist_long(rcp_ctx* h)
 {
+    if (h->c.long_row > 32u) h->c.long_row = 32u;   // short rows are marked in one 32-bit word
     const long long N = h->N;
     const unsigned int nbN = rcp_ceil_div(N, 256);
     h->launches += 1;
@@ -614,6 +616,11 @@ bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy; 
 
 cudaStream_t capture_stream(const rcp_ctx* h) { return capturable(h->stream) ? h->stream : h->own_stream; }
 
+// The replayed graph: a conditional while node whose body is `chunk`
+// iterations followed by k_loop_cond, so one launch advances the packing
+// until an iteration halts (a rebuild due, the rung's iteration limit, the
+// stop, an error) and no launch after the halt runs empty beyond the rest of
+// its body pass.
 rcp_status capture_graph(rcp_ctx* h)
 {
     if (h->gexec && h->gT == h->cfg.chunk && h->g_stream == h->stream && h->g_pcap == h->pcap) return RCP_OK;
@@ -622,21 +629,41 @@ rcp_status capture_graph(rcp_ctx* h)
         h->gexec = nullptr;
     }
     cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle hc;
+    cudaError_t e0 = cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault);
+    // zeroed storage: the params type has no default constructor (a union)
+    alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+    memset(np_buf, 0, sizeof(np_buf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if (e0 == cudaSuccess) e0 = cudaGraphAddNode(&wn, graph, nullptr, nullptr, 0, &np);
+    if (e0 != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(h, RCP_ERR_CUDA, "graph loop node failed: %s", cudaGetErrorString(e0));
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
     cudaStream_t user = h->stream;
     h->stream = capture_stream(h);  // launch_iteration issues on h->stream
-    cudaError_t e0 = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    e0 = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e0 != cudaSuccess) {
         h->stream = user;
+        cudaGraphDestroy(graph);
         return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e0));
     }
-    h->g_kernels = 0;
+    h->g_kernels = 1;
     for (int t = 0; t < h->cfg.chunk; ++t) h->g_kernels += launch_iteration(h, RCP_MODE_ADAM);
-    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    k_loop_cond<<<1, 1, 0, h->stream>>>(h->ctl, hc);
+    cudaGraph_t captured;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &captured);
     h->stream = user;
-    if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(h, RCP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     h->gT = h->cfg.chunk;
     h->g_stream = h->stream;
     h->g_pcap = h->pcap;
@@ -903,6 +930,9 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         if (box[a] < c.Lmin) c.Lmin = box[a];
         if (box[a] > c.Lmax) c.Lmax = box[a];
     }
+    // two fixed-point units of the coarsest axis: covers the remainders the
+    // mixed pre-test leaves out (below one unit per axis, sqrt(3) in all)
+    c.qmargin = 2.0f * std::max(c.qscale[0], std::max(c.qscale[1], c.qscale[2]));
     c.V = d == 2 ? box[0] * box[1] : (box[0] * box[1]) * box[2];   // area when d = 2
     c.walls = h->cfg.walls;
     c.container = h->cfg.container;
@@ -933,7 +963,7 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     c.long_row = RCP_LONG_ROW;
     {
         // blocks serving long rows: about one per 1536 spheres, at least 2
-        long long lb = N / 1536;
+        long long lb = N / RCP_LONG_DIV;
         if (lb < 2) lb = 2;
         if (lb > RCP_LONG_BLOCKS_MAX) lb = RCP_LONG_BLOCKS_MAX;
         c.long_blocks = (unsigned int)lb;
@@ -1408,14 +1438,16 @@ static rcp_status run_impl(rcp_ctx* h, const rcp_stop* stop, rcp_result* out, Pr
                 CK(cudaEventRecord(h->ev_a, h->stream));
                 CK(cudaStreamWaitEvent(cs, h->ev_a, 0));
             }
+            const unsigned long long passes0 = hc->body_passes;
             CK(cudaGraphLaunch(h->gexec, cs));
             if (cs != h->stream) {
                 CK(cudaEventRecord(h->ev_b, cs));
                 CK(cudaStreamWaitEvent(h->stream, h->ev_b, 0));
             }
-            h->launches += h->g_kernels;
+            CKS(sync_ctl(h));
+            h->launches += (long long)(h->ctl_h->body_passes - passes0) * h->g_kernels;
         }
-        CKS(sync_ctl(h));
+        if (prof) CKS(sync_ctl(h));
         hc = h->ctl_h;
         if (hc->status != RCP_OK) {
             result = fail(h, (rcp_status)hc->status, "device status %d (%s) at iteration %lld", hc->status,
@@ -1863,7 +1895,9 @@ rcp_status batch_build(rcp_batch_ctx* b, const std::vector<int>& which)
 rcp_status batch_autotune_rows(rcp_batch_ctx* b)
 {
     if (b->precision != RCP_MIXED) return RCP_OK;
-    const unsigned int cand[4] = {16, 32, 64, 128};
+    // thresholds up to 32: a short row keeps its pre-test marks in one
+    // 32-bit word (the kernel walks longer rows with a warp)
+    const unsigned int cand[3] = {8, 16, 32};
     float best = 1e30f;
     unsigned int pick = RCP_LONG_ROW;
     for (unsigned int lr : cand) {

@@ -5,16 +5,17 @@
 // sigma0 (half its diameter plus its skin); a pair is listed iff its
 // minimum-image distance is below rho_i + rho_j.  Spheres are binned into
 // size classes by rho (class k holds rho in (rho_max 2^-(k+1), rho_max
-// 2^-k]), each class with its own uniform grid whose cell edge is at least
-// the class's largest interaction diameter.  The grids are sparse: particles
-// are sorted by the 62-bit key (class, cz, cy, cx) with a hand-written LSD
-// radix sort, and a hash table maps each occupied cell to its range.  A
-// sphere scans its own class and every coarser class over the cells within
-// its search radius; a pair inside one class is found from both ends, a pair
-// across classes from the finer end only, which emits both directions.  The
-// pairs (row << b | col) are radix-sorted into CSR rows with ascending
-// columns.  Integer and exact-predicate work only: the list is bit-identical
-// to the definition.
+// 2^-k]), each class with its own uniform grid of power-of-two cells per
+// axis, sized by occupancy (a cell holds about `cell_occupancy` spheres of
+// its class; any cell size is correct because the search scans every cell
+// within its radius).  Particles are sorted by the 62-bit key (class, cz, cy,
+// cx) with a hand-written LSD radix sort, and a dense per-class cell table
+// holds each cell's range [start, end) in that order.  A sphere scans its
+// own class and every coarser class over the cells within its search radius;
+// a pair inside one class is found from both ends, a pair across classes
+// from the finer end only, which emits both directions.  The pairs (row << b
+// | col) are radix-sorted into CSR rows with ascending columns.  Integer and
+// exact-predicate work only: the list is bit-identical to the definition.
 #include "rcp_internal.cuh"
 
 __device__ __forceinline__ double min_image_b(double t, double L, double h)
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_level(RcpCtl* ctl, long long N, const d
 // Cells per axis of each class: the largest power of two n <= 2^19 whose
 // cell holds at least c.cell_occ spheres of the class on average
 // (h^3 count >= cell_occ V, h = L/n).  The search scans every cell within
-// its radius, so any cell size is correct; this one balances hash lookups
+// its radius, so any cell size is correct; this one balances cell-table lookups
 // against candidates.  Also the periodic-image rule: every listed pair must
 // be closer than half a box edge, i.e. 4 rho_max < min L.
 __global__ void k_grid(RcpCtl* ctl, RcpConst c)

@@ -17,8 +17,18 @@
 #define RCP_TREE 1024          // elements per block of a tree-reduction pass
 #define RCP_SORT_THREADS 256
 #define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
-#define RCP_LONG_ROW 32        // default: rows longer than this get a warp in the mixed pair kernel
+#ifndef RCP_LONG_ROW
+#define RCP_LONG_ROW 32        // default: rows longer than this get a warp in the mixed pair kernel (<= 32)
+#endif
+#ifndef RCP_LONG_BLOCKS_MAX
 #define RCP_LONG_BLOCKS_MAX 592  // most blocks (8 warps each) that loop over the long rows
+#endif
+#ifndef RCP_LONG_DIV
+#define RCP_LONG_DIV 1536        // one long-row block per this many spheres (at least 2)
+#endif
+#ifndef RCP_LONG_LAST
+#define RCP_LONG_LAST 0          // 1: the long-row blocks come after the short-row blocks in the grid
+#endif
 #define RCP_WARP_ROW_THREADS 128   // binary64 warp-per-row kernel: 4 rows per block
 #define RCP_WARP_ROW_MAX_N 4096    // binary64 packings up to this size take a warp per row (measured
                                    // crossover: 2.5x faster at N = 1440, 2.8x slower at N = 2e4)
@@ -74,6 +84,9 @@ struct RcpCtl {
     // binary32 scalars of the next mixed iteration and the values they came from
     MixScalars mix;
     double mix_src[RCP_MIX_SRC];
+    // device-side loop of a replayed graph (k_loop_cond)
+    long long loop_last_iter;        // iter after the previous body pass of this replay (-1: none yet)
+    unsigned long long body_passes;  // body passes run so far (kernel accounting)
 };
 
 // Kernel parameters that never change during a run.
@@ -92,6 +105,7 @@ struct RcpConst {
     double invL[3];         // 1 / L_a
     float Lf[3];            // L_a in binary32
     float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
+    float qmargin;             // 2 max_a qscale[a]: absolute margin of the mixed pre-test
     unsigned int canon;        // 1: binary64 path (canonical sums); 0: mixed path
     int dim;                   // the caller's dimension: 3, or 2 (disks held in the plane z = L_z / 2)
     unsigned int long_row;     // rows longer than this get a warp (mixed)
@@ -107,11 +121,12 @@ struct RcpConst {
 
 // Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
 // 2^32) (integer subtraction wraps, which is exactly the minimum image), the
-// binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0.  One
-// 32-byte sector per gather.
+// binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0 as an
+// unevaluated binary32 sum.  One 32-byte sector per gather; the first 16
+// bytes (integer position and fl32(D_i^0)) are all the pre-test reads.
 struct __align__(32) MixRec {
-    int4 q;    // qx, qy, qz, and the bits of the binary32 D_i^0 - fl32(D_i^0)
-    float4 l;  // lx, ly, lz, fl32(D_i^0)
+    int4 q;    // qx, qy, qz, and the bits of fl32(D_i^0)
+    float4 l;  // lx, ly, lz, D_i^0 - fl32(D_i^0)
 };
 // Everything a pair kernel and the kappa step need about one packing, for
 // the batched kernels (one device array entry per packing).
@@ -199,6 +214,7 @@ __global__ void k_kappa0(RcpCtl* ctl, double phi0, double V, int dim);
 __global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, double eta_k, double tol,
                            long long iter_limit, int final_rung);
 __global__ void k_clear_halt(RcpCtl* ctl);
+__global__ void k_loop_cond(RcpCtl* ctl, cudaGraphConditionalHandle hc);
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
                                 const unsigned int* perm);
 __global__ void k_get_positions(long long N, RcpConst c, const double4_32a* x, double* out, const unsigned int* perm);

@@ -282,10 +282,29 @@ __global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, dou
     ctl->final_rung = final_rung;
     ctl->halted = ctl->iter >= iter_limit ? 1 : 0;
     ctl->verify = 0;
+    ctl->loop_last_iter = -1;
     if (!c.canon) mix_fill(ctl, c);
 }
 
 __global__ void k_clear_halt(RcpCtl* ctl) { ctl->halted = 0; }
+
+// End of a body pass of the graph's device-side loop: run the body again
+// unless an iteration halted (rebuild due, iteration limit, stop, error).
+// A pass that did not advance the iteration count also ends the loop, with
+// RCP_ERR_TIMEOUT, so the loop is bounded by the iteration limit whatever
+// happens (every pass that does not halt advances the count).
+__global__ void k_loop_cond(RcpCtl* ctl, cudaGraphConditionalHandle hc)
+{
+    ctl->body_passes += 1;
+    bool more = !ctl->halted;
+    if (more && ctl->iter == ctl->loop_last_iter) {
+        ctl->status = RCP_ERR_TIMEOUT;
+        ctl->halted = 1;
+        more = false;
+    }
+    ctl->loop_last_iter = ctl->iter;
+    if (!more) cudaGraphSetConditional(hc, 0);
+}
 
 // Rung values of every packing of a batch before a replay (thread p = packing p).
 __global__ void k_batch_set(const PackDev* P, const RungSet* rs, int B)

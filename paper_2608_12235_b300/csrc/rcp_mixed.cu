@@ -31,10 +31,15 @@ __device__ __forceinline__ MixRec make_rec(double4_32a p, const RcpConst& c)
     to_fixed(p.x, c.L[0], r.q.x, r.l.x);
     to_fixed(p.y, c.L[1], r.q.y, r.l.y);
     to_fixed(p.z, c.L[2], r.q.z, r.l.z);
-    r.l.w = (float)p.w;
-    r.q.w = __float_as_int((float)(p.w - (double)r.l.w));
+    const float dh = (float)p.w;
+    r.q.w = __float_as_int(dh);
+    r.l.w = (float)(p.w - (double)dh);
     return r;
 }
+
+// D_i^0 of a record: fl32(D_i^0) and the remainder D_i^0 - fl32(D_i^0).
+__device__ __forceinline__ float rec_D(const MixRec& r) { return __int_as_float(r.q.w); }
+__device__ __forceinline__ float rec_Dlo(const MixRec& r) { return r.l.w; }
 
 __device__ __forceinline__ double from_fixed(int q, float l, double L)
 {
@@ -196,8 +201,8 @@ __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& r
     const float r2l = ((t1 + t2) + (ex + ey + ez)) + 2.0f * ((xh * xl + yh * yl) + zh * zl);
     // d = kappa (D_i + D_j) / 2
     float sh, se;
-    two_sum(ri.l.w, rj.l.w, sh, se);
-    const float sl = se + (__int_as_float(ri.q.w) + __int_as_float(rj.q.w));
+    two_sum(rec_D(ri), rec_D(rj), sh, se);
+    const float sl = se + (rec_Dlo(ri) + rec_Dlo(rj));
     float dh, de;
     two_prod(S.kappa, 0.5f * sh, dh, de);
     const float dl = de + (S.kappa * (0.5f * sl) + S.kappa_lo * (0.5f * sh));
@@ -217,40 +222,51 @@ __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& r
     return __fdividef(u, 1.0f + sqrtf(1.0f - u));
 }
 
-// Terms of one listed pair (i, j): gradient into the compensated (g, c), the
-// j > i share of e and k into (es, ec), (ks, kc), and the overlap maximum.
-// Pairs are first tested in plain binary32 (r^2 > d^2 (1 + 1e-5) cannot
-// overlap); the rest go through precise_delta.
-struct PairAcc {
-    float g0, g1, g2, c0, c1, c2;
-};
-
-// Plain binary32 test: false when the pair certainly does not overlap.
-__device__ __forceinline__ bool pair_may_overlap(const MixRec& ri, const MixRec& rj, const MixScalars& S,
-                                                 const RcpConst& c)
+// Binary32 pre-test on the integer parts of two records (the first 16 bytes):
+// false when the pair certainly does not overlap.  Leaving out the
+// remainders moves each axis by less than one fixed-point unit, the whole
+// displacement by less than sqrt(3) units, so the pair is kept whenever
+// r_q <= d (1 + 1e-5) + 2 units (c.qmargin), r_q the distance of the integer
+// parts; the binary32 roundings of r_q^2 and d (a few 2^-24 each) sit far
+// inside the 1e-5.
+__device__ __forceinline__ bool pretest_q(const int4& qi, const int4& qj, const MixScalars& S, const RcpConst& c)
 {
-    const float fx = rec_dx(ri.q.x, ri.l.x, rj.q.x, rj.l.x, c.qscale[0]);
-    const float fy = rec_dx(ri.q.y, ri.l.y, rj.q.y, rj.l.y, c.qscale[1]);
-    const float fz = rec_dx(ri.q.z, ri.l.z, rj.q.z, rj.l.z, c.qscale[2]);
+    const float fx = (float)(int)((unsigned int)qi.x - (unsigned int)qj.x) * c.qscale[0];
+    const float fy = (float)(int)((unsigned int)qi.y - (unsigned int)qj.y) * c.qscale[1];
+    const float fz = (float)(int)((unsigned int)qi.z - (unsigned int)qj.z) * c.qscale[2];
     const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
-    const float d = S.kappa * (0.5f * (ri.l.w + rj.l.w));
-    return !(r2 > (d * d) * 1.00001f);
+    const float d = S.kappa * (0.5f * (__int_as_float(qi.w) + __int_as_float(qj.w)));
+    const float T = __fmaf_rn(d, 1.00001f, c.qmargin);
+    return !(r2 > T * T);
 }
 
-// The terms of a pair that passed pair_may_overlap.
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ int4 load_q(const MixRec* r, unsigned int j)
+{
+    return __ldg(reinterpret_cast<const int4*>(r) + 2 * (size_t)j);
+}
+
+// Gradient term of a pair that passed the pre-test (zero when the precise
+// overlap is not positive or the centres coincide); the j > i share of e and
+// k goes into (es, ec), (ks, kc), the overlap into md.
 __device__ __forceinline__ void pair_term_precise(const MixRec& ri, const MixRec& rj, long long i, unsigned int j,
-                                                  const MixScalars& S, const RcpConst& c, PairAcc& a, float& es,
-                                                  float& ec, float& ks, float& kc, float& md)
+                                                  const MixScalars& S, const RcpConst& c, float& t0, float& t1,
+                                                  float& t2, float& es, float& ec, float& ks, float& kc, float& md)
 {
     float dx, dy, dz, r;
+    t0 = t1 = t2 = 0.0f;
     const float delta = precise_delta(ri, rj, S, c, dx, dy, dz, r);
     if (!(delta > 0.0f)) return;
-    const float dd = S.kappa * (0.5f * (ri.l.w + rj.l.w));
+    const float dd = S.kappa * (0.5f * (rec_D(ri) + rec_D(rj)));
     if (r > 0.0f) {
         const float coef = __fdividef(S.eps * delta, dd * r);
-        acc2(a.g0, a.c0, -coef * dx);
-        acc2(a.g1, a.c1, -coef * dy);
-        acc2(a.g2, a.c2, -coef * dz);
+        t0 = -coef * dx;
+        t1 = -coef * dy;
+        t2 = -coef * dz;
     }
     if ((long long)j > i) {
         acc2(es, ec, (0.5f * S.eps) * (delta * delta));
@@ -269,8 +285,8 @@ __device__ __forceinline__ float skin_budget32(RcpCtl* ctl, const RcpConst& c, c
     const float ey = rec_dx(rn.q.y, rn.l.y, b.q.y, b.l.y, c.qscale[1]);
     const float ez = rec_dx(rn.q.z, rn.l.z, b.q.z, b.l.z, c.qscale[2]);
     const float disp = sqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, ez * ez))) * 1.00001f;
-    const float sig = __fmaf_rn(S.limA, rn.l.w, S.limB);
-    const float bi = 2.0f * (sig - disp) / rn.l.w * 0.99999f;
+    const float sig = __fmaf_rn(S.limA, rec_D(rn), S.limB);
+    const float bi = 2.0f * (sig - disp) / rec_D(rn) * 0.99999f;
     if (!(bi >= 0.0f)) {
         atomicOr(&ctl->disp_flag, 1u);
         return INFINITY;
@@ -322,26 +338,52 @@ __device__ __forceinline__ float warp_sum2f(float s, float c)
     return s + c;
 }
 
-// The pair kernel of the mixed path.  Blocks [0, c.long_blocks) give one
-// warp to each row longer than c.long_row (the rows of the largest spheres,
-// which hold hundreds of small neighbours): lanes stride over the row and the
+// The pair kernel of the mixed path.  Listed entries far outnumber
+// overlapping pairs (about 3 % in the dense packings at S = 5e5, where most
+// small spheres rattle in the voids of the large ones), so every row is taken
+// in two passes: pass 1 puts each listed partner through pretest_q, which
+// reads only the first 16 bytes of its record, and keeps a bit per partner
+// that may overlap; pass 2 takes the marked partners, in the row's order,
+// through the precise terms (so the sums are those of a single walk).
+// Blocks [0, c.long_blocks) give one warp to each row longer than c.long_row
+// (the rows of the largest spheres, holding hundreds of small neighbours):
+// lanes stride over the row, four strides per round trip to memory, and the
 // gradient is reduced with compensated shuffles.  The other blocks give one
-// thread to each remaining row.  Every row is taken in two passes: the plain
-// binary32 test over all partners (two or four loads in flight), keeping a
-// bit per partner that may overlap, then the precise terms for the marked
-// partners only, in the row's order (so the sums are those of a single walk).
-// Without the precise arithmetic inside the first loop the kernel fits in 40
-// registers, 6 blocks per SM.  Both paths end with the row's Adam step; warp
-// partials of e and k go to part_e/part_k.
+// thread to each remaining row, four partners per round trip; the row's
+// moments, build snapshot and own record are requested into L2 as the row
+// starts, so the Adam epilogue does not wait on DRAM.  The kernel is bound by
+// the latency of the col -> record chains, not by DRAM bytes or L1 traffic.
+// Both parts end with the row's Adam step (or its gradient out); warp partials
+// of e and k go to part_e/part_k.  The order of every sum depends only on the
+// list, so results are reproducible run to run.
 #ifndef RCP_MIX_MINB
-#define RCP_MIX_MINB 6   // resident blocks per SM the register budget is sized for
+#define RCP_MIX_MINB 5   // resident blocks per SM the register budget is sized for (48 registers)
 #endif
+#ifndef RCP_MIX_UNROLL
+#define RCP_MIX_UNROLL 4  // partners per round trip in pass 1 of a short row (2 or 4)
+#endif
+#ifndef RCP_MIX_PREFETCH
+#define RCP_MIX_PREFETCH 1  // L2 prefetch of the epilogue's streams at the row's start
+#endif
+__device__ __forceinline__ void prefetch_row(const float* m, const float* v, const MixRec* rb, const MixRec* rin,
+                                             long long i)
+{
+    prefetch_l2(m + 3 * i);
+    prefetch_l2(v + 3 * i);
+    prefetch_l2(rb + i);
+    prefetch_l2(rin + i);
+}
+#define RCP_MIX_WARPS (RCP_PAIR_THREADS / 32)
+
+__device__ __forceinline__ unsigned int lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
 __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, float* m, float* v, MixRec* rA,
                                                 MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
-                                                const unsigned int* long_rows, const MixRec* rb, double* part_e,
-                                                double* part_k, int mode, double* g_out, unsigned int blk)
+                                                const unsigned int* long_rows, const MixRec* rb, double* part_e, double* part_k, int mode,
+                                                double* g_out, unsigned int blk)
 {
-    __shared__ MixScalars Sw[RCP_PAIR_THREADS / 32];
+    const unsigned int FULL = 0xffffffffu;
+    __shared__ MixScalars Sw[RCP_MIX_WARPS];
     if (ctl->halted) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     MixScalars& S = Sw[warp];
@@ -351,13 +393,17 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
     MixRec* __restrict__ rout = parity ? rA : rB;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
     float bud = INFINITY;
+#if RCP_LONG_LAST
+    const unsigned int nshort = (unsigned int)((c.N + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS);
+    blk = blk >= nshort ? blk - nshort : blk + c.long_blocks;   // long-row blocks last in the grid
+#endif
     if (blk < c.long_blocks) {
         const unsigned int nlong = ctl->n_long;
-        const unsigned int nw = c.long_blocks * (RCP_PAIR_THREADS / 32);
-        for (unsigned int r = blk * (RCP_PAIR_THREADS / 32) + warp; r < nlong; r += nw) {
+        const unsigned int nw = c.long_blocks * RCP_MIX_WARPS;
+        for (unsigned int r = blk * RCP_MIX_WARPS + warp; r < nlong; r += nw) {
             const long long i = long_rows[r];
-            const MixRec ri = rin[i];
-            PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int4 qi = load_q(rin, (unsigned int)i);
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
             const unsigned int t1 = rowptr[i + 1];
             // windows of 32 warp strides: pass 1 marks, per lane, the strides
             // whose partner may overlap (four strides per round trip to
@@ -368,64 +414,105 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                 for (; m < 32u && w0 + 32u * (m + 3u) < t1; m += 4u) {
                     const unsigned int t = w0 + 32u * m;
                     const unsigned int j0 = col[t], j1 = col[t + 32], j2 = col[t + 64], j3 = col[t + 96];
-                    const MixRec r0 = rin[j0], r1 = rin[j1], r2 = rin[j2], r3 = rin[j3];
-                    if (pair_may_overlap(ri, r0, S, c)) hit |= 1u << m;
-                    if (pair_may_overlap(ri, r1, S, c)) hit |= 2u << m;
-                    if (pair_may_overlap(ri, r2, S, c)) hit |= 4u << m;
-                    if (pair_may_overlap(ri, r3, S, c)) hit |= 8u << m;
+                    const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1), q2 = load_q(rin, j2), q3 = load_q(rin, j3);
+                    if (pretest_q(qi, q0, S, c)) hit |= 1u << m;
+                    if (pretest_q(qi, q1, S, c)) hit |= 2u << m;
+                    if (pretest_q(qi, q2, S, c)) hit |= 4u << m;
+                    if (pretest_q(qi, q3, S, c)) hit |= 8u << m;
                 }
                 for (; m < 32u && w0 + 32u * m < t1; ++m)
-                    if (pair_may_overlap(ri, rin[col[w0 + 32u * m]], S, c)) hit |= 1u << m;
-                while (hit) {
-                    const unsigned int k = (unsigned int)__ffs(hit) - 1u;
-                    hit &= hit - 1u;
-                    const unsigned int j = col[w0 + 32u * k];
-                    pair_term_precise(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
+                    if (pretest_q(qi, load_q(rin, col[w0 + 32u * m]), S, c)) hit |= 1u << m;
+                if (hit) {
+                    const MixRec ri = rin[i];
+                    do {
+                        const unsigned int k = (unsigned int)__ffs(hit) - 1u;
+                        hit &= hit - 1u;
+                        const unsigned int j = col[w0 + 32u * k];
+                        float a0, a1, a2;
+                        pair_term_precise(ri, rin[j], i, j, S, c, a0, a1, a2, es, ec, ks, kc, md);
+                        acc2(g0, c0, a0);
+                        acc2(g1, c1, a1);
+                        acc2(g2, c2, a2);
+                    } while (hit);
                 }
             }
-            const float g0 = warp_sum2f(a.g0, a.c0);
-            const float g1 = warp_sum2f(a.g1, a.c1);
-            const float g2 = warp_sum2f(a.g2, a.c2);
-            if (lane == 0) bud = fminf(bud, row_epilogue(ctl, c, S, i, ri, g0, g1, g2, m, v, rout, rb, mode, g_out));
+            g0 = warp_sum2f(g0, c0);
+            g1 = warp_sum2f(g1, c1);
+            g2 = warp_sum2f(g2, c2);
+            if (lane == 0) bud = fminf(bud, row_epilogue(ctl, c, S, i, rin[i], g0, g1, g2, m, v, rout, rb, mode, g_out));
         }
     } else {
+        // one thread per row
         const long long i = (long long)(blk - c.long_blocks) * RCP_PAIR_THREADS + threadIdx.x;
         if (i < c.N) {
             const unsigned int t0 = rowptr[i], t1 = rowptr[i + 1];
             if (t1 - t0 <= c.long_row) {
-                const MixRec ri = rin[i];
-                PairAcc a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                // pass 1: the plain binary32 test marks the partners that may
-                // overlap (a row holds at most 32 entries here); pass 2 takes
-                // them again, in the same order, through the precise terms
+#if RCP_MIX_PREFETCH
+                // the epilogue's streams, requested now so that they wait in
+                // L2 rather than on the row's last round trip
+                if (mode == RCP_MODE_ADAM) prefetch_row(m, v, rb, rin, i);
+#endif
+                const int4 qi = load_q(rin, (unsigned int)i);
+                // pass 1: the pre-test marks the partners that may overlap (a
+                // row holds at most 32 entries here, RCP_MIX_UNROLL per round
+                // trip to memory)
                 unsigned int hit = 0u;
                 unsigned int t = t0;
+#if RCP_MIX_UNROLL == 4
+                for (; t + 4 <= t1; t += 4) {
+                    const unsigned int j0 = col[t], j1 = col[t + 1], j2 = col[t + 2], j3 = col[t + 3];
+                    const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1), q2 = load_q(rin, j2), q3 = load_q(rin, j3);
+                    if (pretest_q(qi, q0, S, c)) hit |= 1u << (t - t0);
+                    if (pretest_q(qi, q1, S, c)) hit |= 2u << (t - t0);
+                    if (pretest_q(qi, q2, S, c)) hit |= 4u << (t - t0);
+                    if (pretest_q(qi, q3, S, c)) hit |= 8u << (t - t0);
+                }
+#endif
                 for (; t + 2 <= t1; t += 2) {
                     const unsigned int j0 = col[t], j1 = col[t + 1];
-                    const MixRec r0 = rin[j0], r1 = rin[j1];
-                    if (pair_may_overlap(ri, r0, S, c)) hit |= 1u << (t - t0);
-                    if (pair_may_overlap(ri, r1, S, c)) hit |= 2u << (t - t0);
+                    const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1);
+                    if (pretest_q(qi, q0, S, c)) hit |= 1u << (t - t0);
+                    if (pretest_q(qi, q1, S, c)) hit |= 2u << (t - t0);
                 }
-                if (t < t1 && pair_may_overlap(ri, rin[col[t]], S, c)) hit |= 1u << (t - t0);
+                if (t < t1 && pretest_q(qi, load_q(rin, col[t]), S, c)) hit |= 1u << (t - t0);
+                // pass 2: the marked partners through the precise terms, in
+                // the row's order
+                const MixRec ri = rin[i];
+                float g0 = 0.f, g1 = 0.f, g2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
                 while (hit) {
                     const unsigned int k = (unsigned int)__ffs(hit) - 1u;
                     hit &= hit - 1u;
                     const unsigned int j = col[t0 + k];
-                    pair_term_precise(ri, rin[j], i, j, S, c, a, es, ec, ks, kc, md);
+                    float a0, a1, a2;
+                    pair_term_precise(ri, rin[j], i, j, S, c, a0, a1, a2, es, ec, ks, kc, md);
+                    acc2(g0, c0, a0);
+                    acc2(g1, c1, a1);
+                    acc2(g2, c2, a2);
                 }
-                bud = row_epilogue(ctl, c, S, i, ri, a.g0 + a.c0, a.g1 + a.c1, a.g2 + a.c2, m, v, rout, rb, mode,
-                                   g_out);
+                bud = row_epilogue(ctl, c, S, i, ri, g0 + c0, g1 + c1, g2 + c2, m, v, rout, rb, mode, g_out);
             }
         }
     }
     // per-warp partials (no block barrier: warps finish independently)
     push_budget32(ctl, bud);
-    warp_sum2(es, ec);
-    warp_sum2(ks, kc);
-    float wm = md;
-    for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_down_sync(0xffffffffu, wm, o));
+    // most lanes hold no overlap: lane 0 adds the others' compensated sums
+    // in lane order (the same order whatever the timing)
+    unsigned int nz = __ballot_sync(FULL, es != 0.f || ec != 0.f || ks != 0.f || kc != 0.f) & ~1u;
+    while (nz) {
+        const int l = __ffs(nz) - 1;
+        nz &= nz - 1u;
+        const float se = __shfl_sync(FULL, es, l), sec = __shfl_sync(FULL, ec, l);
+        const float sk = __shfl_sync(FULL, ks, l), skc = __shfl_sync(FULL, kc, l);
+        if (lane == 0) {
+            acc2(es, ec, se);
+            ec = ec + sec;
+            acc2(ks, kc, sk);
+            kc = kc + skc;
+        }
+    }
+    const float wm = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(md)));   // md >= 0
     if (lane == 0) {
-        const unsigned long long w = (unsigned long long)blk * (RCP_PAIR_THREADS / 32) + warp;
+        const unsigned long long w = (unsigned long long)blk * RCP_MIX_WARPS + warp;
         part_e[w] = (double)es + (double)ec;
         part_k[w] = (double)ks + (double)kc;
         if (wm > 0.f) {
@@ -461,8 +548,8 @@ k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode
 {
     const int p = batch_pack_m(bstart, B, blockIdx.x);
     const PackDev& q = P[p];
-    pair_mixed_body(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e, q.part_k,
-                    mode, q.g, blockIdx.x - bstart[p]);
+    pair_mixed_body(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e,
+                    q.part_k, mode, q.g, blockIdx.x - bstart[p]);
 }
 
 // Binary64 maximum overlap over the listed pairs of the current binary64

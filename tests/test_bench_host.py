@@ -25,8 +25,15 @@ def _captured_pairs():
         return int(re.search(r"traffic_pairs: (\d+)", f.read()).group(1))
 
 
-def test_traffic_is_reported_for_the_captured_library_and_state():
+def _captured_sha():
+    import re
+    with open(os.path.join(ROOT, "profiles", "k_pair_mixed-lognormal-n1e6-s5e5.md")) as f:
+        return re.search(r"sha256 prefix `([0-9a-f]+)`", f.read()).group(1)
+
+
+def test_traffic_is_reported_for_the_captured_library_and_state(monkeypatch):
     import bench
+    monkeypatch.setattr(bench, "library_sha", lambda: _captured_sha() + "0" * 48)
     P = _captured_pairs()
     for Pn in (P, int(P * 1.02), int(P * 0.98)):
         t, pairs = bench.pair_traffic(_args(), Pn)
@@ -35,8 +42,9 @@ def test_traffic_is_reported_for_the_captured_library_and_state():
 
 @pytest.mark.parametrize("kw,scale", [(dict(skin_abs=20.0), 1.0), (dict(skin_s=0.1), 1.0), ({}, 1.05), ({}, 0.9),
                                       (dict(workload="powerlaw-n1e5-s20"), 1.0)])
-def test_traffic_is_withheld_for_another_state(kw, scale):
+def test_traffic_is_withheld_for_another_state(kw, scale, monkeypatch):
     import bench
+    monkeypatch.setattr(bench, "library_sha", lambda: _captured_sha() + "0" * 48)
     assert bench.pair_traffic(_args(**kw), int(_captured_pairs() * scale)) == (None, None)
 
 

@@ -13,7 +13,11 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_the_allocating_entry_point_twice_in_a_row():
+@pytest.mark.parametrize("n", [3000, 300_000, 1 << 21])
+def test_noalloc_matches_the_allocating_entry_point_twice_in_a_row(n):
+    """Bit for bit against rcp_energy_grad, two calls in a row, at a size of
+    one finishing block, at one that needs the chunked finish (more than 1024
+    blocks of partials), and at the largest size the scratch holds."""
     import torch
 
     import oracle
@@ -21,7 +25,6 @@ def test_noalloc_matches_the_allocating_entry_point_twice_in_a_row():
 
     assert torch.cuda.is_available()
     build.build()
-    n = 3000
     D0 = inputs.lognormal(n, 0.5, 10.0)
     x = oracle.init_positions(5, n)
     k = oracle.kappa0(D0, 1.0, 0.55)
