@@ -473,14 +473,26 @@ rcp_status build_c(rcp_ctx* h)
     }
     // the pair kernels step 32-bit entry indices up to 64 past the last entry
     if (P >= (1ull << 32) - 1024) return fail(h, RCP_ERR_CAPACITY, "more than 2^32 - 1024 listed pairs");
-    // row and column fields are adjacent: 8-bit digits over all 2 nbits bits
-    std::vector<int> ps = field_shifts(0, 2 * nbits);
-    const unsigned long long* spairs = nullptr;
-    CKS(radix_sort(h, h->pairs1, nullptr, P, ps, h->pairs2, nullptr, h->pairs1, nullptr, &spairs, nullptr));
-    h->launches += 1;
-    k_csr<<<rcp_ceil_div((P > (unsigned long long)N ? P : (unsigned long long)N) + 1, 256), 256, 0, h->stream>>>(
-        spairs, (long long)P, N, nbits, h->rowptr, h->col);
-    CKL();
+    // CSR rows: per-row counts and their scan (rowptr), every column into its
+    // row's segment, each segment sorted (k_row_sort): the list a full sort
+    // of the keys gives, in a fraction of the memory passes
+    CK(cudaMemsetAsync(h->cnt, 0, sizeof(unsigned int) * ((size_t)N + 1), h->stream));
+    if (P > 0) {
+        h->launches += 1;
+        k_row_count<<<rcp_ceil_div(P, 256), 256, 0, h->stream>>>(h->pairs1, (long long)P, nbits, h->cnt);
+        CKL();
+    }
+    CKS(scan_u32(h, h->cnt, (unsigned long long)N + 1, h->rowptr, h->scan_tmp));
+    if (P > 0) {
+        CK(cudaMemsetAsync(h->cnt, 0, sizeof(unsigned int) * (size_t)N, h->stream));   // fill cursors
+        unsigned int* colu = reinterpret_cast<unsigned int*>(h->pairs2);
+        h->launches += 2;
+        k_row_scatter<<<rcp_ceil_div(P, 256), 256, 0, h->stream>>>(h->pairs1, (long long)P, nbits, h->rowptr,
+                                                                   h->cnt, colu);
+        k_row_sort<<<rcp_ceil_div(P, RCP_RS_CAP), 256, RCP_RS_BUF * sizeof(unsigned int), h->stream>>>(
+            h->rowptr, N, colu, h->col);
+        CKL();
+    }
     CKS(relist_long(h));
     h->launches += 1;
     k_build_end<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb, P);
@@ -1283,10 +1295,9 @@ rcp_status rcp_energy_grad_at(rcp_handle h, const double* x_dev, const double* k
     const size_t n = (size_t)h->N;
     CK(cudaMemcpyAsync(h->xtmp, x_dev, sizeof(double) * h->c.dim * n, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemcpyAsync(&h->ctl->kappa, kappa_dev, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    CKS(sync_ctl(h));  // parity and build state
-    double4_32a* cur = h->ctl_h->parity ? h->xB : h->xA;
-    h->launches += 1;
-    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, cur, h->perm);
+    h->launches += 1;   // into the current buffer, chosen on the device (no host read of the parity)
+    k_set_positions<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->N, h->c, h->xtmp, h->D0, h->xA, h->perm,
+                                                                  h->ctl, h->xB);
     CKL();
     if (h->cfg.precision == RCP_MIXED) {
         h->launches += 1;

@@ -14,7 +14,8 @@
 // own class and every coarser class over the cells within its search radius;
 // a pair inside one class is found from both ends, a pair across classes
 // from the finer end only, which emits both directions.  The pairs (row << b
-// | col) are radix-sorted into CSR rows with ascending columns.  Integer and
+// | col) become CSR rows with ascending columns (per-row counts, a scatter
+// into the rows, a shared-memory sort of each row).  Integer and
 // exact-predicate work only: the list is bit-identical to the definition.
 #include "rcp_internal.cuh"
 
@@ -570,24 +571,158 @@ k_place_conflicts(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_
                       kcur);
 }
 
-// CSR from the sorted pair keys: columns are the low bits; rowptr[i] is the
-// first entry of row i (binary search), rowptr[N] = P.
-__global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits, unsigned int* rowptr,
-                      unsigned int* col)
+// ---------------------------------------------------------------------------
+// CSR rows from the unsorted pair keys (row << nbits | col) without a global
+// sort: k_row_count counts the entries of every row, an exclusive scan of the
+// counts is rowptr, k_row_scatter drops every column into its row's segment
+// (an atomic cursor per row: arbitrary order inside the segment), and
+// k_row_sort sorts each segment in shared memory.  Columns within a row are
+// distinct, so the sorted list is unique: the same rows and columns, in the
+// same order, as a full sort of the keys, whatever the order of the atomics.
+// Within a warp, lanes of the same row share one atomic (__match_any_sync).
+__global__ void k_row_count(const unsigned long long* pairs, long long P, int nbits, unsigned int* cnt)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long mask = (1ull << nbits) - 1ull;
-    if (t < P) col[t] = (unsigned int)(pairs[t] & mask);
-    if (t <= N) {
-        const unsigned long long key = (unsigned long long)t << nbits;
-        long long lo = 0, hi = P;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int r = t < P ? (unsigned int)(pairs[t] >> nbits) : 0xffffffffu;
+    const unsigned int peers = __match_any_sync(0xffffffffu, r);
+    if (t < P && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[r], (unsigned int)__popc(peers));
+}
+
+__global__ void k_row_scatter(const unsigned long long* pairs, long long P, int nbits, const unsigned int* rowptr,
+                              unsigned int* fill, unsigned int* colu)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long key = t < P ? pairs[t] : ~0ull;
+    const unsigned int r = t < P ? (unsigned int)(key >> nbits) : 0xffffffffu;
+    const unsigned int peers = __match_any_sync(0xffffffffu, r);
+    const int lane = threadIdx.x & 31, lead = __ffs(peers) - 1;
+    unsigned int base = 0;
+    if (t < P && lane == lead) base = atomicAdd(&fill[r], (unsigned int)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (t < P) colu[rowptr[r] + base + __popc(peers & ((1u << lane) - 1u))] = (unsigned int)(key & ((1ull << nbits) - 1ull));
+}
+
+// Sort of the segment [a, a + len) of v ascending: insertion sort by one
+// thread (short rows).
+__device__ __forceinline__ void sort_serial(unsigned int* v, unsigned int len)
+{
+    for (unsigned int q = 1; q < len; ++q) {
+        const unsigned int x = v[q];
+        unsigned int p = q;
+        while (p > 0 && v[p - 1] > x) {
+            v[p] = v[p - 1];
+            --p;
+        }
+        v[p] = x;
+    }
+}
+
+// Bitonic sort of v[0, len) by one warp (rows longer than 32), in the form
+// whose comparators all put the smaller value first: each merge of blocks of
+// k starts by comparing element i with its mirror i ^ (k - 1), then halves.
+// The network runs over the next power of two with the missing elements as
+// +infinity, which then never move, so a comparator that reaches past len is
+// skipped.
+__device__ __forceinline__ void sort_warp(unsigned int* v, unsigned int len, int lane)
+{
+    unsigned int n2 = 1;
+    while (n2 < len) n2 <<= 1;
+    for (unsigned int k = 2; k <= n2; k <<= 1) {
+        for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned int i = (unsigned int)lane; i < n2; i += 32) {
+                const unsigned int l = (j == (k >> 1)) ? (i ^ (k - 1)) : (i ^ j);
+                if (l > i && l < len) {
+                    const unsigned int a = v[i], b = v[l];
+                    if (a > b) {
+                        v[i] = b;
+                        v[l] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// The same network by the whole block (rows longer than 256): one barrier
+// per stage; len is the same in every thread.
+__device__ __forceinline__ void sort_block(unsigned int* v, unsigned int len, int tid)
+{
+    unsigned int n2 = 1;
+    while (n2 < len) n2 <<= 1;
+    for (unsigned int k = 2; k <= n2; k <<= 1) {
+        for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned int i = (unsigned int)tid; i < n2; i += 256) {
+                const unsigned int l = (j == (k >> 1)) ? (i ^ (k - 1)) : (i ^ j);
+                if (l > i && l < len) {
+                    const unsigned int a = v[i], b = v[l];
+                    if (a > b) {
+                        v[i] = b;
+                        v[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Block b sorts the rows whose segment starts in [b RCP_RS_CAP, (b + 1)
+// RCP_RS_CAP): their entries are staged in shared memory when they fit
+// (RCP_RS_BUF), else sorted in place in global memory; rows of up to 32
+// entries by one thread each, up to 256 by a warp each, longer ones by the
+// whole block (a single warp's network over thousands of entries would be a
+// long chain of dependent shared-memory steps).
+__global__ void __launch_bounds__(256)
+k_row_sort(const unsigned int* rowptr, long long N, const unsigned int* colu, unsigned int* col)
+{
+    extern __shared__ unsigned int rs_buf[];
+    __shared__ unsigned int s_r[2], s_nmed, s_nlong;
+    __shared__ unsigned int s_med[256], s_long[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 2) {
+        // first row whose start is at or beyond the bucket's edge
+        const unsigned long long edge = ((unsigned long long)blockIdx.x + (unsigned long long)tid) * RCP_RS_CAP;
+        long long lo = 0, hi = N;
         while (lo < hi) {
-            long long mid = lo + (hi - lo) / 2;
-            if (pairs[mid] < key) lo = mid + 1;
+            const long long mid = (lo + hi) >> 1;
+            if ((unsigned long long)rowptr[mid] < edge) lo = mid + 1;
             else hi = mid;
         }
-        rowptr[t] = (unsigned int)lo;
+        s_r[tid] = (unsigned int)lo;
     }
+    if (tid == 0) s_nmed = s_nlong = 0;
+    __syncthreads();
+    const unsigned int rlo = s_r[0], rhi = s_r[1];
+    const unsigned int e0 = rowptr[rlo], e1 = rowptr[rhi];
+    const bool staged = e1 - e0 <= RCP_RS_BUF;
+    unsigned int* v = staged ? rs_buf : col + e0;
+    for (unsigned int e = e0 + tid; e < e1; e += 256) v[e - e0] = colu[e];
+    __syncthreads();
+    for (unsigned int r0 = rlo; r0 < rhi; r0 += 256) {
+        const unsigned int r = r0 + tid;
+        if (r < rhi) {
+            const unsigned int a = rowptr[r], len = rowptr[r + 1] - a;
+            if (len <= 32) sort_serial(v + (a - e0), len);
+            else if (len <= 256) s_med[atomicAdd(&s_nmed, 1u)] = r;
+            else s_long[atomicAdd(&s_nlong, 1u)] = r;
+        }
+        __syncthreads();
+        for (unsigned int q = warp; q < s_nmed; q += 8) {
+            const unsigned int r2 = s_med[q], a = rowptr[r2];
+            sort_warp(v + (a - e0), rowptr[r2 + 1] - a, lane);
+        }
+        for (unsigned int q = 0; q < s_nlong; ++q) {   // block-uniform loop
+            const unsigned int r2 = s_long[q], a = rowptr[r2];
+            __syncthreads();
+            sort_block(v + (a - e0), rowptr[r2 + 1] - a, tid);
+        }
+        __syncthreads();
+        if (tid == 0) s_nmed = s_nlong = 0;
+        __syncthreads();
+    }
+    if (staged)
+        for (unsigned int e = e0 + tid; e < e1; e += 256) col[e] = v[e - e0];
 }
 
 // Rows longer than long_row, compacted in ascending order (flags, an

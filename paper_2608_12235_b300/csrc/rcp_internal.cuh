@@ -216,7 +216,7 @@ __global__ void k_set_rung(RcpCtl* ctl, RcpConst c, double mu, double eta_x, dou
 __global__ void k_clear_halt(RcpCtl* ctl);
 __global__ void k_loop_cond(RcpCtl* ctl, cudaGraphConditionalHandle hc);
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
-                                const unsigned int* perm);
+                                const unsigned int* perm, const RcpCtl* ctl = nullptr, double4_32a* xB = nullptr);
 __global__ void k_get_positions(long long N, RcpConst c, const double4_32a* x, double* out, const unsigned int* perm);
 __global__ void k_place_draw(unsigned long long seed, long long N, long long r, int k, RcpConst c, const double* D0,
                              const int* lvl, const unsigned char* placed, unsigned char* reject, double4_32a* x);
@@ -306,8 +306,12 @@ __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const d
                          const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
                          const uint2* cells,
                          unsigned long long* pairs, unsigned long long cap, int nbits);
-__global__ void k_csr(const unsigned long long* pairs, long long P, long long N, int nbits,
-                      unsigned int* rowptr, unsigned int* col);
+__global__ void k_row_count(const unsigned long long* pairs, long long P, int nbits, unsigned int* cnt);
+__global__ void k_row_scatter(const unsigned long long* pairs, long long P, int nbits, const unsigned int* rowptr,
+                              unsigned int* fill, unsigned int* colu);
+__global__ void k_row_sort(const unsigned int* rowptr, long long N, const unsigned int* colu, unsigned int* col);
+#define RCP_RS_CAP 4096      // row starts per block of k_row_sort
+#define RCP_RS_BUF 11264     // entries a block of k_row_sort stages in shared memory (44 KB)
 __global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int long_row, unsigned int* flags);
 __global__ void k_long_compact(RcpCtl* ctl, const unsigned int* flags, const unsigned int* offs, long long N,
                                unsigned int* long_rows);

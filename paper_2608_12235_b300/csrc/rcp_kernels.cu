@@ -353,11 +353,14 @@ __global__ void k_batch_status(const PackDev* P, BatchStat* out, int B)
 // Caller positions [N][3] -> (x, y, z, D0) records, wrapped into the box.
 // Positions from a caller's [N][3] array (sphere order of the caller; perm,
 // when not NULL, gives the caller's index of each internal sphere).
+// ctl (when not NULL) picks the buffer holding the current positions on the
+// device (x = xB when the parity is odd), so the host need not read it.
 __global__ void k_set_positions(long long N, RcpConst c, const double* xin, const double* D0, double4_32a* x,
-                                const unsigned int* perm)
+                                const unsigned int* perm, const RcpCtl* ctl, double4_32a* xB)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (ctl && ctl->parity) x = xB;
     const long long u = perm ? (long long)perm[i] : i;
     double p[3];
     for (int a = 0; a < 3; ++a) {
