@@ -386,6 +386,7 @@ def profile_window(args, w):
     p = rcp.Packing(D0, box=1.0, seed=0, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs, skin_s=args.skin_s)
     r = p.run(max_iters=args.densify, shrink=False)
     rcp.rcp_build_neighbors(p.h)
+    listed = int(p.neighbors()[1].size)   # entries of the list the window walks
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     if args.profile_window == "pair":
@@ -396,7 +397,7 @@ def profile_window(args, w):
         p.run(max_iters=100, shrink=False)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print(f"window done: iters={r.iters} pairs={r.pairs}")
+    print(f"window done: iters={r.iters} listed entries={listed}")
     p.close()
 
 

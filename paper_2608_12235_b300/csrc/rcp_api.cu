@@ -933,6 +933,11 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         c.qscale[a] = (float)(box[a] * 0x1.0p-32);
         c.qinv[a] = (float)(0x1.0p32 / box[a]);
         c.invL[a] = 1.0 / box[a];
+        c.invLf[a] = (float)c.invL[a];
+        {
+            int ex = 0;
+            if (std::frexp(box[a], &ex) == 0.5) c.pow2L |= 1 << a;
+        }
         {
             const double sc = box[a] * 0x1.0p-32;
             c.qs_hi[a] = (float)sc;

@@ -161,7 +161,10 @@ __global__ void k_grid(RcpCtl* ctl, RcpConst c)
         const int k = t / 3, a = t % 3;
         const double r = bitsd(ctl->rho_lvl_bits[k]);
         const double cnt = (double)ctl->lvl_count[k];
-        if (a == 0) ctl->rho_lvl[k] = r;
+        if (a == 0) {
+            ctl->rho_lvl[k] = r;
+            ctl->rho_lvl_f[k] = (float)r;
+        }
         unsigned int n = 1;
         if (r > 0.0 && a < c.dim)   // d = 2: one cell layer in z, area occupancy in x and y
             for (;;) {
@@ -193,9 +196,12 @@ __global__ void k_grid(RcpCtl* ctl, RcpConst c)
     }
 }
 
-__device__ __forceinline__ unsigned int cell_of(double x, double L, unsigned int n)
+// fl(x / L) n, floored: with L a power of two the quotient is the product
+// with 1 / L, exactly (both are the correctly rounded x 2^-e), which spares a
+// binary64 division per axis.
+__device__ __forceinline__ unsigned int cell_of(double x, double L, double invL, bool pow2, unsigned int n)
 {
-    double f = floor((x / L) * (double)n);
+    double f = floor((pow2 ? x * invL : x / L) * (double)n);
     long long cc = (long long)f;
     if (cc < 0) cc = 0;
     if (cc > (long long)n - 1) cc = (long long)n - 1;
@@ -217,9 +223,9 @@ __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const
     const double4_32a* x = ctl->parity ? xB : xA;
     const double4_32a p = x[i];
     const int k = lvl[i];
-    unsigned int cx = cell_of(p.x, c.L[0], (unsigned int)ctl->ng[k][0]);
-    unsigned int cy = cell_of(p.y, c.L[1], (unsigned int)ctl->ng[k][1]);
-    unsigned int cz = cell_of(p.z, c.L[2], (unsigned int)ctl->ng[k][2]);
+    unsigned int cx = cell_of(p.x, c.L[0], c.invL[0], c.pow2L & 1, (unsigned int)ctl->ng[k][0]);
+    unsigned int cy = cell_of(p.y, c.L[1], c.invL[1], c.pow2L & 2, (unsigned int)ctl->ng[k][1]);
+    unsigned int cz = cell_of(p.z, c.L[2], c.invL[2], c.pow2L & 4, (unsigned int)ctl->ng[k][2]);
     key[i] = pack_key((unsigned int)k, cz, cy, cx);
     idx[i] = (unsigned int)i;
 }
@@ -451,15 +457,18 @@ __device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, cons
             }
         }
         for (int k = 0; k <= kend; ++k) {
-            const double rk = ctl->rho_lvl[k];
-            if (!(rk > 0.0)) continue;
+            const float rk = ctl->rho_lvl_f[k];
+            if (!(rk > 0.0f)) continue;
             int lo[3];
             unsigned int nc[3], ng[3];
             for (int a = 0; a < 3; ++a) {
                 ng[a] = (unsigned int)ctl->ng[k][a];
-                // search radius in box units with a margin far above the
-                // binary32 errors of u and of the product below
-                const float Ru = (float)(((ri + rk) * c.invL[a]) * (1.0 + 1e-6) + 2e-6);
+                // search radius in box units, in binary32: rho_i, rho_k and
+                // 1/L_a are each within 2^-24 of their binary64 values and the
+                // sum and product round twice more, a few 1e-7 in all, far
+                // inside the 1e-6 relative margin; 2e-6 covers the rounding of
+                // u (a window only has to be wide enough)
+                const float Ru = __fmaf_rn((ui.w + rk) * c.invLf[a], 1.000001f, 2e-6f);
                 const float fn = (float)ng[a];
                 int l = (int)floorf((u3[a] - Ru) * fn);
                 int h = (int)floorf((u3[a] + Ru) * fn);

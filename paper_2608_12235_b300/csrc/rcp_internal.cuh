@@ -26,9 +26,6 @@
 #ifndef RCP_LONG_DIV
 #define RCP_LONG_DIV 1536        // one long-row block per this many spheres (at least 2)
 #endif
-#ifndef RCP_LONG_LAST
-#define RCP_LONG_LAST 0          // 1: the long-row blocks come after the short-row blocks in the grid
-#endif
 #define RCP_WARP_ROW_THREADS 128   // binary64 warp-per-row kernel: 4 rows per block
 #define RCP_WARP_ROW_MAX_N 4096    // binary64 packings up to this size take a warp per row (measured
                                    // crossover: 2.5x faster at N = 1440, 2.8x slower at N = 2e4)
@@ -69,6 +66,7 @@ struct RcpCtl {
     unsigned long long lvl_count[RCP_KMAX];
     unsigned long long pair_cursor;   // entries emitted by the pair search
     double rho_lvl[RCP_KMAX];
+    float rho_lvl_f[RCP_KMAX];   // fl32 of rho_lvl (the search windows' binary32 radii)
     int nlev;
     int ng[RCP_KMAX][3];
     unsigned long long cell_off[RCP_KMAX + 1];  // first entry of each class in the dense cell table
@@ -103,6 +101,8 @@ struct RcpConst {
     float qscale[3];        // L_a / 2^32: fixed-point unit of axis a
     float qinv[3];          // 2^32 / L_a
     double invL[3];         // 1 / L_a
+    float invLf[3];         // fl32(1 / L_a)
+    int pow2L;              // bit a: L_a is a power of two, so x / L_a == x * (1 / L_a) exactly
     float Lf[3];            // L_a in binary32
     float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
     float qmargin;             // 2 max_a qscale[a]: absolute margin of the mixed pre-test

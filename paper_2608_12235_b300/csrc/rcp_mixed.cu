@@ -359,12 +359,6 @@ __device__ __forceinline__ float warp_sum2f(float s, float c)
 #ifndef RCP_MIX_MINB
 #define RCP_MIX_MINB 5   // resident blocks per SM the register budget is sized for (48 registers)
 #endif
-#ifndef RCP_MIX_UNROLL
-#define RCP_MIX_UNROLL 4  // partners per round trip in pass 1 of a short row (2 or 4)
-#endif
-#ifndef RCP_MIX_PREFETCH
-#define RCP_MIX_PREFETCH 1  // L2 prefetch of the epilogue's streams at the row's start
-#endif
 __device__ __forceinline__ void prefetch_row(const float* m, const float* v, const MixRec* rb, const MixRec* rin,
                                              long long i)
 {
@@ -393,10 +387,6 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
     MixRec* __restrict__ rout = parity ? rA : rB;
     float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f, md = 0.f;
     float bud = INFINITY;
-#if RCP_LONG_LAST
-    const unsigned int nshort = (unsigned int)((c.N + RCP_PAIR_THREADS - 1) / RCP_PAIR_THREADS);
-    blk = blk >= nshort ? blk - nshort : blk + c.long_blocks;   // long-row blocks last in the grid
-#endif
     if (blk < c.long_blocks) {
         const unsigned int nlong = ctl->n_long;
         const unsigned int nw = c.long_blocks * RCP_MIX_WARPS;
@@ -447,18 +437,15 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
         if (i < c.N) {
             const unsigned int t0 = rowptr[i], t1 = rowptr[i + 1];
             if (t1 - t0 <= c.long_row) {
-#if RCP_MIX_PREFETCH
                 // the epilogue's streams, requested now so that they wait in
                 // L2 rather than on the row's last round trip
                 if (mode == RCP_MODE_ADAM) prefetch_row(m, v, rb, rin, i);
-#endif
                 const int4 qi = load_q(rin, (unsigned int)i);
                 // pass 1: the pre-test marks the partners that may overlap (a
-                // row holds at most 32 entries here, RCP_MIX_UNROLL per round
-                // trip to memory)
+                // row holds at most 32 entries here, four per round trip to
+                // memory)
                 unsigned int hit = 0u;
                 unsigned int t = t0;
-#if RCP_MIX_UNROLL == 4
                 for (; t + 4 <= t1; t += 4) {
                     const unsigned int j0 = col[t], j1 = col[t + 1], j2 = col[t + 2], j3 = col[t + 3];
                     const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1), q2 = load_q(rin, j2), q3 = load_q(rin, j3);
@@ -467,7 +454,6 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                     if (pretest_q(qi, q2, S, c)) hit |= 4u << (t - t0);
                     if (pretest_q(qi, q3, S, c)) hit |= 8u << (t - t0);
                 }
-#endif
                 for (; t + 2 <= t1; t += 2) {
                     const unsigned int j0 = col[t], j1 = col[t + 1];
                     const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1);
