@@ -597,6 +597,12 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
                                                           h->col, h->xb, h->part_e, h->part_k, mode, h->g);
     }
     if (ev) cudaEventRecord(ev[1], h->stream);
+    if (h->cfg.precision == RCP_MIXED) {
+        // warp partials as compensated binary32 pairs, reduced and closed by one kernel
+        k_kappa_mixed<<<1, 1024, 0, h->stream>>>(h->ctl, h->c, h->part_e, h->part_k, (long long)launch_blocks(h), mode);
+        if (ev) cudaEventRecord(ev[2], h->stream);
+        return 2;
+    }
     const bool wr = warp_rows(h);
     const long long n0 = wr ? h->N : (long long)launch_blocks(h);
     const double* pe;
@@ -1839,7 +1845,10 @@ void batch_iteration(rcp_batch_ctx* b, int mode)
         k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
     else
         k_pair64_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
-    k_kappa_step_batch<<<b->B, 1024, b->kappa_smem, b->stream>>>(b->d_packs, mode);
+    if (b->precision == RCP_MIXED)
+        k_kappa_mixed_batch<<<b->B, 1024, 0, b->stream>>>(b->d_packs, mode);
+    else
+        k_kappa_step_batch<<<b->B, 1024, b->kappa_smem, b->stream>>>(b->d_packs, mode);
 }
 
 rcp_status batch_capture(rcp_batch_ctx* b)

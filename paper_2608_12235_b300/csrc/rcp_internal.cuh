@@ -156,6 +156,37 @@ enum { RCP_MODE_ADAM = 0, RCP_MODE_GRAD = 1 };
 __device__ __forceinline__ double size_at(double D0, double kappa) { return D0 >= 0.0 ? kappa * D0 : -D0; }
 __device__ __forceinline__ double mobile_part(double D0) { return D0 > 0.0 ? D0 : 0.0; }
 
+// ---- binary64 pair pre-test ----
+// A listed pair with fl(r^2) > fl(fl(d d) (1 + 1e-12)) cannot overlap in
+// binary64: then r^2 > d^2 (1 + 0.9999e-12), so fl(sqrt(r^2)) > d (1 + 4e-13)
+// and fl(r / d) > 1, i.e. delta = 1 - r/d <= 0 (each step rounds by at most
+// 2^-53 relative).  Such pairs skip the square root and the division, which
+// are long sequences on B300's binary64 pipe; every pair that may overlap
+// still takes the oracle's exact operations, so results are unchanged.
+#define RCP_NO_OVERLAP_MARGIN (1.0 + 1e-12)
+
+// 2Sum accumulation: s + c carries the sum of the added binary32 terms to
+// within about one rounding of the result (Knuth's TwoSum; no FMA contraction
+// in this library, so the error term is exact).
+__device__ __forceinline__ void acc2(float& s, float& c, float x)
+{
+    const float t = s + x;
+    const float z = t - s;
+    c = c + ((s - (t - z)) + (x - z));
+    s = t;
+}
+
+// Warp sum of compensated pairs; the full (s, c) lands in lane 0.
+__device__ __forceinline__ void warp_sum2(float& s, float& c)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_down_sync(0xffffffffu, s, o);
+        const float co = __shfl_down_sync(0xffffffffu, c, o);
+        acc2(s, c, so);
+        c = c + co;
+    }
+}
+
 // ---- small helpers ----
 #define RCP_KBUD_INF 0x7F800000u
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
@@ -233,6 +264,10 @@ __global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* 
                          double* part_e, double* part_k, int mode, double* g_out);
 __global__ void k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e, const double* part_k,
                              long long nb, int mode);
+__device__ void kappa_close(RcpCtl* ctl, const RcpConst& c, double se, double sk, int mode);
+__global__ void k_kappa_mixed(RcpCtl* ctl, RcpConst c, const double* part_e, const double* part_k, long long n,
+                              int mode);
+__global__ void k_kappa_mixed_batch(const PackDev* P, int mode);
 // Per-packing rung values for a batched replay, and the status read back.
 struct RungSet {
     double mu, eta_x, eta_k, tol;

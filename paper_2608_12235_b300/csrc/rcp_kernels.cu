@@ -500,9 +500,10 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
             double dy = axis_diff(c, 1, xi.y - xj.y);
             double dz = axis_diff(c, 2, xi.z - xj.z);
             double r2 = dx * dx + dy * dy + dz * dz;
-            double r = sqrt(r2);
             const bool both = xi.w > 0.0 && xj.w > 0.0;   // no frozen sphere in the pair
             double dd = both ? kappa * (0.5 * (xi.w + xj.w)) : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
+            if (r2 > (dd * dd) * RCP_NO_OVERLAP_MARGIN) continue;   // certainly delta <= 0: no square root, no division
+            double r = sqrt(r2);
             double delta = 1.0 - r / dd;
             if (delta > 0.0) {
                 if (r > 0.0 && xi.w > 0.0) {
@@ -601,19 +602,22 @@ k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double*
                 double dy = axis_diff(c, 1, xi.y - xj.y);
                 double dz = axis_diff(c, 2, xi.z - xj.z);
                 double r2 = dx * dx + dy * dy + dz * dz;
-                double r = sqrt(r2);
                 const bool both = xi.w > 0.0 && xj.w > 0.0;
                 double dd = both ? kappa * (0.5 * (xi.w + xj.w)) : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
-                double delta = 1.0 - r / dd;
-                if (delta > 0.0) {
-                    hit = true;
-                    if (r > 0.0 && xi.w > 0.0) {
+                double delta = 0.0;
+                if (!(r2 > (dd * dd) * RCP_NO_OVERLAP_MARGIN)) {   // else certainly delta <= 0
+                    double r = sqrt(r2);
+                    delta = 1.0 - r / dd;
+                    if (delta > 0.0 && r > 0.0 && xi.w > 0.0) {
                         grad = true;
                         double coef = (c.eps * delta) / (dd * r);
                         tx = coef * dx;
                         ty = coef * dy;
                         tz = coef * dz;
                     }
+                }
+                if (delta > 0.0) {
+                    hit = true;
                     if ((long long)j > i) {
                         upper = true;
                         te = (0.5 * c.eps) * (delta * delta);
@@ -756,9 +760,17 @@ __device__ __forceinline__ void kappa_step_body(RcpCtl* ctl, const RcpConst& c, 
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
+    kappa_close(ctl, c, be[0], bk[0], mode);
+}
+
+// The scalar part of closing an evaluation (one thread), from the sums of the
+// pair terms: E and dE/dkappa with the growth term, the largest overlap, the
+// stopping test of App. A, and in Adam mode the kappa step.
+__device__ void kappa_close(RcpCtl* ctl, const RcpConst& c, double se, double sk, int mode)
+{
     const double mu = ctl->mu, kappa = ctl->kappa;
-    const double E = be[0] - mu * (kappa * ctl->SD);
-    const double dEdk = bk[0] - mu * ctl->SD;
+    const double E = se - mu * (kappa * ctl->SD);
+    const double dEdk = sk - mu * ctl->SD;
     const double md = bitsd(ctl->maxdelta_bits);
     ctl->maxdelta_bits = 0ull;
     ctl->E = E;
@@ -801,6 +813,61 @@ __global__ void __launch_bounds__(1024) k_kappa_step_batch(const PackDev* P, int
     extern __shared__ double buf[];
     const PackDev& q = P[blockIdx.x];
     kappa_step_body(q.ctl, q.c, q.part_e, q.part_k, q.nparts, mode, buf);
+}
+
+// Close a mixed-precision evaluation: the warp partials (compensated binary32
+// pairs) are summed in one fixed order -- thread t takes partials t, t + 1024,
+// ... with 2Sum, then the threads' pairs meet in a fixed tree -- and widened to
+// binary64 at the end (binary64 adds are slow on B300, and the partials carry
+// no more than binary32 pairs anyway); the rest is the kappa step of the
+// binary64 path.  One kernel instead of a tree pass and the kappa step.
+__device__ __forceinline__ void kappa_mixed_body(RcpCtl* ctl, const RcpConst& c, const float2* pe, const float2* pk,
+                                                 long long n, int mode)
+{
+    __shared__ float sh[4][32];
+    if (ctl->halted) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float es = 0.f, ec = 0.f, ks = 0.f, kc = 0.f;
+    for (long long t = tid; t < n; t += blockDim.x) {
+        const float2 a = pe[t], b = pk[t];
+        acc2(es, ec, a.x);
+        ec = ec + a.y;
+        acc2(ks, kc, b.x);
+        kc = kc + b.y;
+    }
+    warp_sum2(es, ec);
+    warp_sum2(ks, kc);
+    if (lane == 0) {
+        sh[0][warp] = es;
+        sh[1][warp] = ec;
+        sh[2][warp] = ks;
+        sh[3][warp] = kc;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const int nw = (int)(blockDim.x >> 5);
+    es = lane < nw ? sh[0][lane] : 0.f;
+    ec = lane < nw ? sh[1][lane] : 0.f;
+    ks = lane < nw ? sh[2][lane] : 0.f;
+    kc = lane < nw ? sh[3][lane] : 0.f;
+    warp_sum2(es, ec);
+    warp_sum2(ks, kc);
+    if (lane == 0) kappa_close(ctl, c, (double)es + (double)ec, (double)ks + (double)kc, mode);
+}
+
+__global__ void __launch_bounds__(1024) k_kappa_mixed(RcpCtl* ctl, RcpConst c, const double* part_e,
+                                                      const double* part_k, long long n, int mode)
+{
+    kappa_mixed_body(ctl, c, reinterpret_cast<const float2*>(part_e), reinterpret_cast<const float2*>(part_k), n,
+                     mode);
+}
+
+// Batched: block p closes the iteration of packing p.
+__global__ void __launch_bounds__(1024) k_kappa_mixed_batch(const PackDev* P, int mode)
+{
+    const PackDev& q = P[blockIdx.x];
+    kappa_mixed_body(q.ctl, q.c, reinterpret_cast<const float2*>(q.part_e), reinterpret_cast<const float2*>(q.part_k),
+                     q.nparts, mode);
 }
 
 // Binary64 verdict on a binary32 stop candidate: stop on the evaluated state,

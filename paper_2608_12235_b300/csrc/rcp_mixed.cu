@@ -88,28 +88,6 @@ __global__ void k_snap_records(RcpCtl* ctl, long long N, const MixRec* rA, const
     rb[i] = (ctl->parity ? rB : rA)[i];
 }
 
-// 2Sum accumulation: s + c carries the sum of the added binary32 terms to
-// within about one rounding of the result (Knuth's TwoSum; no FMA contraction
-// in this library, so the error term is exact).
-__device__ __forceinline__ void acc2(float& s, float& c, float x)
-{
-    const float t = s + x;
-    const float z = t - s;
-    c = c + ((s - (t - z)) + (x - z));
-    s = t;
-}
-
-// Warp sum of compensated pairs; the full (s, c) lands in lane 0.
-__device__ __forceinline__ void warp_sum2(float& s, float& c)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        const float so = __shfl_down_sync(0xffffffffu, s, o);
-        const float co = __shfl_down_sync(0xffffffffu, c, o);
-        acc2(s, c, so);
-        c = c + co;
-    }
-}
-
 __global__ void k_mix_refresh(RcpCtl* ctl, RcpConst c) { mix_fill(ctl, c); }
 
 // A warp's private copy of the scalars: lanes copy the stored binary32 words;
@@ -498,9 +476,10 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
     }
     const float wm = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(md)));   // md >= 0
     if (lane == 0) {
+        // the warp's compensated sums (sum, correction), in binary32
         const unsigned long long w = (unsigned long long)blk * RCP_MIX_WARPS + warp;
-        part_e[w] = (double)es + (double)ec;
-        part_k[w] = (double)ks + (double)kc;
+        reinterpret_cast<float2*>(part_e)[w] = make_float2(es, ec);
+        reinterpret_cast<float2*>(part_k)[w] = make_float2(ks, kc);
         if (wm > 0.f) {
             const unsigned long long b = dbits((double)wm);
             if (b > *(volatile unsigned long long*)&ctl->maxdelta_bits) atomicMax(&ctl->maxdelta_bits, b);
@@ -558,8 +537,10 @@ k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* 
             if (dx > c.halfL[0]) dx = dx - c.L[0]; else if (dx < -c.halfL[0]) dx = dx + c.L[0];
             if (dy > c.halfL[1]) dy = dy - c.L[1]; else if (dy < -c.halfL[1]) dy = dy + c.L[1];
             if (dz > c.halfL[2]) dz = dz - c.L[2]; else if (dz < -c.halfL[2]) dz = dz + c.L[2];
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            const double r2 = dx * dx + dy * dy + dz * dz;
             const double dd = kappa * (0.5 * (xi.w + xj.w));
+            if (r2 > (dd * dd) * RCP_NO_OVERLAP_MARGIN) continue;   // certainly delta <= 0
+            const double r = sqrt(r2);
             const double delta = 1.0 - r / dd;
             if (delta > md) md = delta;
         }
