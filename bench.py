@@ -221,17 +221,23 @@ def bench_batch(rcp, torch, iters: int, seed: int = 0, count: int = 64):
 
 
 def bench_autograd(rcp, torch, reps: int = 20):
-    """Fused forward + backward of the autograd binding (binary64) on N = 2e5
-    truncated Weibull (k = 1.5, S = 100) at phi = 0.6, uniform positions."""
+    """Fused forward + backward of the autograd binding on N = 2e5 truncated
+    Weibull (k = 1.5, S = 100) at phi = 0.6, uniform positions, in both
+    precisions: calls per second of the whole torch forward + backward, the
+    C-ABI evaluation alone (positions in, E, dE/dx, dE/dkappa out), and the
+    pair kernel on the same list (in an Adam iteration, `rcp_profile`) with
+    its algorithmic bandwidth: per sphere 148 B mixed (row pointer 4, record
+    32 read + 32 written, moments 24 + 24, snapshot 32) or 196 B binary64
+    (row pointer 4, position 32 + 32, moments 48 + 48, snapshot 32), per
+    listed entry 4 B."""
     from paper_2608_12235_b300 import autograd, inputs
     D0 = inputs.weibull(200_000, 1.5, 100.0)
-    p = rcp.Packing(D0, seed=0)
     dev = torch.device("cuda", 0)
     S3 = float(np.sum(D0 ** 3))
     k = (0.6 / (np.pi / 6 * S3)) ** (1 / 3)
     x = torch.rand((D0.size, 3), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(0))
     kt = torch.tensor(k, dtype=torch.float64, device=dev)
-    out = {}
+    out = {"workload": "weibull-n2e5-s100 phi 0.6"}
     for name, prec in (("fp64", rcp.RCP_FP64), ("mixed", rcp.RCP_MIXED)):
         p = rcp.Packing(D0, seed=0, precision=prec)
         xr = x.clone().requires_grad_(True)
@@ -243,10 +249,23 @@ def bench_autograd(rcp, torch, reps: int = 20):
             xr.grad = None
             autograd.energy(xr, kt, p, 0.0).backward()
         torch.cuda.synchronize()
-        out[name] = reps / (time.perf_counter() - t0)
+        out[f"fwd_bwd_per_s_{name}"] = reps / (time.perf_counter() - t0)
+        E = torch.empty(1, dtype=torch.float64, device=dev)
+        dk = torch.empty_like(E)
+        g = torch.empty_like(x)
+        kk = kt.reshape(1)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            rcp.rcp_energy_grad_at(p.h, x, kk, 0.0, E, g, dk, None)
+        torch.cuda.synchronize()
+        out[f"abi_eval_ms_{name}"] = (time.perf_counter() - t0) / reps * 1e3
+        P = int(p.neighbors()[1].size)
+        ms_pair, _, nl = rcp.rcp_profile(p.h, 5)
+        per_sphere = 148.0 if prec == rcp.RCP_MIXED else 196.0
+        out[f"pair_kernel_ms_{name}"] = ms_pair / nl
+        out[f"pair_kernel_gbs_{name}"] = (per_sphere * D0.size + 4.0 * P) / (ms_pair / nl * 1e-3) / 1e9
         p.close()
-    return {"workload": "weibull-n2e5-s100 phi 0.6", "fwd_bwd_per_s_fp64": out["fp64"],
-            "fwd_bwd_per_s_mixed": out["mixed"]}
+    return out
 
 
 def bench_rows(rcp, torch, large: bool = False):

@@ -547,7 +547,7 @@ unsigned int launch_blocks(const rcp_ctx* h)
 // Binary64 packings up to RCP_WARP_ROW_MAX_N spheres take a warp per row
 // (k_pair64_warp), which leaves one e_i and k_i per row instead of block
 // partials.
-bool warp_rows(const rcp_ctx* h) { return h->c.canon && h->row_e != nullptr; }
+bool warp_rows(const rcp_ctx* h) { return h->c.canon && h->N <= RCP_WARP_ROW_MAX_N; }
 
 // Reduce the pair kernel's partials a, b (n of each) to <= 8192 entries by
 // tree passes over aligned groups (the canonical order); returns the buffers
@@ -593,8 +593,12 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
         k_pair64_warp<<<rcp_ceil_div(h->N * 32, RCP_WARP_ROW_THREADS), RCP_WARP_ROW_THREADS, 0, h->stream>>>(
             h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr, h->col, h->xb, h->row_e, h->row_k, mode, h->g);
     } else {
+        k_pair64_long<<<RCP_LONG_BLOCKS_MAX, RCP_PAIR_THREADS, 0, h->stream>>>(
+            h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr, h->col, h->long_rows, h->xb, h->row_e, h->row_k,
+            mode, h->g);
         k_pair64<<<nb, RCP_PAIR_THREADS, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->m64, h->v64, h->rowptr,
-                                                          h->col, h->xb, h->part_e, h->part_k, mode, h->g);
+                                                          h->col, h->xb, h->part_e, h->part_k, mode, h->g, h->row_e,
+                                                          h->row_k);
     }
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (h->cfg.precision == RCP_MIXED) {
@@ -611,7 +615,7 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
     prereduce(h, wr ? h->row_e : h->part_e, wr ? h->row_k : h->part_k, n0, &pe, &pk, &n);
     k_kappa_step<<<1, 1024, kappa_smem(n), h->stream>>>(h->ctl, h->c, pe, pk, n, mode);
     if (ev) cudaEventRecord(ev[2], h->stream);
-    int passes = 0;
+    int passes = h->c.long64 ? 1 : 0;   // k_pair64_long
     for (long long m = n0; m > 8192; m = (m + RCP_TREE - 1) / RCP_TREE) ++passes;
     return 2 + passes;
 }
@@ -984,6 +988,7 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     c.cell_occ = h->cfg.cell_occupancy > 0.0 ? h->cfg.cell_occupancy : 1.0;
     c.canon = h->cfg.precision == RCP_FP64 ? 1u : 0u;
     c.long_row = RCP_LONG_ROW;
+    c.long64 = (c.canon && N > RCP_WARP_ROW_MAX_N) ? 1 : 0;
     {
         // blocks serving long rows: about one per 1536 spheres, at least 2
         long long lb = N / RCP_LONG_DIV;
@@ -1020,10 +1025,10 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         } else {
             CKS(dalloc(h, &h->m64, 3 * n));
             CKS(dalloc(h, &h->v64, 3 * n));
-            if (N <= RCP_WARP_ROW_MAX_N) {
-                CKS(dalloc(h, &h->row_e, n));
-                CKS(dalloc(h, &h->row_k, n));
-            }
+            // e_i, k_i of the rows a warp evaluates: every row of a small
+            // packing, the long rows of a large one
+            CKS(dalloc(h, &h->row_e, n));
+            CKS(dalloc(h, &h->row_k, n));
             CK(cudaMemsetAsync(h->m64, 0, sizeof(double) * 3 * n, h->stream));
             CK(cudaMemsetAsync(h->v64, 0, sizeof(double) * 3 * n, h->stream));
         }
@@ -1758,6 +1763,7 @@ PackDev pack_of(rcp_ctx* h)
     memset(&q, 0, sizeof(q));
     q.ctl = h->ctl;
     q.c = h->c;
+    q.c.long64 = 0;   // the batched binary64 kernel walks every row itself
     q.xA = h->xA;
     q.xB = h->xB;
     q.xb = h->xb;

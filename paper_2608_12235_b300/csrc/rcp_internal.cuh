@@ -108,7 +108,8 @@ struct RcpConst {
     float qmargin;             // 2 max_a qscale[a]: absolute margin of the mixed pre-test
     unsigned int canon;        // 1: binary64 path (canonical sums); 0: mixed path
     int dim;                   // the caller's dimension: 3, or 2 (disks held in the plane z = L_z / 2)
-    unsigned int long_row;     // rows longer than this get a warp (mixed)
+    unsigned int long_row;     // rows longer than this get a warp (mixed; binary64 when long64)
+    int long64;                // binary64 packing above RCP_WARP_ROW_MAX_N: long rows by k_pair64_long
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
     long long nfrozen;         // frozen spheres (binary64 path only; 0 otherwise)
     int walls;                 // bit a: flat walls at 0 and L_a bound axis a (binary64 path only)
@@ -261,7 +262,11 @@ __global__ void k_perm3(long long N, RcpConst c, const unsigned int* perm, const
                         int to_caller);
 __global__ void k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
-                         double* part_e, double* part_k, int mode, double* g_out);
+                         double* part_e, double* part_k, int mode, double* g_out, const double* row_e,
+                         const double* row_k);
+__global__ void k_pair64_long(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+                              const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
+                              const double4_32a* xb, double* row_e, double* row_k, int mode, double* g_out);
 __global__ void k_kappa_step(RcpCtl* ctl, RcpConst c, const double* part_e, const double* part_k,
                              long long nb, int mode);
 __device__ void kappa_close(RcpCtl* ctl, const RcpConst& c, double se, double sk, int mode);

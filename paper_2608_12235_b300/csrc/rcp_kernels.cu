@@ -478,7 +478,8 @@ __device__ __forceinline__ bool skin_exhausted(RcpCtl* ctl, double kappa_new)
 __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, double4_32a* xA, double4_32a* xB,
                                             double* m, double* v, const unsigned int* rowptr, const unsigned int* col,
                                             const double4_32a* xb, double* part_e, double* part_k, int mode,
-                                            double* g_out, unsigned int blk)
+                                            double* g_out, unsigned int blk, const double* row_e = nullptr,
+                                            const double* row_k = nullptr)
 {
     __shared__ double sh[RCP_PAIR_THREADS / 32];
     if (ctl->halted) return;
@@ -489,7 +490,11 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
     const long long i = (long long)blk * RCP_PAIR_THREADS + threadIdx.x;
     double e = 0.0, k = 0.0, md = 0.0;
     float bud = INFINITY;
-    if (i < c.N) {
+    if (i < c.N && c.long64 && rowptr[i + 1] - rowptr[i] > c.long_row) {
+        // a long row: k_pair64_long evaluated it (and took its Adam step)
+        e = row_e[i];
+        k = row_k[i];
+    } else if (i < c.N) {
         const double4_32a xi = xin[i];
         double g0 = 0.0, g1 = 0.0, g2 = 0.0;
         const unsigned int t1 = rowptr[i + 1];
@@ -558,9 +563,9 @@ __device__ __forceinline__ void pair64_body(RcpCtl* ctl, const RcpConst& c, doub
 __global__ void __launch_bounds__(RCP_PAIR_THREADS)
 k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
          const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb,
-         double* part_e, double* part_k, int mode, double* g_out)
+         double* part_e, double* part_k, int mode, double* g_out, const double* row_e, const double* row_k)
 {
-    pair64_body(ctl, c, xA, xB, m, v, rowptr, col, xb, part_e, part_k, mode, g_out, blockIdx.x);
+    pair64_body(ctl, c, xA, xB, m, v, rowptr, col, xb, part_e, part_k, mode, g_out, blockIdx.x, row_e, row_k);
 }
 
 // Binary64 pair kernel for small N: one warp per row.  With a thread per
@@ -571,23 +576,20 @@ k_pair64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, d
 // left folds as pair64_body, so the sums are bit-identical -- then the wall
 // terms.  e_i and k_i go to row_e/row_k[i] for the canonical tree over the
 // rows; lanes 0-2 take the Adam step of one coordinate each.
-__global__ void __launch_bounds__(RCP_WARP_ROW_THREADS)
-k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
-              const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb, double* row_e,
-              double* row_k, int mode, double* g_out)
+// One row of the binary64 pair kernel by a whole warp: the lanes compute the
+// terms of up to 32 partners at once, lane 0's order folds them (the row's
+// order: the same products and the same left folds as pair64_body, so the
+// sums are bit-identical), then the wall terms; e_i and k_i go to
+// row_e/row_k[i]; lanes 0-2 take the Adam step of one coordinate each.
+__device__ __forceinline__ void warp_row64(RcpCtl* ctl, const RcpConst& c, const double4_32a* __restrict__ xin,
+                                           double4_32a* __restrict__ xout, double* m, double* v,
+                                           const unsigned int* rowptr, const unsigned int* col,
+                                           const double4_32a* xb, double* row_e, double* row_k, int mode,
+                                           double* g_out, long long i, int lane, double kappa, double& md,
+                                           float& bud)
 {
-    __shared__ double sh[RCP_WARP_ROW_THREADS / 32];
-    if (ctl->halted) return;
     const unsigned int FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int parity = ctl->parity;
-    const double4_32a* __restrict__ xin = parity ? xB : xA;
-    double4_32a* __restrict__ xout = parity ? xA : xB;
-    const double kappa = ctl->kappa;
-    const long long i = ((long long)blockIdx.x * RCP_WARP_ROW_THREADS + threadIdx.x) >> 5;   // warp-uniform
-    double md = 0.0;
-    float bud = INFINITY;
-    if (i < c.N) {
+    {
         const double4_32a xi = xin[i];
         double g0 = 0.0, g1 = 0.0, g2 = 0.0, e = 0.0, k = 0.0;   // the fold, the same in every lane
         const unsigned int t0 = rowptr[i], t1 = rowptr[i + 1];
@@ -679,6 +681,54 @@ k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double*
             g_out[3 * i + 2] = g2;
         }
     }
+}
+
+__global__ void __launch_bounds__(RCP_WARP_ROW_THREADS)
+k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+              const unsigned int* rowptr, const unsigned int* col, const double4_32a* xb, double* row_e,
+              double* row_k, int mode, double* g_out)
+{
+    __shared__ double sh[RCP_WARP_ROW_THREADS / 32];
+    if (ctl->halted) return;
+    const int lane = threadIdx.x & 31;
+    const int parity = ctl->parity;
+    const double4_32a* __restrict__ xin = parity ? xB : xA;
+    double4_32a* __restrict__ xout = parity ? xA : xB;
+    const long long i = ((long long)blockIdx.x * RCP_WARP_ROW_THREADS + threadIdx.x) >> 5;   // warp-uniform
+    double md = 0.0;
+    float bud = INFINITY;
+    if (i < c.N)
+        warp_row64(ctl, c, xin, xout, m, v, rowptr, col, xb, row_e, row_k, mode, g_out, i, lane, ctl->kappa, md,
+                   bud);
+    if (mode == RCP_MODE_ADAM) push_budget(ctl, bud);
+    const double bm = block_max(md, sh);
+    if (threadIdx.x == 0 && bm > 0.0) atomicMax(&ctl->maxdelta_bits, dbits(bm));
+}
+
+// The rows longer than c.long_row of a large binary64 packing, a warp each
+// (launched before k_pair64, which then takes their e_i, k_i from row_e /
+// row_k for its block trees): with one thread per row, the few rows of the
+// largest spheres (thousands of entries at S = 5e5) would run on long after
+// every other row has finished.
+__global__ void __launch_bounds__(RCP_PAIR_THREADS)
+k_pair64_long(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
+              const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
+              const double4_32a* xb, double* row_e, double* row_k, int mode, double* g_out)
+{
+    __shared__ double sh[RCP_PAIR_THREADS / 32];
+    if (ctl->halted) return;
+    const int lane = threadIdx.x & 31;
+    const int parity = ctl->parity;
+    const double4_32a* __restrict__ xin = parity ? xB : xA;
+    double4_32a* __restrict__ xout = parity ? xA : xB;
+    const double kappa = ctl->kappa;
+    const unsigned int nlong = ctl->n_long;
+    const unsigned int nw = gridDim.x * (RCP_PAIR_THREADS / 32);
+    double md = 0.0;
+    float bud = INFINITY;
+    for (unsigned int r = blockIdx.x * (RCP_PAIR_THREADS / 32) + (threadIdx.x >> 5); r < nlong; r += nw)
+        warp_row64(ctl, c, xin, xout, m, v, rowptr, col, xb, row_e, row_k, mode, g_out, (long long)long_rows[r],
+                   lane, kappa, md, bud);
     if (mode == RCP_MODE_ADAM) push_budget(ctl, bud);
     const double bm = block_max(md, sh);
     if (threadIdx.x == 0 && bm > 0.0) atomicMax(&ctl->maxdelta_bits, dbits(bm));
