@@ -413,7 +413,9 @@ def profile_window(args, w):
     elif args.profile_window == "build":
         rcp.rcp_build_neighbors(p.h)
     else:
-        p.run(max_iters=100, shrink=False)
+        # 100 iterations launched one by one (with their rebuilds): a profiler
+        # does not list the kernels inside the replayed graph's device loop
+        rcp.rcp_profile(p.h, 100)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     print(f"window done: iters={r.iters} listed entries={listed}")
@@ -477,8 +479,8 @@ def main():
     ap.add_argument("--profile-window", choices=["pair", "build", "iters"], default=None,
                     help="densify the workload (mixed) outside the profiled range, then bracket with "
                          "cudaProfilerStart/Stop two iterations launched one by one (pair), one neighbour "
-                         "rebuild (build) or 100 graph-driven iterations (iters), for ncu --profile-from-start "
-                         "off; prints no benchmark line")
+                         "rebuild (build) or 100 iterations launched one by one with their rebuilds (iters), "
+                         "for ncu --profile-from-start off; prints no benchmark line")
     ap.add_argument("--phi-parity", default="",
                     help="comma-separated workloads: mixed beside binary64 runs to the stop; one JSON line")
     ap.add_argument("--phi-seeds", default="0,1,2,3,4")

@@ -305,16 +305,12 @@ __device__ __forceinline__ float row_epilogue(RcpCtl* ctl, const RcpConst& c, co
     return INFINITY;
 }
 
-__device__ __forceinline__ float warp_sum2f(float s, float c)
+__device__ __forceinline__ float warp_sum(float s)
 {
-    for (int o = 16; o > 0; o >>= 1) {
-        const float so = __shfl_xor_sync(0xffffffffu, s, o);
-        const float co = __shfl_xor_sync(0xffffffffu, c, o);
-        acc2(s, c, so);
-        c = c + co;
-    }
-    return s + c;
+    for (int o = 16; o > 0; o >>= 1) s = s + __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
+
 
 // The pair kernel of the mixed path.  Listed entries far outnumber
 // overlapping pairs (about 3 % in the dense packings at S = 5e5, where most
@@ -404,9 +400,12 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                     } while (hit);
                 }
             }
-            g0 = warp_sum2f(g0, c0);
-            g1 = warp_sum2f(g1, c1);
-            g2 = warp_sum2f(g2, c2);
+            // lanes' compensated sums, then a plain tree over the lanes: each
+            // lane's s + c is its terms' sum to ~2^-24, the tree adds five
+            // roundings of the lane sums' magnitude
+            g0 = warp_sum(g0 + c0);
+            g1 = warp_sum(g1 + c1);
+            g2 = warp_sum(g2 + c2);
             if (lane == 0) bud = fminf(bud, row_epilogue(ctl, c, S, i, rin[i], g0, g1, g2, m, v, rout, rb, mode, g_out));
         }
     } else {
