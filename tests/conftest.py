@@ -79,6 +79,38 @@ def grad_check():
     return assert_grad_close
 
 
+def assert_sums_close(E, oE, dk, odk, mu, kappa, D0, rel=1e-6, what=""):
+    """E and dE/dkappa of the mixed path against the oracle's.
+
+    Eq. energy makes E the sum of the pair energies less mu kappa sum D_i^0,
+    and dE/dkappa the sum of the pairs' kappa terms less mu sum D_i^0: each is
+    the difference of two sums that nearly cancel where mu balances the
+    overlaps (E can be 1 % of either sum).  The mixed path forms every pair's
+    energy and kappa term in binary32 from exactly represented displacements
+    (the overlap within a few roundings of 2^-24, its square within ~8e-7 of
+    itself), adds them with compensated sums, and takes the mu terms in
+    binary64, so its error is bounded relative to the magnitudes of the two
+    sums, not to their difference:
+
+      |E - oE|   <= rel (Se + mu kappa sum D0),  Se = oE + mu kappa sum D0,
+      |dk - odk| <= rel (|Sk| + mu sum D0),      Sk = odk + mu sum D0,
+
+    with Se and Sk from the oracle's binary64 values."""
+    SD = float(np.sum(np.asarray(D0, dtype=np.float64)))
+    muE, muK = mu * kappa * SD, mu * SD
+    bE = rel * (abs(oE + muE) + muE)
+    bK = rel * (abs(odk + muK) + muK)
+    if not (abs(E - oE) <= bE and abs(dk - odk) <= bK):
+        raise AssertionError(f"{what} E {E!r} vs {oE!r} (bound {bE:.3e}), dE/dkappa {dk!r} vs {odk!r} "
+                             f"(bound {bK:.3e})")
+    return max(abs(E - oE) / bE if bE > 0 else 0.0, abs(dk - odk) / bK if bK > 0 else 0.0)
+
+
+@pytest.fixture(scope="session")
+def sums_check():
+    return assert_sums_close
+
+
 @pytest.fixture(scope="session")
 def term_scale(orc):
     return lambda *a, **k: row_term_scale(orc, *a, **k)

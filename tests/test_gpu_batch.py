@@ -56,7 +56,7 @@ def test_batch_runs_every_packing_to_its_stop(rcp):
         p.close()
 
 
-def test_batch_autotune_mixed(rcp, orc, term_scale, grad_check):
+def test_batch_autotune_mixed(rcp, orc, term_scale, grad_check, sums_check):
     """The autotuned batch runs, and each packing's evaluation under the
     tuned long-row threshold still matches the oracle (a threshold beyond
     what the short-row path can mark would drop overlaps silently)."""
@@ -72,6 +72,6 @@ def test_batch_autotune_mixed(rcp, orc, term_scale, grad_check):
         x, _, _, s = p.state()
         E, g, dk, md = p.energy_grad(0.01)
         oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, s.kappa, 0.01)
-        assert abs(E - oE) <= 1e-5 * abs(oE) and abs(dk - odk) <= 1e-5 * abs(odk)
+        sums_check(E, oE, dk, odk, 0.01, s.kappa, D0, what=f"tuned long_row {lr}")
         grad_check(g, og, term_scale(x, D0, 1.0, s.kappa), what=f"tuned long_row {lr}")
         p.close()

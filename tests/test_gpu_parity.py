@@ -258,15 +258,14 @@ def test_chunk_size_does_not_change_the_trajectory(rcp):
 
 
 # ------------------------------------------------------------------ mixed precision
-def test_energy_grad_mixed_within_tolerance(rcp, orc, term_scale, grad_check):
+def test_energy_grad_mixed_within_tolerance(rcp, orc, term_scale, grad_check, sums_check):
     for D0, x, k in _states(orc):
         p = _mk(rcp, D0, precision=rcp.RCP_MIXED)
         p.set_positions(x, k)
         mu = 0.013
         E, g, dk, md = p.energy_grad(mu)
         oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, mu)
-        assert abs(E - oE) <= 1e-5 * abs(oE)
-        assert abs(dk - odk) <= 1e-5 * abs(odk)
+        sums_check(E, oE, dk, odk, mu, k, D0, what="mixed")
         assert abs(md - omd) <= 1e-5 * omd
         w = grad_check(g, og, term_scale(x, D0, 1.0, k), what="mixed")
         print(f"N={D0.size} worst gradient error / bound {w:.3g}")
@@ -307,7 +306,7 @@ def test_mixed_state_follows_the_caller_order(rcp, orc):
     p.close()
 
 
-def test_energy_grad_mixed_near_contact(rcp, orc, term_scale, grad_check):
+def test_energy_grad_mixed_near_contact(rcp, orc, term_scale, grad_check, sums_check):
     """Small overlaps (delta ~ 1e-3, a relaxed packing inflated by 0.2 %): the
     regime where a plain binary32 d - r would cancel."""
     D0 = inputs.lognormal(400, 0.5, 10.0)
@@ -322,8 +321,7 @@ def test_energy_grad_mixed_near_contact(rcp, orc, term_scale, grad_check):
         assert 5e-4 < omd < 5e-3
         print(f"mu={mu} relE={abs(E - oE) / abs(oE):.2e} reldk={abs(dk - odk) / abs(odk):.2e} "
               f"relg={np.linalg.norm(g - og) / np.linalg.norm(og):.2e} relmd={abs(md - omd) / omd:.2e}")
-        assert abs(E - oE) <= 1e-5 * abs(oE)
-        assert abs(dk - odk) <= 1e-5 * abs(odk)
+        sums_check(E, oE, dk, odk, mu, k, D0, what="mixed near contact")
         assert abs(md - omd) <= 1e-5 * omd
         w = grad_check(g, og, term_scale(x, D0, 1.0, k), what="mixed near contact")
         print(f"worst gradient error / bound {w:.3g}")
@@ -397,7 +395,7 @@ def test_two_dimensional_initial_state_and_kappa0_bitexact(rcp, orc):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_two_dimensional_list_and_energy(rcp, orc, precision, term_scale, grad_check):
+def test_two_dimensional_list_and_energy(rcp, orc, precision, term_scale, grad_check, sums_check):
     n = 1200
     D0 = inputs.lognormal(n, 1.0, 30.0)
     prec = rcp.RCP_FP64 if precision == "fp64" else rcp.RCP_MIXED
@@ -415,7 +413,7 @@ def test_two_dimensional_list_and_energy(rcp, orc, precision, term_scale, grad_c
     if precision == "fp64":
         assert E == oE and dk == odk and md == omd and np.array_equal(g, og)
     else:
-        assert abs(E - oE) <= 1e-5 * abs(oE) and abs(dk - odk) <= 1e-5 * abs(odk)
+        sums_check(E, oE, dk, odk, 0.01, k, D0, what="mixed d = 2")
         assert abs(md - omd) <= 1e-5 * omd
         grad_check(g, og, term_scale(x, D0, 1.0, k, d=2), what="mixed d = 2")
     p.close()
