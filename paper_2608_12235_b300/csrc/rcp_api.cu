@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -96,6 +97,7 @@ struct rcp_ctx {
     unsigned int* col = nullptr;
     unsigned int* rowptr = nullptr;  // [N+1]
     unsigned int* long_rows = nullptr;  // [N] rows longer than RCP_LONG_ROW
+    uint2* sheavy = nullptr;            // [N] search windows queued for a warp each (sphere, class)
     unsigned long long pcap = 0;
     unsigned int* hist = nullptr;
     unsigned long long hist_cap = 0;
@@ -448,10 +450,17 @@ rcp_status search_once(rcp_ctx* h)
         CKL();
         return RCP_OK;
     }
-    CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long), h->stream));
-    h->launches += 1;
+    // the entry cursor and the queue of heavy windows (adjacent in RcpCtl)
+    static_assert(offsetof(RcpCtl, search_heavy) == offsetof(RcpCtl, pair_cursor) + sizeof(unsigned long long),
+                  "pair_cursor and search_heavy are cleared together");
+    CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long) + sizeof(unsigned int), h->stream));
+    const unsigned int hcap = (unsigned int)N;
+    h->launches += 2;
     k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xsf,
-                                         h->cells, h->pairs1, h->pcap, nbits);
+                                         h->cells, h->pairs1, h->pcap, nbits, h->sheavy, hcap);
+    k_search_heavy<<<std::min(nbN, 8u * 148u), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl,
+                                                                     h->idx_sorted, h->xsf, h->cells, h->pairs1,
+                                                                     h->pcap, nbits, h->sheavy, hcap);
     CKL();
     CK(cudaMemcpyAsync(&h->ctl_h->pair_cursor, &h->ctl->pair_cursor, sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, h->stream));
@@ -797,7 +806,7 @@ rcp_status rcp_destroy(rcp_handle h)
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
                     h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->cells, h->cnt,
-                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->hist, h->scan_tmp, h->perm, h->perm_alt, h->D0_alt, h->rho_alt,
+                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->sheavy, h->hist, h->scan_tmp, h->perm, h->perm_alt, h->D0_alt, h->rho_alt,
                     h->lvl_alt, h->row_e, h->row_k};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1057,6 +1066,7 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         CKS(dalloc(h, &h->offs, n + 1));
         CKS(dalloc(h, &h->rowptr, n + 1));
         CKS(dalloc(h, &h->long_rows, n));
+        CKS(dalloc(h, &h->sheavy, n));
         CKS(ensure_pair_capacity(h, 16 * (unsigned long long)n));
         CK(cudaFuncSetAttribute(k_kappa_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8192 * 8));
         CKS(ensure_scan_tmp(h, n + 1));

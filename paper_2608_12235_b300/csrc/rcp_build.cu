@@ -11,9 +11,9 @@
 // within its radius).  Particles are sorted by the 62-bit key (class, cz, cy,
 // cx) with a hand-written LSD radix sort, and a dense per-class cell table
 // holds each cell's range [start, end) in that order.  A sphere scans its
-// own class and every coarser class over the cells within its search radius;
+// own class and every finer class over the cells within its search radius;
 // a pair inside one class is found from both ends, a pair across classes
-// from the finer end only, which emits both directions.  The pairs (row << b
+// from the coarser end only, which emits both directions.  The pairs (row << b
 // | col) become CSR rows with ascending columns (per-row counts, a scatter
 // into the rows, a shared-memory sort of each row).  Integer and
 // exact-predicate work only: the list is bit-identical to the definition.
@@ -371,28 +371,76 @@ __global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys,
 
 // ---------------------------------------------------------------------------
 // Pair search, one pass.  Threads take the spheres in cell-key order.  Each
-// thread keeps the entries it finds in a small
-// local buffer; a full buffer is flushed to the global array through one
-// atomic reservation, and the final flush is aggregated over the warp.  The
-// order of entries in the array is arbitrary (they are radix-sorted next);
-// entries beyond `cap` are counted but not written, and the host re-runs the
-// search with a larger array.  The inclusion test is the exact binary64
-// predicate  dx^2 + dy^2 + dz^2 < (rho_i + rho_j)^2  (minimum image).
+// thread keeps the entries it finds in a small local buffer; a full buffer is
+// flushed to the global array through one atomic reservation, and the final
+// flush is aggregated over the warp.  The order of entries in the array is
+// arbitrary (the CSR pass orders them); entries beyond `cap` are counted but
+// not written, and the host re-runs the search with a larger array.  The
+// inclusion test is the exact binary64 predicate
+// dx^2 + dy^2 + dz^2 < (rho_i + rho_j)^2  (minimum image).
 #define RCP_SEARCH_BUF 32
+// a window of at least this many cells goes to k_search_heavy, in chunks of
+// RCP_SEARCH_CHUNK cells, one warp each
+#ifndef RCP_SEARCH_HEAVY
+#define RCP_SEARCH_HEAVY 32
+#endif
+#define RCP_SEARCH_CHUNK 64
 
-__device__ __forceinline__ void flush_entries(unsigned long long* pairs, unsigned long long cap,
-                                              unsigned long long base, const unsigned long long* buf, int n)
+// Minimum-image component in box units (d = u_i - u_j in (-1, 1)): d minus
+// its nearest integer, exact (d - 1 for d in [1/2, 1) is exact by Sterbenz's
+// lemma), and +-1/2 stay as they are (round half to even gives 0 there).
+__device__ __forceinline__ float wrap_unit(float d) { return d - rintf(d); }
+
+// The class-k cells within reach of a sphere at ui (box units, radius ui.w):
+// per axis the first cell (before the periodic wrap), the count and the grid.
+struct SearchWin {
+    int lo[3];
+    unsigned int nc[3], ng[3];
+};
+
+__device__ __forceinline__ SearchWin search_window(const RcpCtl* ctl, const RcpConst& c, const float4& ui, int k)
 {
-    for (int q = 0; q < n; ++q)
-        if (base + q < cap) pairs[base + q] = buf[q];
+    SearchWin w;
+    const float rk = ctl->rho_lvl_f[k];
+    const float u3[3] = {ui.x, ui.y, ui.z};
+    for (int a = 0; a < 3; ++a) {
+        w.ng[a] = (unsigned int)ctl->ng[k][a];
+        // search radius in box units, in binary32: rho_i, rho_k and 1/L_a are
+        // each within 2^-24 of their binary64 values and the sum and product
+        // round twice more, a few 1e-7 in all, far inside the 1e-6 relative
+        // margin; 2e-6 covers the rounding of u (a window only has to be wide
+        // enough)
+        const float Ru = __fmaf_rn((ui.w + rk) * c.invLf[a], 1.000001f, 2e-6f);
+        const float fn = (float)w.ng[a];
+        int l = (int)floorf((u3[a] - Ru) * fn);
+        int h = (int)floorf((u3[a] + Ru) * fn);
+        if ((c.bounded >> a) & 1) {
+            // bounded axis, no wrap: clamp the window (the edge cells also
+            // hold the spheres beyond the walls)
+            const int top = (int)w.ng[a] - 1;
+            l = l < 0 ? 0 : (l > top ? top : l);
+            h = h < 0 ? 0 : (h > top ? top : h);
+            w.lo[a] = l;
+            w.nc[a] = (unsigned int)(h - l + 1);
+        } else if (h - l + 1 >= (int)w.ng[a]) {
+            w.lo[a] = 0;
+            w.nc[a] = w.ng[a];
+        } else {
+            w.lo[a] = l;
+            w.nc[a] = (unsigned int)(h - l + 1);
+        }
+    }
+    return w;
 }
 
-// Minimum-image component in box units (u in [0, 1]): the wrap is exact.
-__device__ __forceinline__ float wrap_unit(float d)
+// Range [start, end) of the window's cell (cx, cy, cz) in the class-k table.
+__device__ __forceinline__ uint2 window_cell(const uint2* ck, const SearchWin& w, unsigned int cx, unsigned int cy,
+                                             unsigned int cz)
 {
-    if (d > 0.5f) d = d - 1.0f;
-    else if (d < -0.5f) d = d + 1.0f;
-    return d;
+    const unsigned int z = (unsigned int)(w.lo[2] + (int)cz) & (w.ng[2] - 1);
+    const unsigned int y = (unsigned int)(w.lo[1] + (int)cy) & (w.ng[1] - 1);
+    const unsigned int x = (unsigned int)(w.lo[0] + (int)cx) & (w.ng[0] - 1);
+    return ck[((unsigned long long)z * w.ng[1] + y) * w.ng[0] + x];
 }
 
 // Binary32 prefilter with rigorous bounds.  With u = fl32(x/L) (error <=
@@ -403,181 +451,286 @@ __device__ __forceinline__ float wrap_unit(float d)
 // margins on top; pairs inside the band where those bounds cannot decide are
 // settled by the exact binary64 predicate, so the listed set is exactly the
 // binary64 one.
-// PLACE: the same walk for the placement rounds; an overlapping pair marks
-// the candidate that must give way (D0, placed and reject are used only then).
-template <bool PLACE>
-__device__ __forceinline__ void search_body(RcpCtl* ctl, const RcpConst& c, const double4_32a* xA,
-                                            const double4_32a* xB, const double* rho, const int* lvl,
-                                            const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
-                                            unsigned long long* pairs, unsigned long long cap, int nbits,
-                                            const double* D0, const unsigned char* placed, unsigned char* reject,
-                                            int kcur)
+// Candidate t (a sorted position) against sphere i: its index j when the
+// pair is listed (j != i), else 0xffffffff.
+__device__ __forceinline__ unsigned int listed_partner(const RcpConst& c, float Eabs, const double4_32a* x,
+                                                       const double* rho, const unsigned int* idx_sorted,
+                                                       const float4* xsf, unsigned int t, long long i,
+                                                       const float4& ui, double ri)
 {
-    // threads take the spheres in cell-key order (size class, then cell), so
-    // a warp shares its size class, its trip counts and most of its cells;
-    // idx_sorted is NULL when the state itself is in that order
-    const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long buf[RCP_SEARCH_BUF];
-    int nb = 0;
-    long long i0 = -1;
-    if (ts < c.N) {
-        i0 = idx_sorted ? (long long)idx_sorted[ts] : ts;
-        // placement: only the candidates of the current class search (every
-        // overlap with a placed sphere or a class-mate is found from their side)
-        if (PLACE && (placed[i0] || lvl[i0] != kcur)) i0 = -1;
-    }
-    if (i0 >= 0) {
-        const long long i = i0;
-        const double4_32a* x = ctl->parity ? xB : xA;
-        const float4 ui = xsf[ts];
-        const double ri = rho[i];
-        const int li = lvl[i];
-        const float L0 = c.Lf[0], L1 = c.Lf[1], L2 = c.Lf[2];
-        const float Eabs = (float)(5e-7 * c.Lmax);
-        const float up = 1.0f + 2e-6f, dn = 1.0f - 2e-6f;
-        const float u3[3] = {ui.x, ui.y, ui.z};
-        // a placement candidate also meets frozen spheres of finer classes,
-        // which are placed before any class is
-        const int kend = (PLACE && c.nfrozen > 0) ? ctl->nlev - 1 : li;
-        if (PLACE && (c.walls | c.container)) {   // a candidate must keep off the walls too (distance below rho_i)
-            const double4_32a xi = x[i];
-            for (int a = 0; a < 3; ++a) {
-                if (!((c.walls >> a) & 1)) continue;
-                const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
-                if (xa < ri || c.L[a] - xa < ri) reject[i] = 1;
-            }
-            if (c.container) {   // distance to the curved wall R - |x - c| over its axes
-                double s2 = 0.0;
-                for (int a = 0; a < 3; ++a) {
-                    if (!((c.caxes >> a) & 1)) continue;
-                    const double o = (a == 0 ? xi.x : (a == 1 ? xi.y : xi.z)) - c.halfL[a];
-                    s2 = s2 + o * o;
-                }
-                if (c.Rc - sqrt(s2) < ri) reject[i] = 1;
-            }
-        }
-        for (int k = 0; k <= kend; ++k) {
-            const float rk = ctl->rho_lvl_f[k];
-            if (!(rk > 0.0f)) continue;
-            int lo[3];
-            unsigned int nc[3], ng[3];
-            for (int a = 0; a < 3; ++a) {
-                ng[a] = (unsigned int)ctl->ng[k][a];
-                // search radius in box units, in binary32: rho_i, rho_k and
-                // 1/L_a are each within 2^-24 of their binary64 values and the
-                // sum and product round twice more, a few 1e-7 in all, far
-                // inside the 1e-6 relative margin; 2e-6 covers the rounding of
-                // u (a window only has to be wide enough)
-                const float Ru = __fmaf_rn((ui.w + rk) * c.invLf[a], 1.000001f, 2e-6f);
-                const float fn = (float)ng[a];
-                int l = (int)floorf((u3[a] - Ru) * fn);
-                int h = (int)floorf((u3[a] + Ru) * fn);
-                if ((c.bounded >> a) & 1) {
-                    // bounded axis, no wrap: clamp the window (the edge cells
-                    // also hold the spheres beyond the walls)
-                    const int top = (int)ng[a] - 1;
-                    l = l < 0 ? 0 : (l > top ? top : l);
-                    h = h < 0 ? 0 : (h > top ? top : h);
-                    lo[a] = l;
-                    nc[a] = (unsigned int)(h - l + 1);
-                } else if (h - l + 1 >= (int)ng[a]) {
-                    lo[a] = 0;
-                    nc[a] = ng[a];
-                } else {
-                    lo[a] = l;
-                    nc[a] = (unsigned int)(h - l + 1);
-                }
-            }
-            const uint2* ck = cells + ctl->cell_off[k];
-            for (unsigned int cz = 0; cz < nc[2]; ++cz) {
-                const unsigned int z = (unsigned int)(lo[2] + (int)cz) & (ng[2] - 1);
-                for (unsigned int cy = 0; cy < nc[1]; ++cy) {
-                    const unsigned int y = (unsigned int)(lo[1] + (int)cy) & (ng[1] - 1);
-                    const uint2* row = ck + ((unsigned long long)z * ng[1] + y) * ng[0];
-                    for (unsigned int cx = 0; cx < nc[0]; ++cx) {
-                        const unsigned int xx = (unsigned int)(lo[0] + (int)cx) & (ng[0] - 1);
-                        const uint2 range = row[xx];
-                        for (unsigned int t = range.x; t < range.y; ++t) {
-                            const float4 uj = xsf[t];
-                            const float dx = ((c.bounded & 1) ? ui.x - uj.x : wrap_unit(ui.x - uj.x)) * L0;
-                            const float dy = ((c.bounded & 2) ? ui.y - uj.y : wrap_unit(ui.y - uj.y)) * L1;
-                            const float dz = ((c.bounded & 4) ? ui.z - uj.z : wrap_unit(ui.z - uj.z)) * L2;
-                            const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
-                            const float cut = ui.w + uj.w;
-                            const float hi = (cut * up + Eabs) * up;
-                            if (r2 > hi * hi) continue;                    // certainly not listed
-                            const unsigned int j = idx_sorted ? idx_sorted[t] : t;
-                            if ((long long)j == i) continue;
-                            const float lo_in = (cut * dn - Eabs) * dn;
-                            bool in = lo_in > 0.0f && r2 < lo_in * lo_in;   // certainly listed
-                            if (!in) {
-                                // the band: exact binary64 predicate
-                                const double4_32a xi = x[i], xj = x[j];
-                                double ex = (c.bounded & 1) ? xi.x - xj.x : min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
-                                double ey = (c.bounded & 2) ? xi.y - xj.y : min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
-                                double ez = (c.bounded & 4) ? xi.z - xj.z : min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
-                                double d2 = ex * ex + ey * ey + ez * ez;
-                                double cc = ri + rho[j];
-                                in = d2 < cc * cc;
-                            }
-                            if (!in) continue;
-                            if (PLACE) {
-                                // i is a candidate of class kcur; it gives way to
-                                // a placed sphere and to a class-mate candidate
-                                // that precedes it (larger D0, then lower index);
-                                // spheres of later classes are not there yet
-                                if (placed[j]) reject[i] = 1;
-                                else if (lvl[j] == kcur) {
-                                    const bool j_first = D0[j] > D0[i] || (D0[j] == D0[i] && (long long)j < i);
-                                    reject[j_first ? i : (long long)j] = 1;
-                                }
-                                continue;
-                            }
-                            const int need = (k < li) ? 2 : 1;
-                            if (nb + need > RCP_SEARCH_BUF) {
-                                const unsigned long long base = atomicAdd(&ctl->pair_cursor, (unsigned long long)nb);
-                                flush_entries(pairs, cap, base, buf, nb);
-                                nb = 0;
-                            }
-                            buf[nb++] = ((unsigned long long)i << nbits) | j;
-                            if (k < li) buf[nb++] = ((unsigned long long)j << nbits) | (unsigned long long)i;
-                        }
-                    }
-                }
-            }
-        }
-    }
-    if (PLACE) return;
-    // warp-aggregated final flush
-    const int lane = threadIdx.x & 31;
-    unsigned int incl = (unsigned int)nb;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && total) base = atomicAdd(&ctl->pair_cursor, (unsigned long long)total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    flush_entries(pairs, cap, base + (incl - (unsigned int)nb), buf, nb);
+    const float up = 1.0f + 2e-6f, dn = 1.0f - 2e-6f;
+    const float4 uj = xsf[t];
+    const float dx = ((c.bounded & 1) ? ui.x - uj.x : wrap_unit(ui.x - uj.x)) * c.Lf[0];
+    const float dy = ((c.bounded & 2) ? ui.y - uj.y : wrap_unit(ui.y - uj.y)) * c.Lf[1];
+    const float dz = ((c.bounded & 4) ? ui.z - uj.z : wrap_unit(ui.z - uj.z)) * c.Lf[2];
+    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+    const float cut = ui.w + uj.w;
+    const float hi = (cut * up + Eabs) * up;
+    if (r2 > hi * hi) return 0xffffffffu;            // certainly not listed
+    const unsigned int j = idx_sorted ? idx_sorted[t] : t;
+    if ((long long)j == i) return 0xffffffffu;
+    const float lo_in = (cut * dn - Eabs) * dn;
+    if (lo_in > 0.0f && r2 < lo_in * lo_in) return j;  // certainly listed
+    // the band: exact binary64 predicate
+    const double4_32a xi = x[i], xj = x[j];
+    const double ex = (c.bounded & 1) ? xi.x - xj.x : min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
+    const double ey = (c.bounded & 2) ? xi.y - xj.y : min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
+    const double ez = (c.bounded & 4) ? xi.z - xj.z : min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
+    const double d2 = ex * ex + ey * ey + ez * ez;
+    const double cc = ri + rho[j];
+    return d2 < cc * cc ? j : 0xffffffffu;
 }
 
+template <class F>
+__device__ __forceinline__ void scan_cell(const RcpConst& c, float Eabs, const double4_32a* x, const double* rho,
+                                          const unsigned int* idx_sorted, const float4* xsf, uint2 range,
+                                          long long i, const float4& ui, double ri, F&& hit)
+{
+    for (unsigned int t = range.x; t < range.y; ++t) {
+        const unsigned int j = listed_partner(c, Eabs, x, rho, idx_sorted, xsf, t, i, ui, ri);
+        if (j != 0xffffffffu) hit(j);
+    }
+}
+
+// A thread's buffer of list entries (row << nbits | col).
+struct EntryBuf {
+    unsigned long long b[RCP_SEARCH_BUF];
+    int n;
+
+    __device__ __forceinline__ void flush_to(unsigned long long* pairs, unsigned long long cap,
+                                             unsigned long long base) const
+    {
+        for (int q = 0; q < n; ++q)
+            if (base + q < cap) pairs[base + q] = b[q];
+    }
+    // the entry (i, j), and (j, i) too when `both`
+    __device__ __forceinline__ void put(RcpCtl* ctl, unsigned long long* pairs, unsigned long long cap, int nbits,
+                                        unsigned long long i, unsigned long long j, bool both)
+    {
+        if (n + (both ? 2 : 1) > RCP_SEARCH_BUF) {
+            flush_to(pairs, cap, atomicAdd(&ctl->pair_cursor, (unsigned long long)n));
+            n = 0;
+        }
+        b[n++] = (i << nbits) | j;
+        if (both) b[n++] = (j << nbits) | i;
+    }
+    // warp-aggregated final flush (every lane of the warp calls it)
+    __device__ __forceinline__ void flush_warp(RcpCtl* ctl, unsigned long long* pairs, unsigned long long cap)
+    {
+        const int lane = threadIdx.x & 31;
+        unsigned int incl = (unsigned int)n;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && total) base = atomicAdd(&ctl->pair_cursor, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        flush_to(pairs, cap, base + (incl - (unsigned int)n));
+        n = 0;
+    }
+};
+
+// The list search.  Sphere i of class l_i scans its own class and every
+// finer one (k >= l_i): a pair inside one class is found from both ends, a
+// pair across classes from the coarser end only, which emits both
+// directions.  Searching from the coarse end keeps the windows' cell slack
+// small: a window over the fine grid exceeds 2 (rho_i + rho_k) by one fine
+// cell per axis, whereas a fine sphere's window over a coarse grid exceeds it
+// by a coarse cell, which then holds many candidates that are out of reach.
+// A window of RCP_SEARCH_HEAVY cells or more (the largest spheres over the
+// finest grid) is queued for k_search_heavy, which gives it a warp; the rest
+// are scanned here, one thread per sphere.  Threads take the spheres in
+// cell-key order (size class, then cell), so a warp shares its size class,
+// its trip counts and most of its cells; idx_sorted is NULL when the state
+// itself is in that order.
 __global__ void __launch_bounds__(256)
 k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
          const unsigned int* idx_sorted, const float4* xsf, const uint2* cells, unsigned long long* pairs,
-         unsigned long long cap, int nbits)
+         unsigned long long cap, int nbits, uint2* heavy, unsigned int heavy_cap)
 {
-    search_body<false>(ctl, c, xA, xB, rho, lvl, idx_sorted, xsf, cells, pairs, cap, nbits, nullptr, nullptr,
-                       nullptr, 0);
+    const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = ts < c.N;
+    const float Eabs = (float)(5e-7 * c.Lmax);
+    const double4_32a* x = ctl->parity ? xB : xA;
+    long long i = 0;
+    float4 ui = make_float4(0.f, 0.f, 0.f, 0.f);
+    double ri = 0.0;
+    int li = RCP_KMAX;
+    if (act) {
+        i = idx_sorted ? (long long)idx_sorted[ts] : ts;
+        ui = xsf[ts];
+        ri = rho[i];
+        li = lvl[i];
+    }
+    EntryBuf eb;
+    eb.n = 0;
+    const int nlev = ctl->nlev;
+    for (int k = 0; k < nlev; ++k) {   // warp-uniform, so the flushes below see the whole warp
+        if (k >= li && ctl->rho_lvl_f[k] > 0.0f) {
+            const SearchWin w = search_window(ctl, c, ui, k);
+            const unsigned long long ncell = (unsigned long long)w.nc[0] * w.nc[1] * w.nc[2];
+            bool queued = false;
+            if (ncell >= RCP_SEARCH_HEAVY && ncell < (1ull << 31)) {
+                // one queue item (sphere, chunk << 5 | class) per chunk of cells
+                const unsigned int nch = (unsigned int)((ncell + RCP_SEARCH_CHUNK - 1) / RCP_SEARCH_CHUNK);
+                const unsigned int s = atomicAdd(&ctl->search_heavy, nch);
+                if ((unsigned long long)s + nch <= heavy_cap) {
+                    for (unsigned int h = 0; h < nch; ++h)
+                        heavy[s + h] = make_uint2((unsigned int)ts, (h << 5) | (unsigned int)k);
+                    queued = true;
+                } else {
+                    // queue full: the slots it was given are marked empty and
+                    // the window is scanned here
+                    for (unsigned long long h = s; h < heavy_cap && h < (unsigned long long)s + nch; ++h)
+                        heavy[h] = make_uint2(0xffffffffu, 0u);
+                }
+            }
+            if (!queued) {
+                const bool both = k > li;
+                const uint2* ck = cells + ctl->cell_off[k];
+                for (unsigned int cz = 0; cz < w.nc[2]; ++cz)
+                    for (unsigned int cy = 0; cy < w.nc[1]; ++cy)
+                        for (unsigned int cx = 0; cx < w.nc[0]; ++cx)
+                            scan_cell(c, Eabs, x, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
+                                      [&](unsigned int j) { eb.put(ctl, pairs, cap, nbits, i, j, both); });
+            }
+        }
+        // buffers past half full go out with one reservation for the warp
+        // (a lane that fills its buffer inside a window reserves alone)
+        if (__any_sync(0xffffffffu, eb.n > RCP_SEARCH_BUF / 2)) eb.flush_warp(ctl, pairs, cap);
+    }
+    eb.flush_warp(ctl, pairs, cap);
 }
 
+// The queued chunks of windows, one warp each.  Each round the lanes read
+// the ranges of 32 cells, a warp scan of their counts lays the candidates end
+// to end, and the lanes take the candidates 32 at a time (the owning cell by a
+// binary search over the scan), so the lanes stay busy whatever the cells
+// hold.  The grid strides over the queue, whose length the device holds.
+__global__ void __launch_bounds__(256)
+k_search_heavy(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
+               const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
+               unsigned long long* pairs, unsigned long long cap, int nbits, const uint2* heavy,
+               unsigned int heavy_cap)
+{
+    const unsigned int FULL = 0xffffffffu;
+    const unsigned int lane = threadIdx.x & 31;
+    const unsigned int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned int nw = (gridDim.x * blockDim.x) >> 5;
+    const unsigned int nq = min(ctl->search_heavy, heavy_cap);
+    const double4_32a* x = ctl->parity ? xB : xA;
+    const float Eabs = (float)(5e-7 * c.Lmax);
+    EntryBuf eb;
+    eb.n = 0;
+    for (unsigned int q = w0; q < nq; q += nw) {   // warp-uniform
+        const uint2 item = heavy[q];
+        if (item.x == 0xffffffffu) continue;        // a slot of a window scanned in place
+        const long long ts = item.x;
+        const int k = (int)(item.y & 31u);
+        const long long i = idx_sorted ? (long long)idx_sorted[ts] : ts;
+        const float4 ui = xsf[ts];
+        const double ri = rho[i];
+        const bool both = k > lvl[i];
+        const SearchWin w = search_window(ctl, c, ui, k);
+        const uint2* ck = cells + ctl->cell_off[k];
+        const unsigned int nxy = w.nc[0] * w.nc[1], ncell = nxy * w.nc[2];
+        const unsigned int e_lo = (item.y >> 5) * RCP_SEARCH_CHUNK;
+        const unsigned int e_hi = min(ncell, e_lo + RCP_SEARCH_CHUNK);
+        for (unsigned int e0 = e_lo; e0 < e_hi; e0 += 32) {   // warp-uniform rounds of 32 cells
+            const unsigned int e = e0 + lane;
+            uint2 range = make_uint2(0u, 0u);
+            if (e < e_hi) {
+                const unsigned int cz = e / nxy, r = e - cz * nxy;
+                const unsigned int cy = r / w.nc[0], cx = r - cy * w.nc[0];
+                range = window_cell(ck, w, cx, cy, cz);
+            }
+            const unsigned int cnt = range.y - range.x;
+            unsigned int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(FULL, incl, o);
+                if ((int)lane >= o) incl += y;
+            }
+            const unsigned int total = __shfl_sync(FULL, incl, 31);
+            for (unsigned int cb = 0; cb < total; cb += 32) {   // warp-uniform
+                const unsigned int cc = cb + lane;
+                // owner: the first lane whose inclusive count exceeds cc
+                int o = 0;
+                for (int b = 16; b > 0; b >>= 1)
+                    if (__shfl_sync(FULL, incl, o + b - 1) <= cc) o += b;
+                const unsigned int first = __shfl_sync(FULL, range.x, o);
+                const unsigned int before = __shfl_sync(FULL, incl - cnt, o);
+                if (cc < total) {
+                    const unsigned int j =
+                        listed_partner(c, Eabs, x, rho, idx_sorted, xsf, first + (cc - before), i, ui, ri);
+                    if (j != 0xffffffffu) eb.put(ctl, pairs, cap, nbits, i, j, both);
+                }
+                if (__any_sync(FULL, eb.n > RCP_SEARCH_BUF / 2)) eb.flush_warp(ctl, pairs, cap);
+            }
+        }
+    }
+    eb.flush_warp(ctl, pairs, cap);
+}
+
+// Placement rounds: the candidates of class kcur (those not yet placed) scan
+// their own class and every coarser one (and, with frozen spheres, every
+// class: frozen spheres of finer classes are placed before any class is); an
+// overlapping pair marks the candidate that must give way.
 __global__ void __launch_bounds__(256)
 k_place_conflicts(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
                   const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
                   const double* D0, const unsigned char* placed, unsigned char* reject, int kcur)
 {
-    search_body<true>(ctl, c, xA, xB, rho, lvl, idx_sorted, xsf, cells, nullptr, 0ull, 0, D0, placed, reject,
-                      kcur);
+    const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ts >= c.N) return;
+    const long long i = idx_sorted ? (long long)idx_sorted[ts] : ts;
+    // every overlap with a placed sphere or a class-mate is found from the
+    // candidate's side
+    if (placed[i] || lvl[i] != kcur) return;
+    const double4_32a* x = ctl->parity ? xB : xA;
+    const float4 ui = xsf[ts];
+    const double ri = rho[i];
+    const int li = lvl[i];
+    const int kend = c.nfrozen > 0 ? ctl->nlev - 1 : li;
+    const float Eabs = (float)(5e-7 * c.Lmax);
+    if (c.walls | c.container) {   // a candidate must keep off the walls too (distance below rho_i)
+        const double4_32a xi = x[i];
+        for (int a = 0; a < 3; ++a) {
+            if (!((c.walls >> a) & 1)) continue;
+            const double xa = a == 0 ? xi.x : (a == 1 ? xi.y : xi.z);
+            if (xa < ri || c.L[a] - xa < ri) reject[i] = 1;
+        }
+        if (c.container) {   // distance to the curved wall R - |x - c| over its axes
+            double s2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                if (!((c.caxes >> a) & 1)) continue;
+                const double o = (a == 0 ? xi.x : (a == 1 ? xi.y : xi.z)) - c.halfL[a];
+                s2 = s2 + o * o;
+            }
+            if (c.Rc - sqrt(s2) < ri) reject[i] = 1;
+        }
+    }
+    for (int k = 0; k <= kend; ++k) {
+        if (!(ctl->rho_lvl_f[k] > 0.0f)) continue;
+        const SearchWin w = search_window(ctl, c, ui, k);
+        const uint2* ck = cells + ctl->cell_off[k];
+        for (unsigned int cz = 0; cz < w.nc[2]; ++cz)
+            for (unsigned int cy = 0; cy < w.nc[1]; ++cy)
+                for (unsigned int cx = 0; cx < w.nc[0]; ++cx)
+                    scan_cell(c, Eabs, x, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
+                              [&](unsigned int j) {
+                                  // i gives way to a placed sphere and to a
+                                  // class-mate candidate that precedes it
+                                  // (larger D0, then lower index); spheres of
+                                  // later classes are not there yet
+                                  if (placed[j]) reject[i] = 1;
+                                  else if (lvl[j] == kcur) {
+                                      const bool j_first = D0[j] > D0[i] || (D0[j] == D0[i] && (long long)j < i);
+                                      reject[j_first ? i : (long long)j] = 1;
+                                  }
+                              });
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -65,6 +65,7 @@ struct RcpCtl {
     unsigned long long rho_lvl_bits[RCP_KMAX];
     unsigned long long lvl_count[RCP_KMAX];
     unsigned long long pair_cursor;   // entries emitted by the pair search
+    unsigned int search_heavy;        // search windows queued for k_search_heavy
     double rho_lvl[RCP_KMAX];
     float rho_lvl_f[RCP_KMAX];   // fl32 of rho_lvl (the search windows' binary32 radii)
     int nlev;
@@ -343,9 +344,13 @@ __global__ void k_flip_parity(RcpCtl* ctl);
 __global__ void k_iota(long long N, unsigned int* out);
 __global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys, long long n, uint2* cells);
 __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
-                         const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
-                         const uint2* cells,
-                         unsigned long long* pairs, unsigned long long cap, int nbits);
+                         const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
+                         unsigned long long* pairs, unsigned long long cap, int nbits, uint2* heavy,
+                         unsigned int heavy_cap);
+__global__ void k_search_heavy(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
+                               const double* rho, const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
+                               const uint2* cells, unsigned long long* pairs, unsigned long long cap, int nbits,
+                               const uint2* heavy, unsigned int heavy_cap);
 __global__ void k_row_count(const unsigned long long* pairs, long long P, int nbits, unsigned int* cnt);
 __global__ void k_row_scatter(const unsigned long long* pairs, long long P, int nbits, const unsigned int* rowptr,
                               unsigned int* fill, unsigned int* colu);

@@ -138,14 +138,15 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
 }
 
 // Displacement a - b along one axis as an unevaluated binary32 sum hi + lo in
-// length units, exact up to ~2^-40 relative: the integer part is split so
-// that no digit of the remainder difference is lost.
+// length units, exact up to ~2^-40 relative: the integer part is split into
+// its upper 24 bits and its low 8 bits (each exact in binary32, no 64-bit
+// conversion) so that no digit of the remainder difference is lost.
 __device__ __forceinline__ void rec_dx2(int qa, float la, int qb, float lb, float shi, float slo, float& hi,
                                         float& lo)
 {
     const int dq = (int)((unsigned int)qa - (unsigned int)qb);
-    const float hq = (float)dq;
-    const float eq = (float)((long long)dq - __float2ll_rn(hq));   // |eq| <= 64, exact
+    const float hq = (float)((dq >> 8) * 256);   // at most 24 significant bits: exact
+    const float eq = (float)(dq & 0xff);         // dq - the above, in [0, 255]: exact
     float s1, e1, x_hi, t;
     two_sum(eq, la - lb, s1, e1);
     two_sum(hq, s1, x_hi, t);
