@@ -78,7 +78,6 @@ struct rcp_ctx {
     unsigned long long* key2 = nullptr;
     unsigned int* idx1 = nullptr;
     unsigned int* idx2 = nullptr;
-    unsigned int* idx0 = nullptr;
     const unsigned int* idx_sorted = nullptr;
     const unsigned long long* skeys = nullptr;  // sorted cell keys of the last build
     // mixed path: the state is kept in cell-key order; perm[i] is the caller's
@@ -99,8 +98,8 @@ struct rcp_ctx {
     unsigned int* long_rows = nullptr;  // [N] rows longer than RCP_LONG_ROW
     uint2* sheavy = nullptr;            // [N] search windows queued for a warp each (sphere, class)
     unsigned long long pcap = 0;
-    unsigned int* hist = nullptr;
-    unsigned long long hist_cap = 0;
+    unsigned int* cptr = nullptr;       // cell row pointers of the counting sort [ncells + 1]
+    unsigned int* ccnt = nullptr;       // per-cell counts, then fill cursors [ncells + 1]
     unsigned int* scan_tmp = nullptr;
     unsigned long long scan_tmp_cap = 0;
     bool built = false;
@@ -276,62 +275,6 @@ rcp_status scan_u32(rcp_ctx* h, const unsigned int* in, unsigned long long n, un
     return RCP_OK;
 }
 
-rcp_status ensure_hist(rcp_ctx* h, unsigned long long n)
-{
-    unsigned long long nb = (n + RCP_SORT_THREADS * RCP_SORT_ITEMS - 1) / (RCP_SORT_THREADS * RCP_SORT_ITEMS);
-    unsigned long long need = 256 * (nb > 0 ? nb : 1);
-    if (need > h->hist_cap) {
-        CKS(dalloc(h, &h->hist, need));
-        h->hist_cap = need;
-    }
-    return ensure_scan_tmp(h, need);
-}
-
-// LSD radix sort of (key, val) over the digit shifts given, stable.  Reads
-// `in` (kept intact), ping-pongs between b1 and b2; *result receives the
-// buffer holding the sorted keys (and *vres the values).
-rcp_status radix_sort(rcp_ctx* h, const unsigned long long* in, const unsigned int* vin, unsigned long long n,
-                      const std::vector<int>& shifts, unsigned long long* b1, unsigned int* v1,
-                      unsigned long long* b2, unsigned int* v2, const unsigned long long** result,
-                      const unsigned int** vres)
-{
-    CKS(ensure_hist(h, n));
-    const unsigned long long* src = in;
-    const unsigned int* vsrc = vin;
-    unsigned long long* dst = b1;
-    unsigned int* vdst = v1;
-    if (n == 0 || shifts.empty()) {
-        *result = in;
-        if (vres) *vres = vin;
-        return RCP_OK;
-    }
-    unsigned int nb = rcp_ceil_div(n, RCP_SORT_THREADS * RCP_SORT_ITEMS);
-    for (size_t p = 0; p < shifts.size(); ++p) {
-        h->launches += 1;
-        k_radix_hist<<<nb, RCP_SORT_THREADS, 0, h->stream>>>(src, (long long)n, shifts[p], h->hist, nb);
-        CKL();
-        CKS(scan_u32(h, h->hist, 256ull * nb, h->hist, h->scan_tmp));
-        h->launches += 1;
-        k_radix_scatter<<<nb, RCP_SORT_THREADS, 0, h->stream>>>(src, vsrc, (long long)n, shifts[p], h->hist, nb,
-                                                               dst, vsrc ? vdst : nullptr);
-        CKL();
-        src = dst;
-        vsrc = vsrc ? vdst : nullptr;
-        dst = (dst == b1) ? b2 : b1;
-        vdst = (vdst == v1) ? v2 : v1;
-    }
-    *result = src;
-    if (vres) *vres = vsrc;
-    return RCP_OK;
-}
-
-std::vector<int> field_shifts(int lo, int nbits)
-{
-    std::vector<int> s;
-    for (int b = 0; b < nbits; b += 8) s.push_back(lo + b);
-    return s;
-}
-
 // ---------------------------------------------------------------- build
 rcp_status search_once(rcp_ctx* h);
 rcp_status relist_long(rcp_ctx* h);
@@ -344,7 +287,7 @@ rcp_status ensure_pair_capacity(rcp_ctx* h, unsigned long long P)
     CKS(dalloc(h, &h->pairs2, cap));
     CKS(dalloc(h, &h->col, cap));
     h->pcap = cap;
-    return ensure_hist(h, cap > (unsigned long long)h->N ? cap : (unsigned long long)h->N);
+    return RCP_OK;
 }
 
 // The build runs in three phases separated by host reads, so that several
@@ -379,29 +322,39 @@ rcp_status build_b(rcp_ctx* h)
                     "largest interaction diameter 4 rho_max = %.6g reaches the smallest box edge %.6g: a sphere "
                     "would meet its own periodic image",
                     4.0 * h->ctl_h->rho_lvl[0], h->c.Lmin);
-    int nlev = h->ctl_h->nlev;
-    int maxn[3] = {1, 1, 1};
-    for (int k = 0; k < nlev; ++k)
-        for (int a = 0; a < 3; ++a)
-            if (h->ctl_h->ng[k][a] > maxn[a]) maxn[a] = h->ctl_h->ng[k][a];
-    std::vector<int> shifts;
-    for (int a = 0; a < 3; ++a) {
-        int b = 0;
-        while ((1 << b) < maxn[a]) ++b;
-        for (int s : field_shifts(19 * a, b)) shifts.push_back(s);
-    }
-    {
-        int b = 0;
-        while ((1 << b) < nlev) ++b;
-        for (int s : field_shifts(57, b)) shifts.push_back(s);
-    }
     h->launches += 1;
-    k_cell_key<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->lvl, h->key, h->idx0);
+    k_cell_key<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->lvl, h->key);
     CKL();
-    const unsigned long long* skeys = nullptr;
-    const unsigned int* sidx = nullptr;
-    CKS(radix_sort(h, h->key, h->idx0, (unsigned long long)N, shifts, h->key1, h->idx1, h->key2, h->idx2, &skeys,
-                   &sidx));
+    // spheres by cell: a counting sort over the dense cell table through the
+    // CSR kernels (rows = cells, each row sorted by sphere index), the order
+    // of a stable sort of the cell keys
+    const unsigned long long ncells = h->ctl_h->cell_off[RCP_KMAX];
+    if (ncells > h->cells_cap) {
+        CKS(dalloc(h, &h->cells, ncells));
+        CKS(dalloc(h, &h->cptr, ncells + 1));
+        CKS(dalloc(h, &h->ccnt, ncells + 1));
+        CKS(ensure_scan_tmp(h, ncells + 1));
+        h->cells_cap = ncells;
+    }
+    const int cbits = bits_for((unsigned long long)N);
+    unsigned long long* ck = h->key1;
+    unsigned int* colu = h->idx1;
+    const unsigned int* sidx = h->idx2;
+    const unsigned long long* skeys = h->key2;
+    CK(cudaMemsetAsync(h->ccnt, 0, sizeof(unsigned int) * (ncells + 1), h->stream));
+    h->launches += 2;
+    k_cell_pairs<<<nbN, 256, 0, h->stream>>>(h->ctl, N, h->key, cbits, ck);
+    k_row_count<<<nbN, 256, 0, h->stream>>>(ck, N, cbits, h->ccnt);
+    CKL();
+    CKS(scan_u32(h, h->ccnt, ncells + 1, h->cptr, h->scan_tmp));
+    CK(cudaMemsetAsync(h->ccnt, 0, sizeof(unsigned int) * ncells, h->stream));   // fill cursors
+    h->launches += 5;
+    k_row_scatter<<<nbN, 256, 0, h->stream>>>(ck, N, cbits, h->cptr, h->ccnt, colu);
+    k_row_sort<<<rcp_ceil_div(N, RCP_RS_CAP), 256, RCP_RS_BUF * sizeof(unsigned int), h->stream>>>(
+        h->cptr, (long long)ncells, colu, h->idx2);
+    k_gather_keys<<<nbN, 256, 0, h->stream>>>(N, sidx, h->key, h->key2);
+    k_cell_table<<<rcp_ceil_div(ncells, 256), 256, 0, h->stream>>>(h->cptr, ncells, h->cells);
+    CKL();
     h->idx_sorted = sidx;
     h->skeys = skeys;
     h->launches += 1;
@@ -425,15 +378,6 @@ rcp_status build_b(rcp_ctx* h)
         std::swap(h->perm, h->perm_alt);
         h->idx_sorted = nullptr;   // sphere t is now the t-th in key order
     }
-    const unsigned long long ncells = h->ctl_h->cell_off[RCP_KMAX];
-    if (ncells > h->cells_cap) {
-        CKS(dalloc(h, &h->cells, ncells));
-        h->cells_cap = ncells;
-    }
-    CK(cudaMemsetAsync(h->cells, 0, sizeof(uint2) * ncells, h->stream));
-    h->launches += 1;
-    k_cell_ranges<<<nbN, 256, 0, h->stream>>>(h->ctl, skeys, N, h->cells);
-    CKL();
     return search_once(h);
 }
 
@@ -805,8 +749,8 @@ rcp_status rcp_destroy(rcp_handle h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     void* ptrs[] = {h->D0, h->xA, h->xB, h->xb, h->m64, h->v64, h->m32, h->v32, h->rA, h->rB, h->rb, h->g, h->part_e, h->part_k, h->part_e2, h->part_k2, h->xtmp, h->ctl, h->rho,
-                    h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx0, h->idx1, h->idx2, h->cells, h->cnt,
-                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->sheavy, h->hist, h->scan_tmp, h->perm, h->perm_alt, h->D0_alt, h->rho_alt,
+                    h->lvl, h->xf, h->xsf, h->key, h->key1, h->key2, h->idx1, h->idx2, h->cells, h->cnt,
+                    h->offs, h->pairs1, h->pairs2, h->col, h->rowptr, h->long_rows, h->sheavy, h->cptr, h->ccnt, h->scan_tmp, h->perm, h->perm_alt, h->D0_alt, h->rho_alt,
                     h->lvl_alt, h->row_e, h->row_k};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1059,7 +1003,6 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
         CKS(dalloc(h, &h->key, n));
         CKS(dalloc(h, &h->key1, n));
         CKS(dalloc(h, &h->key2, n));
-        CKS(dalloc(h, &h->idx0, n));
         CKS(dalloc(h, &h->idx1, n));
         CKS(dalloc(h, &h->idx2, n));
         CKS(dalloc(h, &h->cnt, n + 1));

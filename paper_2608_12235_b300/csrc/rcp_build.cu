@@ -8,9 +8,10 @@
 // 2^-k]), each class with its own uniform grid of power-of-two cells per
 // axis, sized by occupancy (a cell holds about `cell_occupancy` spheres of
 // its class; any cell size is correct because the search scans every cell
-// within its radius).  Particles are sorted by the 62-bit key (class, cz, cy,
-// cx) with a hand-written LSD radix sort, and a dense per-class cell table
-// holds each cell's range [start, end) in that order.  A sphere scans its
+// within its radius).  Particles are ordered by the key (class, cz, cy, cx)
+// with a counting sort over the dense per-class cell table (counts, a scan,
+// a scatter, each cell's spheres sorted by index), and the table holds each
+// cell's range [start, end) in that order.  A sphere scans its
 // own class and every finer class over the cells within its search radius;
 // a pair inside one class is found from both ends, a pair across classes
 // from the coarser end only, which emits both directions.  The pairs (row << b
@@ -216,7 +217,7 @@ __device__ __forceinline__ unsigned long long pack_key(unsigned int k, unsigned 
 }
 
 __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const int* lvl,
-                           unsigned long long* key, unsigned int* idx)
+                           unsigned long long* key)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.N) return;
@@ -227,74 +228,6 @@ __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const
     unsigned int cy = cell_of(p.y, c.L[1], c.invL[1], c.pow2L & 2, (unsigned int)ctl->ng[k][1]);
     unsigned int cz = cell_of(p.z, c.L[2], c.invL[2], c.pow2L & 4, (unsigned int)ctl->ng[k][2]);
     key[i] = pack_key((unsigned int)k, cz, cy, cx);
-    idx[i] = (unsigned int)i;
-}
-
-// ---------------------------------------------------------------------------
-// LSD radix sort, 8-bit digits.  Pass = histogram per block of
-// RCP_SORT_THREADS * RCP_SORT_ITEMS keys (digit-major layout), exclusive scan
-// over (digit, block), stable scatter.
-#define RCP_TILE (RCP_SORT_THREADS * RCP_SORT_ITEMS)
-
-__global__ void __launch_bounds__(RCP_SORT_THREADS)
-k_radix_hist(const unsigned long long* keys, long long n, int shift, unsigned int* hist, unsigned int nblocks)
-{
-    __shared__ unsigned int cnt[256];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * RCP_TILE;
-    for (int j = 0; j < RCP_SORT_ITEMS; ++j) {
-        long long t = base + (long long)j * RCP_SORT_THREADS + threadIdx.x;
-        if (t < n) atomicAdd(&cnt[(unsigned int)(keys[t] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[(unsigned long long)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
-}
-
-// Stable scatter: within a block, keys are placed in (chunk, warp, lane)
-// order; ranks inside a warp come from __match_any_sync.
-__global__ void __launch_bounds__(RCP_SORT_THREADS)
-k_radix_scatter(const unsigned long long* keys, const unsigned int* vals, long long n, int shift,
-                const unsigned int* hist, unsigned int nblocks, unsigned long long* okeys, unsigned int* ovals)
-{
-    constexpr int NW = RCP_SORT_THREADS / 32;
-    __shared__ unsigned int base[256];
-    __shared__ unsigned int wc[NW][256];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    base[tid] = hist[(unsigned long long)tid * nblocks + blockIdx.x];
-    for (int w = 0; w < NW; ++w) wc[w][tid] = 0;
-    __syncthreads();
-    const unsigned int lt = (1u << lane) - 1u;
-    const long long tile = (long long)blockIdx.x * RCP_TILE;
-    for (int j = 0; j < RCP_SORT_ITEMS; ++j) {
-        const long long t = tile + (long long)j * RCP_SORT_THREADS + tid;
-        const bool valid = t < n;
-        const unsigned long long key = valid ? keys[t] : 0ull;
-        const unsigned int val = (valid && vals) ? vals[t] : 0u;
-        const unsigned int digit = valid ? ((unsigned int)(key >> shift) & 255u) : 256u;
-        const unsigned int peers = __match_any_sync(0xffffffffu, digit);
-        const unsigned int rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[warp][digit] = __popc(peers);
-        __syncthreads();
-        {
-            unsigned int run = base[tid];
-            for (int w = 0; w < NW; ++w) {
-                unsigned int cc = wc[w][tid];
-                wc[w][tid] = run;
-                run += cc;
-            }
-            base[tid] = run;
-        }
-        __syncthreads();
-        if (valid) {
-            const unsigned int pos = wc[warp][digit] + rank;
-            okeys[pos] = key;
-            if (vals) ovals[pos] = val;
-        }
-        __syncthreads();
-        for (int w = 0; w < NW; ++w) wc[w][tid] = 0;
-        __syncthreads();
-    }
 }
 
 // Exclusive scan, 4096 items per block (1024 threads x 4); block totals are
@@ -354,19 +287,36 @@ __device__ __forceinline__ unsigned long long cell_index(const RcpCtl* ctl, unsi
            ((unsigned long long)cz * (unsigned int)ctl->ng[k][1] + cy) * (unsigned int)ctl->ng[k][0] + cx;
 }
 
-__global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys, long long n, uint2* cells)
+// Spheres sorted by cell: a counting sort through the CSR kernels, with the
+// cells as rows.  k_cell_pairs forms (cell index << nbits | sphere); the
+// cell index orders the cells as the key (class, cz, cy, cx) does, so the
+// rows, each sorted by sphere index (k_row_sort), give exactly the order a
+// stable sort of the cell keys gives.
+__global__ void k_cell_pairs(const RcpCtl* ctl, long long N, const unsigned long long* key, int nbits,
+                             unsigned long long* ck)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const unsigned long long key = keys[t];
-    const bool head = (t == 0) || keys[t - 1] != key;
-    const bool tail = (t == n - 1) || keys[t + 1] != key;
-    if (!head && !tail) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned long long k = key[i];
     const unsigned long long m = (1ull << 19) - 1ull;
-    const unsigned long long ci = cell_index(ctl, (unsigned int)(key >> 57), (unsigned int)((key >> 38) & m),
-                                             (unsigned int)((key >> 19) & m), (unsigned int)(key & m));
-    if (head) cells[ci].x = (unsigned int)t;
-    if (tail) cells[ci].y = (unsigned int)(t + 1);
+    const unsigned long long ci = cell_index(ctl, (unsigned int)(k >> 57), (unsigned int)((k >> 38) & m),
+                                             (unsigned int)((k >> 19) & m), (unsigned int)(k & m));
+    ck[i] = (ci << nbits) | (unsigned long long)i;
+}
+
+// The dense cell table from the cells' row pointers: [start, end) per cell.
+__global__ void k_cell_table(const unsigned int* cptr, unsigned long long ncells, uint2* cells)
+{
+    const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncells) cells[c] = make_uint2(cptr[c], cptr[c + 1]);
+}
+
+// The sorted keys (key position t holds the key of sphere sorted[t]).
+__global__ void k_gather_keys(long long N, const unsigned int* sorted, const unsigned long long* key,
+                              unsigned long long* skeys)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) skeys[t] = key[sorted[t]];
 }
 
 // ---------------------------------------------------------------------------

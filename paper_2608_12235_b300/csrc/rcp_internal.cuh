@@ -15,8 +15,6 @@
 #define RCP_NMAX_AXIS (1u << RCP_NBITS_AXIS)
 #define RCP_PAIR_THREADS 256
 #define RCP_TREE 1024          // elements per block of a tree-reduction pass
-#define RCP_SORT_THREADS 256
-#define RCP_SORT_ITEMS 16      // items per thread per block of a radix pass
 #ifndef RCP_LONG_ROW
 #define RCP_LONG_ROW 32        // default: rows longer than this get a warp in the mixed pair kernel (<= 32)
 #endif
@@ -328,12 +326,12 @@ __global__ void k_gather_sorted(long long N, const unsigned int* idx_sorted, con
 __global__ void k_level(RcpCtl* ctl, long long N, const double* rho, int* lvl);
 __global__ void k_grid(RcpCtl* ctl, RcpConst c);
 __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const int* lvl,
-                           unsigned long long* key, unsigned int* idx);
-__global__ void k_radix_hist(const unsigned long long* keys, long long n, int shift, unsigned int* hist,
-                             unsigned int nblocks);
-__global__ void k_radix_scatter(const unsigned long long* keys, const unsigned int* vals, long long n, int shift,
-                                const unsigned int* hist, unsigned int nblocks,
-                                unsigned long long* okeys, unsigned int* ovals);
+                           unsigned long long* key);
+__global__ void k_cell_pairs(const RcpCtl* ctl, long long N, const unsigned long long* key, int nbits,
+                             unsigned long long* ck);
+__global__ void k_cell_table(const unsigned int* cptr, unsigned long long ncells, uint2* cells);
+__global__ void k_gather_keys(long long N, const unsigned int* sorted, const unsigned long long* key,
+                              unsigned long long* skeys);
 __global__ void k_scan_block(const unsigned int* in, long long n, unsigned int* out, unsigned int* totals);
 __global__ void k_scan_add(unsigned int* out, long long n, const unsigned int* offs);
 __global__ void k_permute_state(const RcpCtl* ctl, long long N, const unsigned int* sorted, MixRec* rA, MixRec* rB,
@@ -342,7 +340,6 @@ __global__ void k_permute_state(const RcpCtl* ctl, long long N, const unsigned i
                                 const int* lvl, int* lvl2, const unsigned int* perm, unsigned int* perm2);
 __global__ void k_flip_parity(RcpCtl* ctl);
 __global__ void k_iota(long long N, unsigned int* out);
-__global__ void k_cell_ranges(const RcpCtl* ctl, const unsigned long long* keys, long long n, uint2* cells);
 __global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
                          const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
                          unsigned long long* pairs, unsigned long long cap, int nbits, uint2* heavy,
@@ -355,8 +352,9 @@ __global__ void k_row_count(const unsigned long long* pairs, long long P, int nb
 __global__ void k_row_scatter(const unsigned long long* pairs, long long P, int nbits, const unsigned int* rowptr,
                               unsigned int* fill, unsigned int* colu);
 __global__ void k_row_sort(const unsigned int* rowptr, long long N, const unsigned int* colu, unsigned int* col);
-#define RCP_RS_CAP 4096      // row starts per block of k_row_sort
-#define RCP_RS_BUF 11264     // entries a block of k_row_sort stages in shared memory (44 KB)
+#define RCP_RS_CAP 2048      // row starts per block of k_row_sort
+#define RCP_RS_BUF 6144      // entries a block of k_row_sort stages in shared memory (24 KB; a block whose
+                             // rows span more sorts them in place in global memory)
 __global__ void k_long_flags(const unsigned int* rowptr, long long N, unsigned int long_row, unsigned int* flags);
 __global__ void k_long_compact(RcpCtl* ctl, const unsigned int* flags, const unsigned int* offs, long long N,
                                unsigned int* long_rows);
