@@ -493,7 +493,7 @@ unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_
 // long-row blocks).
 unsigned int launch_blocks(const rcp_ctx* h)
 {
-    if (h->cfg.precision == RCP_MIXED) return (pair_blocks(h) + h->c.long_blocks) * (RCP_PAIR_THREADS / 32);
+    if (h->cfg.precision == RCP_MIXED) return pair_blocks(h) + h->c.long_blocks;
     return pair_blocks(h);
 }
 
@@ -555,7 +555,7 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
     }
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (h->cfg.precision == RCP_MIXED) {
-        // warp partials as compensated binary32 pairs, reduced and closed by one kernel
+        // block partials as compensated binary32 pairs, reduced and closed by one kernel
         k_kappa_mixed<<<1, 1024, 0, h->stream>>>(h->ctl, h->c, h->part_e, h->part_k, (long long)launch_blocks(h), mode);
         if (ev) cudaEventRecord(ev[2], h->stream);
         return 2;

@@ -328,8 +328,8 @@ __device__ __forceinline__ float warp_sum(float s)
 // moments, build snapshot and own record are requested into L2 as the row
 // starts, so the Adam epilogue does not wait on DRAM.  The kernel is bound by
 // the latency of the col -> record chains, not by DRAM bytes or L1 traffic.
-// Both parts end with the row's Adam step (or its gradient out); warp partials
-// of e and k go to part_e/part_k.  The order of every sum depends only on the
+// Both parts end with the row's Adam step (or its gradient out); block
+// partials of e and k go to part_e/part_k.  The order of every sum depends only on the
 // list, so results are reproducible run to run.
 #ifndef RCP_MIX_MINB
 #define RCP_MIX_MINB 5   // resident blocks per SM the register budget is sized for (48 registers)
@@ -457,7 +457,6 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
             }
         }
     }
-    // per-warp partials (no block barrier: warps finish independently)
     push_budget32(ctl, bud);
     // most lanes hold no overlap: lane 0 adds the others' compensated sums
     // in lane order (the same order whatever the timing)
@@ -475,14 +474,34 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
         }
     }
     const float wm = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(md)));   // md >= 0
+    // the block's partials: warp 0 adds the warps' compensated sums in warp
+    // order (a block retires only when its last warp ends, so the barrier
+    // holds no resource longer), one (sum, correction) pair per block
+    __shared__ float4 s_part[RCP_MIX_WARPS];
+    __shared__ float s_max[RCP_MIX_WARPS];
     if (lane == 0) {
-        // the warp's compensated sums (sum, correction), in binary32
-        const unsigned long long w = (unsigned long long)blk * RCP_MIX_WARPS + warp;
-        reinterpret_cast<float2*>(part_e)[w] = make_float2(es, ec);
-        reinterpret_cast<float2*>(part_k)[w] = make_float2(ks, kc);
-        if (wm > 0.f) {
-            const unsigned long long b = dbits((double)wm);
-            if (b > *(volatile unsigned long long*)&ctl->maxdelta_bits) atomicMax(&ctl->maxdelta_bits, b);
+        s_part[warp] = make_float4(es, ec, ks, kc);
+        s_max[warp] = wm;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const float4 p = lane < RCP_MIX_WARPS ? s_part[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float bm = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(lane < RCP_MIX_WARPS ? s_max[lane] : 0.f)));
+        if (lane == 0) {
+            float be = p.x, bec = p.y, bk = p.z, bkc = p.w;
+            for (int w = 1; w < RCP_MIX_WARPS; ++w) {
+                const float4 q = s_part[w];
+                acc2(be, bec, q.x);
+                bec = bec + q.y;
+                acc2(bk, bkc, q.z);
+                bkc = bkc + q.w;
+            }
+            reinterpret_cast<float2*>(part_e)[blk] = make_float2(be, bec);
+            reinterpret_cast<float2*>(part_k)[blk] = make_float2(bk, bkc);
+            if (bm > 0.f) {
+                const unsigned long long b = dbits((double)bm);
+                if (b > *(volatile unsigned long long*)&ctl->maxdelta_bits) atomicMax(&ctl->maxdelta_bits, b);
+            }
         }
     }
 }
