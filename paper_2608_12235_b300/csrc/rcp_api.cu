@@ -295,15 +295,22 @@ rcp_status ensure_pair_capacity(rcp_ctx* h, unsigned long long P)
 //   A: class sizes and grids (ctl copied to the host);
 //   B: keys, sort, cell table, search (entry count copied to the host);
 //   C: pair sort, CSR, long-row list, snapshot.
+// A mixed build (outside placement) works from the fixed-point records
+// alone: radii, keys and the prefilter's copy from the records, the search's
+// band positions converted where needed; no binary64 view is formed.
+static bool records_build(const rcp_ctx* h) { return h->cfg.precision == RCP_MIXED && !h->placing; }
+
 rcp_status build_a(rcp_ctx* h)
 {
     const long long N = h->N;
     const unsigned int nbN = rcp_ceil_div(N, 256);
-    if (!h->placing) CKS(materialize(h));   // placement writes the binary64 positions itself
     h->launches += 1;
     k_build_begin<<<1, 1, 0, h->stream>>>(h->ctl, h->sigma0);
     h->launches += 1;
-    k_rho<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->xf);
+    if (records_build(h))
+        k_rho_mixed<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->D0, h->rho, h->xf);
+    else   // binary64 positions (placement writes them itself)
+        k_rho<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->xf);
     h->launches += 1;
     k_level<<<nbN, 256, 0, h->stream>>>(h->ctl, N, h->rho, h->lvl);
     h->launches += 1;
@@ -323,7 +330,10 @@ rcp_status build_b(rcp_ctx* h)
                     "would meet its own periodic image",
                     4.0 * h->ctl_h->rho_lvl[0], h->c.Lmin);
     h->launches += 1;
-    k_cell_key<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->lvl, h->key);
+    if (records_build(h))
+        k_cell_key_mixed<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->rA, h->rB, h->lvl, h->key);
+    else
+        k_cell_key<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->lvl, h->key);
     CKL();
     // spheres by cell: a counting sort over the dense cell table through the
     // CSR kernels (rows = cells, each row sorted by sphere index), the order
@@ -365,7 +375,7 @@ rcp_status build_b(rcp_ctx* h)
         float* m2 = reinterpret_cast<float*>(h->g);
         float* v2 = m2 + 3 * (size_t)N;
         h->launches += 2;
-        k_permute_state<<<nbN, 256, 0, h->stream>>>(h->ctl, N, sidx, h->rA, h->rB, h->xA, h->xB, h->m32, h->v32, m2,
+        k_permute_state<<<nbN, 256, 0, h->stream>>>(h->ctl, N, sidx, h->rA, h->rB, nullptr, nullptr, h->m32, h->v32, m2,
                                                     v2, h->D0, h->D0_alt, h->rho, h->rho_alt, h->lvl, h->lvl_alt,
                                                     h->perm, h->perm_alt);
         k_flip_parity<<<1, 1, 0, h->stream>>>(h->ctl);
@@ -400,11 +410,13 @@ rcp_status search_once(rcp_ctx* h)
     CK(cudaMemsetAsync(&h->ctl->pair_cursor, 0, sizeof(unsigned long long) + sizeof(unsigned int), h->stream));
     const unsigned int hcap = (unsigned int)N;
     h->launches += 2;
-    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl, h->idx_sorted, h->xsf,
+    const MixRec* rA = records_build(h) ? h->rA : nullptr;
+    const MixRec* rB = records_build(h) ? h->rB : nullptr;
+    k_search<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, rA, rB, h->rho, h->lvl, h->idx_sorted, h->xsf,
                                          h->cells, h->pairs1, h->pcap, nbits, h->sheavy, hcap);
-    k_search_heavy<<<std::min(nbN, 8u * 148u), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->rho, h->lvl,
-                                                                     h->idx_sorted, h->xsf, h->cells, h->pairs1,
-                                                                     h->pcap, nbits, h->sheavy, hcap);
+    k_search_heavy<<<std::min(nbN, 8u * 148u), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, rA, rB, h->rho,
+                                                                     h->lvl, h->idx_sorted, h->xsf, h->cells,
+                                                                     h->pairs1, h->pcap, nbits, h->sheavy, hcap);
     CKL();
     CK(cudaMemcpyAsync(&h->ctl_h->pair_cursor, &h->ctl->pair_cursor, sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, h->stream));
@@ -448,7 +460,7 @@ rcp_status build_c(rcp_ctx* h)
     }
     CKS(relist_long(h));
     h->launches += 1;
-    k_build_end<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb, P);
+    k_build_end<<<nbN, 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, records_build(h) ? nullptr : h->xb, P);
     CKL();
     if (h->cfg.precision == RCP_MIXED) {
         h->launches += 1;
@@ -1204,6 +1216,11 @@ rcp_status rcp_set_positions(rcp_handle h, const double* x, double kappa, int on
         CKL();
     }
     if (h->built) {
+        if (h->cfg.precision == RCP_MIXED) {
+            // the binary64 build snapshot from the records' snapshot
+            h->launches += 1;
+            k_from_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rb, h->rb, h->D0, h->xb, h->xb);
+        }
         h->launches += 1;
         k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
         CKL();
@@ -1274,6 +1291,11 @@ rcp_status rcp_energy_grad_at(rcp_handle h, const double* x_dev, const double* k
         CKL();
     }
     if (h->built) {
+        if (h->cfg.precision == RCP_MIXED) {
+            // the binary64 build snapshot from the records' snapshot
+            h->launches += 1;
+            k_from_fixed<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->rb, h->rb, h->D0, h->xb, h->xb);
+        }
         h->launches += 1;
         k_disp_check<<<rcp_ceil_div(n, 256), 256, 0, h->stream>>>(h->ctl, h->c, h->xA, h->xB, h->xb);
         CKL();

@@ -64,6 +64,35 @@ __global__ void __launch_bounds__(256) k_rho(RcpCtl* ctl, RcpConst c, const doub
     }
 }
 
+// Mixed path: the same radii and binary32 copy from the fixed-point records,
+// with no binary64 view of the positions: u_a = fl32(q_a) 2^-32 drops the
+// remainder (below one unit, 2^-32) and rounds q_a to 24 bits, so it is
+// within 2^-25 + 2^-32 of x_a / L_a -- the prefilter's error budget for
+// fl32(x_a / L_a) (2^-25) grows by under 1 %, far inside its margins.
+// rho_i from D_i^0 exactly as k_rho forms it.
+__global__ void __launch_bounds__(256) k_rho_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB,
+                                                   const double* D0, double* rho, float4* xf)
+{
+    __shared__ double sh[8];
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double r = 0.0;
+    if (i < c.N) {
+        const int4 q = reinterpret_cast<const int4*>(ctl->parity ? rB : rA)[2 * i];
+        r = size_at(D0[i], ctl->kappa_b) * (0.5 + c.skin_s) + ctl->sigma0;
+        rho[i] = r;
+        xf[i] = make_float4(__uint2float_rn((unsigned int)q.x) * 0x1.0p-32f,
+                            __uint2float_rn((unsigned int)q.y) * 0x1.0p-32f,
+                            __uint2float_rn((unsigned int)q.z) * 0x1.0p-32f, (float)r);
+    }
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) r = fmax(r, sh[w]);
+        if (r > 0.0) atomicMax(&ctl->rho_max_bits, dbits(r));
+    }
+}
+
 // Mixed path: the per-sphere state in cell-key order (sphere t of the new
 // order is sphere sorted[t] of the old), so that the rows a warp evaluates
 // lie in neighbouring cells of one size class and their partners sit close
@@ -80,7 +109,7 @@ __global__ void k_permute_state(const RcpCtl* ctl, long long N, const unsigned i
     const int parity = ctl->parity;
     const long long s = sorted[t];
     (parity ? rA : rB)[t] = (parity ? rB : rA)[s];
-    (parity ? xA : xB)[t] = (parity ? xB : xA)[s];
+    if (xA) (parity ? xA : xB)[t] = (parity ? xB : xA)[s];   // binary64 view, when the build uses one
     for (int a = 0; a < 3; ++a) {
         m2[3 * t + a] = m[3 * s + a];
         v2[3 * t + a] = v[3 * s + a];
@@ -228,6 +257,26 @@ __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const
     unsigned int cy = cell_of(p.y, c.L[1], c.invL[1], c.pow2L & 2, (unsigned int)ctl->ng[k][1]);
     unsigned int cz = cell_of(p.z, c.L[2], c.invL[2], c.pow2L & 4, (unsigned int)ctl->ng[k][2]);
     key[i] = pack_key((unsigned int)k, cz, cy, cx);
+}
+
+// Mixed path: the cell of a record from its integer part alone.  With n = 2^b
+// cells per axis, floor((q + l) 2^-32 n) = q >> (32 - b) because l < 1: the
+// same cell as floor(fl(x/L) n) for the binary64 position the record was made
+// from (q = floor(fl(x/L) 2^32)), in integer arithmetic.
+__device__ __forceinline__ unsigned int cell_q(int q, unsigned int n)
+{
+    return n <= 1u ? 0u : (unsigned int)q >> (32 - (31 - __clz(n)));
+}
+
+__global__ void k_cell_key_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const int* lvl,
+                                 unsigned long long* key)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.N) return;
+    const int4 q = reinterpret_cast<const int4*>(ctl->parity ? rB : rA)[2 * i];
+    const int k = lvl[i];
+    key[i] = pack_key((unsigned int)k, cell_q(q.z, (unsigned int)ctl->ng[k][2]), cell_q(q.y, (unsigned int)ctl->ng[k][1]),
+                      cell_q(q.x, (unsigned int)ctl->ng[k][0]));
 }
 
 // Exclusive scan, 4096 items per block (1024 threads x 4); block totals are
@@ -401,12 +450,20 @@ __device__ __forceinline__ uint2 window_cell(const uint2* ck, const SearchWin& w
 // margins on top; pairs inside the band where those bounds cannot decide are
 // settled by the exact binary64 predicate, so the listed set is exactly the
 // binary64 one.
+__device__ __forceinline__ double4_32a rec_position(const MixRec& r, const RcpConst& c)
+{
+    return make_double4_32a(from_fixed(r.q.x, r.l.x, c.L[0]), from_fixed(r.q.y, r.l.y, c.L[1]),
+                            from_fixed(r.q.z, r.l.z, c.L[2]), 0.0);
+}
+
 // Candidate t (a sorted position) against sphere i: its index j when the
-// pair is listed (j != i), else 0xffffffff.
+// pair is listed (j != i), else 0xffffffff.  The band's binary64 positions
+// come from the records when the build has no binary64 view (recs != NULL),
+// the values the view would hold.
 __device__ __forceinline__ unsigned int listed_partner(const RcpConst& c, float Eabs, const double4_32a* x,
-                                                       const double* rho, const unsigned int* idx_sorted,
-                                                       const float4* xsf, unsigned int t, long long i,
-                                                       const float4& ui, double ri)
+                                                       const MixRec* recs, const double* rho,
+                                                       const unsigned int* idx_sorted, const float4* xsf,
+                                                       unsigned int t, long long i, const float4& ui, double ri)
 {
     const float up = 1.0f + 2e-6f, dn = 1.0f - 2e-6f;
     const float4 uj = xsf[t];
@@ -422,7 +479,8 @@ __device__ __forceinline__ unsigned int listed_partner(const RcpConst& c, float 
     const float lo_in = (cut * dn - Eabs) * dn;
     if (lo_in > 0.0f && r2 < lo_in * lo_in) return j;  // certainly listed
     // the band: exact binary64 predicate
-    const double4_32a xi = x[i], xj = x[j];
+    const double4_32a xi = recs ? rec_position(recs[i], c) : x[i];
+    const double4_32a xj = recs ? rec_position(recs[j], c) : x[j];
     const double ex = (c.bounded & 1) ? xi.x - xj.x : min_image_b(xi.x - xj.x, c.L[0], c.halfL[0]);
     const double ey = (c.bounded & 2) ? xi.y - xj.y : min_image_b(xi.y - xj.y, c.L[1], c.halfL[1]);
     const double ez = (c.bounded & 4) ? xi.z - xj.z : min_image_b(xi.z - xj.z, c.L[2], c.halfL[2]);
@@ -432,12 +490,12 @@ __device__ __forceinline__ unsigned int listed_partner(const RcpConst& c, float 
 }
 
 template <class F>
-__device__ __forceinline__ void scan_cell(const RcpConst& c, float Eabs, const double4_32a* x, const double* rho,
-                                          const unsigned int* idx_sorted, const float4* xsf, uint2 range,
-                                          long long i, const float4& ui, double ri, F&& hit)
+__device__ __forceinline__ void scan_cell(const RcpConst& c, float Eabs, const double4_32a* x, const MixRec* recs,
+                                          const double* rho, const unsigned int* idx_sorted, const float4* xsf,
+                                          uint2 range, long long i, const float4& ui, double ri, F&& hit)
 {
     for (unsigned int t = range.x; t < range.y; ++t) {
-        const unsigned int j = listed_partner(c, Eabs, x, rho, idx_sorted, xsf, t, i, ui, ri);
+        const unsigned int j = listed_partner(c, Eabs, x, recs, rho, idx_sorted, xsf, t, i, ui, ri);
         if (j != 0xffffffffu) hit(j);
     }
 }
@@ -496,10 +554,11 @@ struct EntryBuf {
 // its trip counts and most of its cells; idx_sorted is NULL when the state
 // itself is in that order.
 __global__ void __launch_bounds__(256)
-k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho, const int* lvl,
-         const unsigned int* idx_sorted, const float4* xsf, const uint2* cells, unsigned long long* pairs,
-         unsigned long long cap, int nbits, uint2* heavy, unsigned int heavy_cap)
+k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const MixRec* rA, const MixRec* rB,
+         const double* rho, const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
+         unsigned long long* pairs, unsigned long long cap, int nbits, uint2* heavy, unsigned int heavy_cap)
 {
+    const MixRec* recs = rA ? (ctl->parity ? rB : rA) : nullptr;
     const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = ts < c.N;
     const float Eabs = (float)(5e-7 * c.Lmax);
@@ -543,7 +602,7 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
                 for (unsigned int cz = 0; cz < w.nc[2]; ++cz)
                     for (unsigned int cy = 0; cy < w.nc[1]; ++cy)
                         for (unsigned int cx = 0; cx < w.nc[0]; ++cx)
-                            scan_cell(c, Eabs, x, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
+                            scan_cell(c, Eabs, x, recs, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
                                       [&](unsigned int j) { eb.put(ctl, pairs, cap, nbits, i, j, both); });
             }
         }
@@ -560,11 +619,12 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
 // binary search over the scan), so the lanes stay busy whatever the cells
 // hold.  The grid strides over the queue, whose length the device holds.
 __global__ void __launch_bounds__(256)
-k_search_heavy(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
-               const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
-               unsigned long long* pairs, unsigned long long cap, int nbits, const uint2* heavy,
-               unsigned int heavy_cap)
+k_search_heavy(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const MixRec* rA,
+               const MixRec* rB, const double* rho, const int* lvl, const unsigned int* idx_sorted,
+               const float4* xsf, const uint2* cells, unsigned long long* pairs, unsigned long long cap, int nbits,
+               const uint2* heavy, unsigned int heavy_cap)
 {
+    const MixRec* recs = rA ? (ctl->parity ? rB : rA) : nullptr;
     const unsigned int FULL = 0xffffffffu;
     const unsigned int lane = threadIdx.x & 31;
     const unsigned int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -613,7 +673,7 @@ k_search_heavy(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a
                 const unsigned int before = __shfl_sync(FULL, incl - cnt, o);
                 if (cc < total) {
                     const unsigned int j =
-                        listed_partner(c, Eabs, x, rho, idx_sorted, xsf, first + (cc - before), i, ui, ri);
+                        listed_partner(c, Eabs, x, recs, rho, idx_sorted, xsf, first + (cc - before), i, ui, ri);
                     if (j != 0xffffffffu) eb.put(ctl, pairs, cap, nbits, i, j, both);
                 }
                 if (__any_sync(FULL, eb.n > RCP_SEARCH_BUF / 2)) eb.flush_warp(ctl, pairs, cap);
@@ -668,7 +728,7 @@ k_place_conflicts(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_
         for (unsigned int cz = 0; cz < w.nc[2]; ++cz)
             for (unsigned int cy = 0; cy < w.nc[1]; ++cy)
                 for (unsigned int cx = 0; cx < w.nc[0]; ++cx)
-                    scan_cell(c, Eabs, x, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
+                    scan_cell(c, Eabs, x, nullptr, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
                               [&](unsigned int j) {
                                   // i gives way to a placed sphere and to a
                                   // class-mate candidate that precedes it
@@ -858,7 +918,7 @@ __global__ void k_build_end(RcpCtl* ctl, RcpConst c, const double4_32a* xA, cons
                             unsigned long long P)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < c.N) xb[i] = (ctl->parity ? xB : xA)[i];
+    if (i < c.N && xb) xb[i] = (ctl->parity ? xB : xA)[i];   // no binary64 snapshot in a mixed build
     if (i == 0) {
         ctl->need_rebuild = 0;
         ctl->disp_flag = 0u;

@@ -188,6 +188,14 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c)
 }
 
 // ---- small helpers ----
+// Binary64 coordinate of a fixed-point record axis: (q + l) L 2^-32, in [0, L).
+__device__ __forceinline__ double from_fixed(int q, float l, double L)
+{
+    double v = ((double)(unsigned int)q + (double)l) * (L * 0x1.0p-32);
+    if (v >= L) v = v - L;
+    return v;
+}
+
 #define RCP_KBUD_INF 0x7F800000u
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
@@ -340,14 +348,19 @@ __global__ void k_permute_state(const RcpCtl* ctl, long long N, const unsigned i
                                 const int* lvl, int* lvl2, const unsigned int* perm, unsigned int* perm2);
 __global__ void k_flip_parity(RcpCtl* ctl);
 __global__ void k_iota(long long N, unsigned int* out);
-__global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const double* rho,
-                         const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
-                         unsigned long long* pairs, unsigned long long cap, int nbits, uint2* heavy,
-                         unsigned int heavy_cap);
+__global__ void k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const MixRec* rA,
+                         const MixRec* rB, const double* rho, const int* lvl, const unsigned int* idx_sorted,
+                         const float4* xsf, const uint2* cells, unsigned long long* pairs, unsigned long long cap,
+                         int nbits, uint2* heavy, unsigned int heavy_cap);
 __global__ void k_search_heavy(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
-                               const double* rho, const int* lvl, const unsigned int* idx_sorted, const float4* xsf,
-                               const uint2* cells, unsigned long long* pairs, unsigned long long cap, int nbits,
-                               const uint2* heavy, unsigned int heavy_cap);
+                               const MixRec* rA, const MixRec* rB, const double* rho, const int* lvl,
+                               const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
+                               unsigned long long* pairs, unsigned long long cap, int nbits, const uint2* heavy,
+                               unsigned int heavy_cap);
+__global__ void k_rho_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const double* D0,
+                            double* rho, float4* xf);
+__global__ void k_cell_key_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const int* lvl,
+                                 unsigned long long* key);
 __global__ void k_row_count(const unsigned long long* pairs, long long P, int nbits, unsigned int* cnt);
 __global__ void k_row_scatter(const unsigned long long* pairs, long long P, int nbits, const unsigned int* rowptr,
                               unsigned int* fill, unsigned int* colu);

@@ -41,13 +41,6 @@ __device__ __forceinline__ MixRec make_rec(double4_32a p, const RcpConst& c)
 __device__ __forceinline__ float rec_D(const MixRec& r) { return __int_as_float(r.q.w); }
 __device__ __forceinline__ float rec_Dlo(const MixRec& r) { return r.l.w; }
 
-__device__ __forceinline__ double from_fixed(int q, float l, double L)
-{
-    double v = ((double)(unsigned int)q + (double)l) * (L * 0x1.0p-32);
-    if (v >= L) v = v - L;
-    return v;
-}
-
 // Displacement a - b of two records along one axis, in length units.
 __device__ __forceinline__ float rec_dx(int qa, float la, int qb, float lb, float scale)
 {
