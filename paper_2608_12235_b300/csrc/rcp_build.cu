@@ -540,6 +540,43 @@ struct EntryBuf {
     }
 };
 
+// The first lane whose inclusive count exceeds v (31 when none does).
+__device__ __forceinline__ int warp_owner(unsigned int incl, unsigned int v)
+{
+    int o = 0;
+    for (int b = 16; b > 0; b >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, o + b - 1) <= v) o += b;
+    return o;
+}
+
+__device__ __forceinline__ unsigned int warp_incl_scan(unsigned int v, int lane)
+{
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Queue a window of ncell cells for k_search_heavy: one item (sphere,
+// chunk << 5 | class) per chunk of RCP_SEARCH_CHUNK cells.  False when the
+// queue is full (its slots are then marked empty and the caller scans the
+// window itself).
+__device__ __forceinline__ bool queue_window(RcpCtl* ctl, uint2* heavy, unsigned int heavy_cap, long long ts, int k,
+                                             unsigned long long ncell)
+{
+    if (ncell >= (1ull << 31)) return false;
+    const unsigned int nch = (unsigned int)((ncell + RCP_SEARCH_CHUNK - 1) / RCP_SEARCH_CHUNK);
+    const unsigned int s = atomicAdd(&ctl->search_heavy, nch);
+    if ((unsigned long long)s + nch <= heavy_cap) {
+        for (unsigned int h = 0; h < nch; ++h) heavy[s + h] = make_uint2((unsigned int)ts, (h << 5) | (unsigned int)k);
+        return true;
+    }
+    for (unsigned long long h = s; h < heavy_cap && h < (unsigned long long)s + nch; ++h)
+        heavy[h] = make_uint2(0xffffffffu, 0u);
+    return false;
+}
+
 // The list search.  Sphere i of class l_i scans its own class and every
 // finer one (k >= l_i): a pair inside one class is found from both ends, a
 // pair across classes from the coarser end only, which emits both
@@ -548,18 +585,26 @@ struct EntryBuf {
 // cell per axis, whereas a fine sphere's window over a coarse grid exceeds it
 // by a coarse cell, which then holds many candidates that are out of reach.
 // A window of RCP_SEARCH_HEAVY cells or more (the largest spheres over the
-// finest grid) is queued for k_search_heavy, which gives it a warp; the rest
-// are scanned here, one thread per sphere.  Threads take the spheres in
-// cell-key order (size class, then cell), so a warp shares its size class,
-// its trip counts and most of its cells; idx_sorted is NULL when the state
-// itself is in that order.
-__global__ void __launch_bounds__(256)
+// finest grid) is queued for k_search_heavy, which gives it a warp.  The
+// other windows of a warp's 32 spheres (one class at a time) are laid end
+// to end, first cell by cell and then candidate by candidate, and the lanes
+// take them 32 at a time: each lane tests one candidate for whichever sphere
+// owns it, so the lanes stay busy however the windows and cells differ
+// (when each lane walked its own sphere's window, 9 of 32 lanes were busy).
+// Threads take the spheres in cell-key order (size class, then cell), so a
+// warp shares its size class and most of its cells; idx_sorted is NULL when
+// the state itself is in that order.
+// (64 registers, 4 blocks per SM: the unbounded build took 76 and ran 1.5x
+// slower for the lost occupancy)
+__global__ void __launch_bounds__(256, 4)
 k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const MixRec* rA, const MixRec* rB,
          const double* rho, const int* lvl, const unsigned int* idx_sorted, const float4* xsf, const uint2* cells,
          unsigned long long* pairs, unsigned long long cap, int nbits, uint2* heavy, unsigned int heavy_cap)
 {
+    const unsigned int FULL = 0xffffffffu;
     const MixRec* recs = rA ? (ctl->parity ? rB : rA) : nullptr;
     const long long ts = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const bool act = ts < c.N;
     const float Eabs = (float)(5e-7 * c.Lmax);
     const double4_32a* x = ctl->parity ? xB : xA;
@@ -576,39 +621,70 @@ k_search(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, 
     EntryBuf eb;
     eb.n = 0;
     const int nlev = ctl->nlev;
-    for (int k = 0; k < nlev; ++k) {   // warp-uniform, so the flushes below see the whole warp
+    for (int k = 0; k < nlev; ++k) {   // warp-uniform
+        SearchWin w = {{0, 0, 0}, {0u, 0u, 0u}, {1u, 1u, 1u}};
+        unsigned int ncell = 0u;   // this lane's light window
         if (k >= li && ctl->rho_lvl_f[k] > 0.0f) {
-            const SearchWin w = search_window(ctl, c, ui, k);
-            const unsigned long long ncell = (unsigned long long)w.nc[0] * w.nc[1] * w.nc[2];
-            bool queued = false;
-            if (ncell >= RCP_SEARCH_HEAVY && ncell < (1ull << 31)) {
-                // one queue item (sphere, chunk << 5 | class) per chunk of cells
-                const unsigned int nch = (unsigned int)((ncell + RCP_SEARCH_CHUNK - 1) / RCP_SEARCH_CHUNK);
-                const unsigned int s = atomicAdd(&ctl->search_heavy, nch);
-                if ((unsigned long long)s + nch <= heavy_cap) {
-                    for (unsigned int h = 0; h < nch; ++h)
-                        heavy[s + h] = make_uint2((unsigned int)ts, (h << 5) | (unsigned int)k);
-                    queued = true;
-                } else {
-                    // queue full: the slots it was given are marked empty and
-                    // the window is scanned here
-                    for (unsigned long long h = s; h < heavy_cap && h < (unsigned long long)s + nch; ++h)
-                        heavy[h] = make_uint2(0xffffffffu, 0u);
-                }
-            }
-            if (!queued) {
+            w = search_window(ctl, c, ui, k);
+            const unsigned long long nc = (unsigned long long)w.nc[0] * w.nc[1] * w.nc[2];
+            if (nc < RCP_SEARCH_HEAVY) {
+                ncell = (unsigned int)nc;
+            } else if (!queue_window(ctl, heavy, heavy_cap, ts, k, nc)) {
+                // queue full: this lane walks the window by itself
                 const bool both = k > li;
                 const uint2* ck = cells + ctl->cell_off[k];
                 for (unsigned int cz = 0; cz < w.nc[2]; ++cz)
                     for (unsigned int cy = 0; cy < w.nc[1]; ++cy)
                         for (unsigned int cx = 0; cx < w.nc[0]; ++cx)
-                            scan_cell(c, Eabs, x, recs, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui, ri,
-                                      [&](unsigned int j) { eb.put(ctl, pairs, cap, nbits, i, j, both); });
+                            scan_cell(c, Eabs, x, recs, rho, idx_sorted, xsf, window_cell(ck, w, cx, cy, cz), i, ui,
+                                      ri, [&](unsigned int j) { eb.put(ctl, pairs, cap, nbits, i, j, both); });
             }
         }
-        // buffers past half full go out with one reservation for the warp
-        // (a lane that fills its buffer inside a window reserves alone)
-        if (__any_sync(0xffffffffu, eb.n > RCP_SEARCH_BUF / 2)) eb.flush_warp(ctl, pairs, cap);
+        const unsigned int cin = warp_incl_scan(ncell, lane);
+        const unsigned int C = __shfl_sync(FULL, cin, 31);   // < 32 RCP_SEARCH_HEAVY
+        if (C == 0u) continue;
+        const uint2* ck = cells + ctl->cell_off[k];
+        const unsigned int ng0 = (unsigned int)ctl->ng[k][0], ng1 = (unsigned int)ctl->ng[k][1];
+        const unsigned int ng2 = (unsigned int)ctl->ng[k][2];
+        for (unsigned int cb = 0; cb < C; cb += 32u) {   // warp-uniform rounds of 32 cells
+            const unsigned int cc = cb + (unsigned int)lane;
+            const int o = warp_owner(cin, cc);   // the lane whose window holds cell cc
+            const unsigned int e = cc - (__shfl_sync(FULL, cin, o) - __shfl_sync(FULL, ncell, o));
+            const int lo0 = __shfl_sync(FULL, w.lo[0], o), lo1 = __shfl_sync(FULL, w.lo[1], o);
+            const int lo2 = __shfl_sync(FULL, w.lo[2], o);
+            const unsigned int n0 = __shfl_sync(FULL, w.nc[0], o), n1 = __shfl_sync(FULL, w.nc[1], o);
+            uint2 range = make_uint2(0u, 0u);
+            if (cc < C) {
+                const unsigned int n01 = n0 * n1;
+                const unsigned int cz = e / n01, r = e - cz * n01;
+                const unsigned int cy = r / n0, cx = r - cy * n0;
+                const unsigned int zz = (unsigned int)(lo2 + (int)cz) & (ng2 - 1u);
+                const unsigned int yy = (unsigned int)(lo1 + (int)cy) & (ng1 - 1u);
+                const unsigned int xx = (unsigned int)(lo0 + (int)cx) & (ng0 - 1u);
+                range = ck[((unsigned long long)zz * ng1 + yy) * ng0 + xx];
+            }
+            const unsigned int cnt = range.y - range.x;
+            const unsigned int tin = warp_incl_scan(cnt, lane);
+            const unsigned int T = __shfl_sync(FULL, tin, 31);
+            for (unsigned int tb = 0; tb < T; tb += 32u) {   // warp-uniform rounds of 32 candidates
+                const unsigned int tt = tb + (unsigned int)lane;
+                const int L = warp_owner(tin, tt);   // the lane holding that candidate's cell
+                const unsigned int cand =
+                    __shfl_sync(FULL, range.x, L) + (tt - (__shfl_sync(FULL, tin, L) - __shfl_sync(FULL, cnt, L)));
+                const int so = __shfl_sync(FULL, o, L);   // the lane of the sphere that owns the cell
+                const float4 us = make_float4(__shfl_sync(FULL, ui.x, so), __shfl_sync(FULL, ui.y, so),
+                                              __shfl_sync(FULL, ui.z, so), __shfl_sync(FULL, ui.w, so));
+                const double rs = __shfl_sync(FULL, ri, so);
+                const long long is = __shfl_sync(FULL, i, so);
+                const int ls = __shfl_sync(FULL, li, so);
+                if (tt < T) {
+                    const unsigned int j = listed_partner(c, Eabs, x, recs, rho, idx_sorted, xsf, cand, is, us, rs);
+                    if (j != 0xffffffffu) eb.put(ctl, pairs, cap, nbits, is, j, k > ls);
+                }
+                // buffers past half full go out with one reservation per warp
+                if (__any_sync(FULL, eb.n > RCP_SEARCH_BUF / 2)) eb.flush_warp(ctl, pairs, cap);
+            }
+        }
     }
     eb.flush_warp(ctl, pairs, cap);
 }
