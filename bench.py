@@ -220,10 +220,12 @@ def bench_batch(rcp, torch, iters: int, seed: int = 0, count: int = 64):
             "speedup": (n_it / tb) / (count * iters / ts), "tuned_long_row": lr, "tuned_chunk": chunk}
 
 
-def bench_autograd(rcp, torch, reps: int = 20):
+def bench_autograd(rcp, torch, reps: int = 50, trials: int = 3):
     """Fused forward + backward of the autograd binding on N = 2e5 truncated
     Weibull (k = 1.5, S = 100) at phi = 0.6, uniform positions, in both
-    precisions: calls per second of the whole torch forward + backward, the
+    precisions: calls per second of the whole torch forward + backward (the
+    median of `trials` runs of `reps` calls: the host's share of a call, torch's
+    autograd bookkeeping, varies from run to run on a shared host), the
     C-ABI evaluation alone (positions in, E, dE/dx, dE/dkappa out), and the
     pair kernel on the same list (in an Adam iteration, `rcp_profile`) with
     its algorithmic bandwidth: per sphere 148 B mixed (row pointer 4, record
@@ -243,13 +245,16 @@ def bench_autograd(rcp, torch, reps: int = 20):
         xr = x.clone().requires_grad_(True)
         for _ in range(3):
             autograd.energy(xr, kt, p, 0.0).backward()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            xr.grad = None
-            autograd.energy(xr, kt, p, 0.0).backward()
-        torch.cuda.synchronize()
-        out[f"fwd_bwd_per_s_{name}"] = reps / (time.perf_counter() - t0)
+        rates = []
+        for _ in range(trials):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                xr.grad = None
+                autograd.energy(xr, kt, p, 0.0).backward()
+            torch.cuda.synchronize()
+            rates.append(reps / (time.perf_counter() - t0))
+        out[f"fwd_bwd_per_s_{name}"] = float(np.median(rates))
         E = torch.empty(1, dtype=torch.float64, device=dev)
         dk = torch.empty_like(E)
         g = torch.empty_like(x)
