@@ -9,9 +9,9 @@ is chaotic in the rounding, so the mixed path's phi differs from the binary64
 phi of the same seed by an amount of the order of the protocol's own
 run-to-run scatter; the paper reports phi reproducible only to a few 1e-4
 when merely the thread count changes (Data and code availability).  Measured
-on B300 over seeds 0-4: phi_mixed - phi_fp64 = -2.03e-3 ... +1.12e-3, mean
--4.4e-4 (an earlier build of the mixed kernel: -1.05e-3 ... +7.6e-4, mean
-+1.6e-4), against a binary64 seed-to-seed standard deviation of 1.4e-3.  The
+on B300 over seeds 0-4: phi_mixed - phi_fp64 = -1.51e-3 ... +1.28e-3, mean
+-2.7e-4 (earlier builds of the mixed kernel: -2.03e-3 ... +1.12e-3), against
+a binary64 seed-to-seed standard deviation of 1.4e-3.  The
 bounds below are twice that scatter per seed and 1e-3 on the mean of five
 seeds (about 3.5 standard errors of a five-seed mean); the 1e-4 per-seed
 target of a single run is not met and is not asserted.
