@@ -865,8 +865,8 @@ __global__ void __launch_bounds__(1024) k_kappa_step_batch(const PackDev* P, int
     kappa_step_body(q.ctl, q.c, q.part_e, q.part_k, q.nparts, mode, buf);
 }
 
-// Close a mixed-precision evaluation: the warp partials (compensated binary32
-// pairs) are summed in one fixed order -- thread t takes partials t, t + 1024,
+// Close a mixed-precision evaluation: the block partials (compensated binary32
+// pairs, one per block of the pair kernel) are summed in one fixed order -- thread t takes partials t, t + 1024,
 // ... with 2Sum, then the threads' pairs meet in a fixed tree -- and widened to
 // binary64 at the end (binary64 adds are slow on B300, and the partials carry
 // no more than binary32 pairs anyway); the rest is the kappa step of the
