@@ -271,7 +271,10 @@ int rcp_dim(rcp_handle h);
  * inflated to contact with those held fixed, then everything is released and
  * relaxed together, and so on down the classes.  The calls below give the
  * "held fixed" part: frozen spheres keep their positions and a contact
- * diameter that kappa does not scale.  Binary64 path only. */
+ * diameter that kappa does not scale.  Both precisions: the mixed path
+ * carries the frozen flag in the sign of the record's D^0 and runs a pair
+ * kernel that tells the contact diameters apart whenever the packing holds
+ * frozen spheres. */
 
 /* Create a seated packing: Nf >= 1 frozen spheres (internal indices
  * 0..Nf-1) and N >= 1 mobile ones (indices Nf..Nf+N-1; every array of the
@@ -281,7 +284,8 @@ int rcp_dim(rcp_handle h);
  *   diameters: host [N] relative diameters D_i^0 of the mobile spheres;
  *   d, box, seed: as for rcp_create (the uniform draw covers all Nf + N
  *         indices; the frozen rows are then replaced by fixed_x);
- *   cfg: required, precision RCP_FP64 (else RCP_ERR_UNSUPPORTED).
+ *   cfg: required, either precision (flat walls and containers remain
+ *         binary64 only, as for rcp_create).
  * Pairs with a frozen sphere have d_ij = (F_i + kappa D_j^0)/2 (or (F_i +
  * F_j)/2), so dE/dkappa takes (mobile D^0)/2 from them; a frozen sphere's
  * gradient is zero and Adam does not move it; the growth term -mu kappa sum
@@ -307,7 +311,8 @@ long long rcp_frozen(rcp_handle h);
  * every sphere: rcp_create of the contact diameters with phi0 = the seated
  * phi and placement off, positions from the seated run with kappa = 1, run to
  * the stop and shrunk.  After each stage the diameters are the contact
- * diameters kappa_c D.  cfg: required, RCP_FP64.
+ * diameters kappa_c D.  cfg: required, either precision (every stage runs
+ * in it).
  *   x_out: host [N][d] final positions, diam_out: host [N] final contact
  *   diameters (caller order); phi_out, iters_out (may be NULL): host [2C-1]
  *   phi and Adam steps of the stages in order: pack, seat 1, release 1,

@@ -551,7 +551,9 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
     const unsigned int nb = pair_blocks(h);
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->cfg.precision == RCP_MIXED) {
-        k_pair_mixed<<<nb + h->c.long_blocks, RCP_PAIR_THREADS, 0, h->stream>>>(
+        // frozen spheres (a seated stage) take the kernel that tells their
+        // contact diameters apart; the rest the plain one
+        (h->c.nfrozen > 0 ? k_pair_mixed_fz : k_pair_mixed)<<<nb + h->c.long_blocks, RCP_PAIR_THREADS, 0, h->stream>>>(
             h->ctl, h->c, h->m32, h->v32, h->rA, h->rB, h->rowptr, h->col, h->long_rows, h->rb, h->part_e, h->part_k,
             mode, h->g);
     } else if (warp_rows(h)) {
@@ -861,7 +863,6 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     if (!diameters || !box || Nm < 1 || Nf < 0 || (Nf > 0 && (!fixed_d || !fixed_x))) return RCP_ERR_ARG;
     if (d != 2 && d != 3) return RCP_ERR_UNSUPPORTED;
     if (Nf >= (1LL << 31) || Nm >= (1LL << 31) - Nf) return RCP_ERR_ARG;
-    if (Nf > 0 && cfg && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     if (cfg && (cfg->walls & ~((1 << d) - 1))) return RCP_ERR_ARG;   // one bit per axis of the caller
     if (cfg && cfg->walls && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     if (cfg && (cfg->container < 0 || cfg->container > 2 || (cfg->container == 2 && d != 3))) return RCP_ERR_ARG;
@@ -1099,7 +1100,6 @@ rcp_status rcp_create_seated(const double* fixed_d, const double* fixed_x, long 
 {
     if (Nf < 1) return RCP_ERR_ARG;
     if (out) *out = nullptr;
-    if (!cfg || cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     return create_impl(fixed_d, fixed_x, Nf, diameters, N, d, box, seed, cfg, out);
 }
 
@@ -1115,7 +1115,6 @@ rcp_status rcp_cascade(const double* diameters, const int* cls, long long N, int
                        double* phi_out, long long* iters_out)
 {
     if (!diameters || !cls || !box || N < 1 || !x_out || !diam_out) return RCP_ERR_ARG;
-    if (!cfg || cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     int C = 0;
     for (long long i = 0; i < N; ++i) {
         if (cls[i] < 0) return RCP_ERR_ARG;
@@ -1782,6 +1781,7 @@ struct rcp_batch_ctx {
     int autotune = 0;
     bool tuned = false;
     int long_row = RCP_LONG_ROW;
+    bool any_frozen = false;   // some packing holds frozen spheres
     std::vector<cudaEvent_t> ev;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     long long launches = 0;
@@ -1823,7 +1823,7 @@ rcp_status batch_refresh(rcp_batch_ctx* b)
 void batch_iteration(rcp_batch_ctx* b, int mode)
 {
     if (b->precision == RCP_MIXED)
-        k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
+        (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
     else
         k_pair64_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
     if (b->precision == RCP_MIXED)
@@ -1914,11 +1914,11 @@ rcp_status batch_autotune_rows(rcp_batch_ctx* b)
         for (rcp_ctx* h : b->hs) BK(cudaStreamSynchronize(h->stream));
         BKS(b->hs[0], batch_refresh(b));
         for (int w = 0; w < 2; ++w)
-            k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
+            (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
                                                                                     RCP_MODE_GRAD);
         BK(cudaEventRecord(b->t0, b->stream));
         for (int w = 0; w < 5; ++w)
-            k_pair_mixed_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
+            (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
                                                                                     RCP_MODE_GRAD);
         BK(cudaEventRecord(b->t1, b->stream));
         BK(cudaEventSynchronize(b->t1));
@@ -1975,6 +1975,7 @@ rcp_status rcp_batch_create(rcp_handle* hs, int B, int autotune, rcp_batch* out)
             bstart[p] = blocks;
             blocks += q.nblocks;
             b->hs.push_back(h);
+            if (h->c.nfrozen > 0) b->any_frozen = true;
             h->stream = h->own_stream;
         }
         b->total_blocks = blocks;

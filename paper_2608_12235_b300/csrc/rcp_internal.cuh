@@ -301,6 +301,7 @@ __global__ void k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_
                               double* row_e, double* row_k, int mode, double* g_out);
 __global__ void k_kappa_step_batch(const PackDev* P, int mode);
 __global__ void k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode);
+__global__ void k_pair_mixed_batch_fz(const PackDev* P, const unsigned int* bstart, int B, int mode);
 __global__ void k_tree_pass2(const double* ina, const double* inb, long long n, double* outa, double* outb);
 __global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const double* g, const double4_32a* xb, double eta_x);
@@ -316,6 +317,9 @@ __global__ void k_to_fixed(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const
 __global__ void k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB,
                              const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
                              const MixRec* rb, double* part_e, double* part_k, int mode, double* g_out);
+__global__ void k_pair_mixed_fz(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB,
+                                const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
+                                const MixRec* rb, double* part_e, double* part_k, int mode, double* g_out);
 __global__ void k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                              const unsigned int* rowptr, const unsigned int* col);
 __global__ void k_verify_final(RcpCtl* ctl, RcpConst c);

@@ -155,6 +155,28 @@ __device__ __forceinline__ void rec_dx2(int qa, float la, int qb, float lb, floa
 // (d = kappa (D_i + D_j)/2 and r^2 from the split displacements), then
 // u = N / d^2 and delta = 1 - sqrt(1 - u) = u / (1 + sqrt(1 - u)).  Returns
 // delta (<= 0 for no overlap), r, and the displacement (binary32).
+// Contact diameter of a record as an unevaluated binary32 sum: kappa D^0 for
+// a mobile sphere (D^0 > 0), the fixed F = -D^0 for a frozen one (Sec. IV).
+__device__ __forceinline__ void contact_diameter2(const MixRec& r, const MixScalars& S, float& hi, float& lo)
+{
+    const float D = rec_D(r), Dl = rec_Dlo(r);
+    if (D > 0.0f) {
+        float p, pe;
+        two_prod(S.kappa, D, p, pe);
+        hi = p;
+        lo = pe + (S.kappa * Dl + S.kappa_lo * D);
+    } else {
+        hi = -D;
+        lo = -Dl;
+    }
+}
+
+// Binary32 contact diameter (the same choice).
+__device__ __forceinline__ float contact_diameter(float D, const MixScalars& S) { return D > 0.0f ? S.kappa * D : -D; }
+
+// FZ: the packing holds frozen spheres (D^0 = -F < 0), whose contact
+// diameter does not scale with kappa.
+template <bool FZ>
 __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& rj, const MixScalars& S,
                                                const RcpConst& c, float& dx, float& dy, float& dz, float& r)
 {
@@ -171,13 +193,24 @@ __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& r
     two_sum(px, py, s1, t1);
     two_sum(s1, pz, s2, t2);
     const float r2l = ((t1 + t2) + (ex + ey + ez)) + 2.0f * ((xh * xl + yh * yl) + zh * zl);
-    // d = kappa (D_i + D_j) / 2
-    float sh, se;
-    two_sum(rec_D(ri), rec_D(rj), sh, se);
-    const float sl = se + (rec_Dlo(ri) + rec_Dlo(rj));
-    float dh, de;
-    two_prod(S.kappa, 0.5f * sh, dh, de);
-    const float dl = de + (S.kappa * (0.5f * sl) + S.kappa_lo * (0.5f * sh));
+    // d = kappa (D_i + D_j) / 2; with a frozen sphere in the pair, the mean
+    // of the two contact diameters
+    float dh, dl;
+    if (!FZ || (rec_D(ri) > 0.0f && rec_D(rj) > 0.0f)) {
+        float sh, se;
+        two_sum(rec_D(ri), rec_D(rj), sh, se);
+        const float sl = se + (rec_Dlo(ri) + rec_Dlo(rj));
+        float de;
+        two_prod(S.kappa, 0.5f * sh, dh, de);
+        dl = de + (S.kappa * (0.5f * sl) + S.kappa_lo * (0.5f * sh));
+    } else {
+        float ai, ei, aj, ej, sh, se;
+        contact_diameter2(ri, S, ai, ei);
+        contact_diameter2(rj, S, aj, ej);
+        two_sum(ai, aj, sh, se);
+        dh = 0.5f * sh;
+        dl = 0.5f * (se + (ei + ej));
+    }
     // d^2 - r^2
     float d2h, d2e;
     two_prod(dh, dh, d2h, d2e);
@@ -201,13 +234,15 @@ __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& r
 // r_q <= d (1 + 1e-5) + 2 units (c.qmargin), r_q the distance of the integer
 // parts; the binary32 roundings of r_q^2 and d (a few 2^-24 each) sit far
 // inside the 1e-5.
+template <bool FZ>
 __device__ __forceinline__ bool pretest_q(const int4& qi, const int4& qj, const MixScalars& S, const RcpConst& c)
 {
     const float fx = (float)(int)((unsigned int)qi.x - (unsigned int)qj.x) * c.qscale[0];
     const float fy = (float)(int)((unsigned int)qi.y - (unsigned int)qj.y) * c.qscale[1];
     const float fz = (float)(int)((unsigned int)qi.z - (unsigned int)qj.z) * c.qscale[2];
     const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
-    const float d = S.kappa * (0.5f * (__int_as_float(qi.w) + __int_as_float(qj.w)));
+    const float Di = __int_as_float(qi.w), Dj = __int_as_float(qj.w);
+    const float d = FZ ? 0.5f * (contact_diameter(Di, S) + contact_diameter(Dj, S)) : S.kappa * (0.5f * (Di + Dj));
     const float T = __fmaf_rn(d, 1.00001f, c.qmargin);
     return !(r2 > T * T);
 }
@@ -223,18 +258,24 @@ __device__ __forceinline__ int4 load_q(const MixRec* r, unsigned int j)
 }
 
 // Gradient term of a pair that passed the pre-test (zero when the precise
-// overlap is not positive or the centres coincide); the j > i share of e and
-// k goes into (es, ec), (ks, kc), the overlap into md.
+// overlap is not positive or the centres coincide, and for a frozen row);
+// the j > i share of e and k goes into (es, ec), (ks, kc), the overlap into
+// md.  With a frozen sphere in the pair, d d / d kappa is half the mobile
+// D^0 rather than d / kappa, so k takes eps delta (1 - delta) (mobile parts)
+// / (2 d).
+template <bool FZ>
 __device__ __forceinline__ void pair_term_precise(const MixRec& ri, const MixRec& rj, long long i, unsigned int j,
                                                   const MixScalars& S, const RcpConst& c, float& t0, float& t1,
                                                   float& t2, float& es, float& ec, float& ks, float& kc, float& md)
 {
     float dx, dy, dz, r;
     t0 = t1 = t2 = 0.0f;
-    const float delta = precise_delta(ri, rj, S, c, dx, dy, dz, r);
+    const float delta = precise_delta<FZ>(ri, rj, S, c, dx, dy, dz, r);
     if (!(delta > 0.0f)) return;
-    const float dd = S.kappa * (0.5f * (rec_D(ri) + rec_D(rj)));
-    if (r > 0.0f) {
+    const float Di = rec_D(ri), Dj = rec_D(rj);
+    const bool mob = !FZ || (Di > 0.0f && Dj > 0.0f);
+    const float dd = mob ? S.kappa * (0.5f * (Di + Dj)) : 0.5f * (contact_diameter(Di, S) + contact_diameter(Dj, S));
+    if (r > 0.0f && (!FZ || Di > 0.0f)) {
         const float coef = __fdividef(S.eps * delta, dd * r);
         t0 = -coef * dx;
         t1 = -coef * dy;
@@ -242,7 +283,8 @@ __device__ __forceinline__ void pair_term_precise(const MixRec& ri, const MixRec
     }
     if ((long long)j > i) {
         acc2(es, ec, (0.5f * S.eps) * (delta * delta));
-        acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) * S.rkappa);
+        const float ek = (S.eps * delta) * (1.0f - delta);
+        acc2(ks, kc, mob ? ek * S.rkappa : __fdividef(ek * (0.5f * (fmaxf(Di, 0.0f) + fmaxf(Dj, 0.0f))), dd));
     }
     md = fmaxf(md, delta);
 }
@@ -277,10 +319,23 @@ __device__ __forceinline__ void push_budget32(RcpCtl* ctl, float bud)
 
 // Close row i: the Adam step of its record (Adam mode) or its gradient out.
 // Returns the row's skin budget (infinity in gradient mode).
+template <bool FZ>
 __device__ __forceinline__ float row_epilogue(RcpCtl* ctl, const RcpConst& c, const MixScalars& S, long long i,
                                               const MixRec& ri, float g0, float g1, float g2, float* m, float* v,
                                               MixRec* rout, const MixRec* rb, int mode, double* g_out)
 {
+    if (FZ && !(rec_D(ri) > 0.0f)) {
+        // a frozen sphere: no Adam step (its record carries over to the
+        // other buffer), no gradient, no skin use
+        if (mode == RCP_MODE_ADAM) {
+            rout[i] = ri;
+        } else {
+            g_out[3 * i] = 0.0;
+            g_out[3 * i + 1] = 0.0;
+            g_out[3 * i + 2] = 0.0;
+        }
+        return INFINITY;
+    }
     if (mode == RCP_MODE_ADAM) {
         MixRec rn = ri;
         float m0 = m[3 * i], m1 = m[3 * i + 1], m2 = m[3 * i + 2];
@@ -339,6 +394,7 @@ __device__ __forceinline__ void prefetch_row(const float* m, const float* v, con
 
 __device__ __forceinline__ unsigned int lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
+template <bool FZ>
 __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, float* m, float* v, MixRec* rA,
                                                 MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
                                                 const unsigned int* long_rows, const MixRec* rb, double* part_e, double* part_k, int mode,
@@ -373,13 +429,13 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                     const unsigned int t = w0 + 32u * m;
                     const unsigned int j0 = col[t], j1 = col[t + 32], j2 = col[t + 64], j3 = col[t + 96];
                     const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1), q2 = load_q(rin, j2), q3 = load_q(rin, j3);
-                    if (pretest_q(qi, q0, S, c)) hit |= 1u << m;
-                    if (pretest_q(qi, q1, S, c)) hit |= 2u << m;
-                    if (pretest_q(qi, q2, S, c)) hit |= 4u << m;
-                    if (pretest_q(qi, q3, S, c)) hit |= 8u << m;
+                    if (pretest_q<FZ>(qi, q0, S, c)) hit |= 1u << m;
+                    if (pretest_q<FZ>(qi, q1, S, c)) hit |= 2u << m;
+                    if (pretest_q<FZ>(qi, q2, S, c)) hit |= 4u << m;
+                    if (pretest_q<FZ>(qi, q3, S, c)) hit |= 8u << m;
                 }
                 for (; m < 32u && w0 + 32u * m < t1; ++m)
-                    if (pretest_q(qi, load_q(rin, col[w0 + 32u * m]), S, c)) hit |= 1u << m;
+                    if (pretest_q<FZ>(qi, load_q(rin, col[w0 + 32u * m]), S, c)) hit |= 1u << m;
                 if (hit) {
                     const MixRec ri = rin[i];
                     do {
@@ -387,7 +443,7 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                         hit &= hit - 1u;
                         const unsigned int j = col[w0 + 32u * k];
                         float a0, a1, a2;
-                        pair_term_precise(ri, rin[j], i, j, S, c, a0, a1, a2, es, ec, ks, kc, md);
+                        pair_term_precise<FZ>(ri, rin[j], i, j, S, c, a0, a1, a2, es, ec, ks, kc, md);
                         acc2(g0, c0, a0);
                         acc2(g1, c1, a1);
                         acc2(g2, c2, a2);
@@ -400,7 +456,7 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
             g0 = warp_sum(g0 + c0);
             g1 = warp_sum(g1 + c1);
             g2 = warp_sum(g2 + c2);
-            if (lane == 0) bud = fminf(bud, row_epilogue(ctl, c, S, i, rin[i], g0, g1, g2, m, v, rout, rb, mode, g_out));
+            if (lane == 0) bud = fminf(bud, row_epilogue<FZ>(ctl, c, S, i, rin[i], g0, g1, g2, m, v, rout, rb, mode, g_out));
         }
     } else {
         // one thread per row
@@ -420,18 +476,18 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                 for (; t + 4 <= t1; t += 4) {
                     const unsigned int j0 = col[t], j1 = col[t + 1], j2 = col[t + 2], j3 = col[t + 3];
                     const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1), q2 = load_q(rin, j2), q3 = load_q(rin, j3);
-                    if (pretest_q(qi, q0, S, c)) hit |= 1u << (t - t0);
-                    if (pretest_q(qi, q1, S, c)) hit |= 2u << (t - t0);
-                    if (pretest_q(qi, q2, S, c)) hit |= 4u << (t - t0);
-                    if (pretest_q(qi, q3, S, c)) hit |= 8u << (t - t0);
+                    if (pretest_q<FZ>(qi, q0, S, c)) hit |= 1u << (t - t0);
+                    if (pretest_q<FZ>(qi, q1, S, c)) hit |= 2u << (t - t0);
+                    if (pretest_q<FZ>(qi, q2, S, c)) hit |= 4u << (t - t0);
+                    if (pretest_q<FZ>(qi, q3, S, c)) hit |= 8u << (t - t0);
                 }
                 for (; t + 2 <= t1; t += 2) {
                     const unsigned int j0 = col[t], j1 = col[t + 1];
                     const int4 q0 = load_q(rin, j0), q1 = load_q(rin, j1);
-                    if (pretest_q(qi, q0, S, c)) hit |= 1u << (t - t0);
-                    if (pretest_q(qi, q1, S, c)) hit |= 2u << (t - t0);
+                    if (pretest_q<FZ>(qi, q0, S, c)) hit |= 1u << (t - t0);
+                    if (pretest_q<FZ>(qi, q1, S, c)) hit |= 2u << (t - t0);
                 }
-                if (t < t1 && pretest_q(qi, load_q(rin, col[t]), S, c)) hit |= 1u << (t - t0);
+                if (t < t1 && pretest_q<FZ>(qi, load_q(rin, col[t]), S, c)) hit |= 1u << (t - t0);
                 // pass 2: the marked partners through the precise terms, in
                 // the row's order
                 const MixRec ri = rin[i];
@@ -441,12 +497,12 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                     hit &= hit - 1u;
                     const unsigned int j = col[t0 + k];
                     float a0, a1, a2;
-                    pair_term_precise(ri, rin[j], i, j, S, c, a0, a1, a2, es, ec, ks, kc, md);
+                    pair_term_precise<FZ>(ri, rin[j], i, j, S, c, a0, a1, a2, es, ec, ks, kc, md);
                     acc2(g0, c0, a0);
                     acc2(g1, c1, a1);
                     acc2(g2, c2, a2);
                 }
-                bud = row_epilogue(ctl, c, S, i, ri, g0 + c0, g1 + c1, g2 + c2, m, v, rout, rb, mode, g_out);
+                bud = row_epilogue<FZ>(ctl, c, S, i, ri, g0 + c0, g1 + c1, g2 + c2, m, v, rout, rb, mode, g_out);
             }
         }
     }
@@ -504,7 +560,19 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
              const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
              double* part_k, int mode, double* g_out)
 {
-    pair_mixed_body(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out, blockIdx.x);
+    pair_mixed_body<false>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
+                           blockIdx.x);
+}
+
+// The same for a packing that holds frozen spheres (seated stages of the
+// cascade, Sec. IV).
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed_fz(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB, const unsigned int* rowptr,
+                const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
+                double* part_k, int mode, double* g_out)
+{
+    pair_mixed_body<true>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
+                          blockIdx.x);
 }
 
 __device__ __forceinline__ int batch_pack_m(const unsigned int* bstart, int B, unsigned int block)
@@ -520,13 +588,26 @@ __device__ __forceinline__ int batch_pack_m(const unsigned int* bstart, int B, u
 
 // Batched mixed pair kernel: block b serves packing p with local block
 // b - bstart[p], so each packing computes exactly what its own launch would.
-__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
-k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode)
+// FZ: some packing of the batch holds frozen spheres.
+template <bool FZ>
+__device__ __forceinline__ void pair_mixed_batch_body(const PackDev* P, const unsigned int* bstart, int B, int mode)
 {
     const int p = batch_pack_m(bstart, B, blockIdx.x);
     const PackDev& q = P[p];
-    pair_mixed_body(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e,
-                    q.part_k, mode, q.g, blockIdx.x - bstart[p]);
+    pair_mixed_body<FZ>(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e,
+                        q.part_k, mode, q.g, blockIdx.x - bstart[p]);
+}
+
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode)
+{
+    pair_mixed_batch_body<false>(P, bstart, B, mode);
+}
+
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed_batch_fz(const PackDev* P, const unsigned int* bstart, int B, int mode)
+{
+    pair_mixed_batch_body<true>(P, bstart, B, mode);
 }
 
 // Binary64 maximum overlap over the listed pairs of the current binary64
@@ -550,7 +631,8 @@ k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* 
             if (dy > c.halfL[1]) dy = dy - c.L[1]; else if (dy < -c.halfL[1]) dy = dy + c.L[1];
             if (dz > c.halfL[2]) dz = dz - c.L[2]; else if (dz < -c.halfL[2]) dz = dz + c.L[2];
             const double r2 = dx * dx + dy * dy + dz * dz;
-            const double dd = kappa * (0.5 * (xi.w + xj.w));
+            const double dd = (xi.w > 0.0 && xj.w > 0.0) ? kappa * (0.5 * (xi.w + xj.w))
+                                                         : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
             if (r2 > (dd * dd) * RCP_NO_OVERLAP_MARGIN) continue;   // certainly delta <= 0
             const double r = sqrt(r2);
             const double delta = 1.0 - r / dd;
@@ -577,16 +659,18 @@ __global__ void k_adam_mixed(RcpCtl* ctl, RcpConst c, MixRec* rA, MixRec* rB, fl
     if (i < c.N) {
         MixRec* r = ctl->parity ? rB : rA;
         MixRec rn = r[i];
-        for (int a = 0; a < 3; ++a) {
-            float mm = m[3 * i + a], vv = v[3 * i + a];
-            int* q = a == 0 ? &rn.q.x : (a == 1 ? &rn.q.y : &rn.q.z);
-            float* l = a == 0 ? &rn.l.x : (a == 1 ? &rn.l.y : &rn.l.z);
-            adam_fixed((float)g[3 * i + a], mm, vv, *q, *l, c.qinv[a], S);
-            m[3 * i + a] = mm;
-            v[3 * i + a] = vv;
+        if (rec_D(rn) > 0.0f) {   // a frozen sphere does not move
+            for (int a = 0; a < 3; ++a) {
+                float mm = m[3 * i + a], vv = v[3 * i + a];
+                int* q = a == 0 ? &rn.q.x : (a == 1 ? &rn.q.y : &rn.q.z);
+                float* l = a == 0 ? &rn.l.x : (a == 1 ? &rn.l.y : &rn.l.z);
+                adam_fixed((float)g[3 * i + a], mm, vv, *q, *l, c.qinv[a], S);
+                m[3 * i + a] = mm;
+                v[3 * i + a] = vv;
+            }
+            r[i] = rn;
+            bud = skin_budget32(ctl, c, S, rn, rb[i]);
         }
-        r[i] = rn;
-        bud = skin_budget32(ctl, c, S, rn, rb[i]);
     }
     push_budget32(ctl, bud);
 }

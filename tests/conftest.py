@@ -26,7 +26,8 @@ def row_term_scale(orc, x, D0, L, kappa, d=3, eps=1.0, band=1e-8):
     the inputs alone (binary64, no value of the CUDA path):
 
       s_i = sum over the overlapping partners j of sphere i of the magnitude
-            eps delta_ij / d_ij of its term of dE/dx_i;
+            eps delta_ij / d_ij of its term of dE/dx_i (d_ij the mean of the
+            two contact diameters: kappa D^0, or F for a frozen sphere);
       a_i = sum over the partners with |delta_ij| < band of eps 2 band / d_ij.
 
     The mixed path forms each pair term in binary32 from exactly represented
@@ -48,7 +49,8 @@ def row_term_scale(orc, x, D0, L, kappa, d=3, eps=1.0, band=1e-8):
     dx = x[rows] - x[col]
     dx -= L * np.rint(dx / L)
     r = np.sqrt(np.sum(dx * dx, axis=1))
-    dd = kappa * 0.5 * (D0[rows] + D0[col])
+    size = np.where(D0 > 0.0, kappa * D0, -D0)   # a frozen sphere (D0 = -F) keeps its contact diameter F
+    dd = 0.5 * (size[rows] + size[col])
     delta = 1.0 - r / dd
     t = np.where(delta > 0.0, eps * delta / dd, 0.0)
     a = np.where(np.abs(delta) < band, eps * 2.0 * band / dd, 0.0)

@@ -56,9 +56,9 @@ def test_create_rejects_bad_input_before_touching_the_gpu(lib):
 def test_seated_and_cascade_reject_bad_input_before_touching_the_gpu(lib):
     from paper_2608_12235_b300 import rcp
     import numpy as np
-    mixed = rcp.rcp_config_default(precision=rcp.RCP_MIXED)
-    with pytest.raises(rcp.RcpError) as e:   # frozen spheres: binary64 path only
-        rcp.rcp_create_seated([1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0, mixed)
+    mixed_walls = rcp.rcp_config_default(precision=rcp.RCP_MIXED, walls=1)
+    with pytest.raises(rcp.RcpError) as e:   # frozen spheres in either precision, walls binary64 only
+        rcp.rcp_create_seated([1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0, mixed_walls)
     assert e.value.status == 9
     with pytest.raises(rcp.RcpError) as e:   # a frozen diameter must be positive
         rcp.rcp_create_seated([-1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0)
@@ -69,8 +69,8 @@ def test_seated_and_cascade_reject_bad_input_before_touching_the_gpu(lib):
     with pytest.raises(rcp.RcpError) as e:   # class 1 is empty
         rcp.rcp_cascade([1.0, 1.0], [0, 2])
     assert e.value.status == 1
-    with pytest.raises(rcp.RcpError) as e:
-        rcp.rcp_cascade([1.0, 1.0], [0, 1], cfg=mixed)
+    with pytest.raises(rcp.RcpError) as e:   # walls: binary64 only, whatever the call
+        rcp.rcp_cascade([1.0, 1.0], [0, 1], cfg=mixed_walls)
     assert e.value.status == 9
 
 

@@ -1,5 +1,7 @@
 """Frozen spheres and the sequential cascade (Sec. IV): the binary64 CUDA path
-against the oracle, bit for bit, on the same seeded inputs.
+against the oracle, bit for bit, on the same seeded inputs; the mixed path
+within its tolerances (element-wise gradient, E and dE/dkappa against the
+magnitudes of their sums) and its runs to the stop beside binary64.
 
 Sizes: a few hundred spheres across several size classes and cell levels,
 frozen spheres in the coarsest class (the cascade's case) and in a finer
@@ -135,3 +137,63 @@ def test_cascade_in_a_ball_bitexact(rcp, orc):
     assert list(phi) == [f for _, _, f, _ in log]
     assert list(iters) == [t for _, _, _, t in log]
     assert np.array_equal(dm, do) and np.array_equal(x, xo)
+
+
+# ------------------------------------------------------------------ mixed precision
+def test_seated_energy_grad_mixed(rcp, orc, term_scale, grad_check, sums_check):
+    """Pairs with a frozen sphere take d = (F + kappa D^0)/2 (or (F_i + F_j)/2)
+    and half the mobile D^0 in dE/dkappa; frozen rows have no gradient."""
+    F, X = _lattice(2, 8.0, 2.4)
+    D = np.linspace(0.6, 1.0, 300)
+    Dall, x = orc.seated_state(F, X, D, seed=8, L=8.0, placement=0)
+    p = rcp.Packing(D, box=8.0, seed=8, fixed_d=F, fixed_x=X, precision=rcp.RCP_MIXED)
+    for k in (0.7, 1.3):
+        p.set_positions(x, k)
+        for mu in (0.0, 0.02):
+            E, g, dk, md = p.energy_grad(mu)
+            oE, og, odk, omd = orc.energy_grad(x, Dall, 8.0, k, mu)
+            assert omd > 0.0
+            # the mu terms take the mobile spheres only
+            sums_check(E, oE, dk, odk, mu, k, np.where(Dall > 0.0, Dall, 0.0), what="seated mixed")
+            assert abs(md - omd) <= 1e-5 * omd
+            assert not g[:F.size].any()
+            w = grad_check(g, og, term_scale(x, Dall, 8.0, k), what="seated mixed")
+            print(f"kappa {k} mu {mu}: worst gradient error / bound {w:.3g}")
+    p.close()
+
+
+def test_seated_run_mixed(rcp, orc):
+    """A seated stage in mixed precision to the stop and the shrink: the frozen
+    spheres keep their positions bit for bit, and phi lands beside the
+    binary64 run's (a whole run is chaotic in the rounding: a few 1e-3 at
+    this size)."""
+    F, X = _lattice(2, 8.0, 2.4)
+    D = np.linspace(0.7, 1.0, 240)
+    out = {}
+    for prec in (rcp.RCP_FP64, rcp.RCP_MIXED):
+        p = rcp.Packing(D, box=8.0, seed=9, fixed_d=F, fixed_x=X, placement=1, precision=prec)
+        r = p.run()
+        got = p.positions()
+        p.close()
+        assert r.stopped and r.max_delta < 5e-4
+        assert np.array_equal(got[:F.size], X)
+        out[prec] = r.phi
+    print(f"seated phi: binary64 {out[rcp.RCP_FP64]:.6f}, mixed {out[rcp.RCP_MIXED]:.6f}")
+    assert abs(out[rcp.RCP_MIXED] - out[rcp.RCP_FP64]) < 1e-2
+
+
+def test_cascade_mixed(rcp, orc):
+    """The two-class cascade in mixed precision: every stage reaches the stop
+    and lands beside the binary64 cascade's phi."""
+    nc, nf = 32, 256
+    D0 = np.concatenate([np.full(nc, 4.0), np.full(nf, 1.0)])
+    cls = np.concatenate([np.zeros(nc, int), np.ones(nf, int)])
+    perm = np.random.default_rng(1).permutation(D0.size)
+    D0, cls = D0[perm], cls[perm]
+    x64, d64, phi64, it64 = rcp.rcp_cascade(D0, cls, box=12.0, seed=7, cfg=rcp.rcp_config_default(placement=1))
+    cfg = rcp.rcp_config_default(placement=1, precision=rcp.RCP_MIXED)
+    x, dm, phi, iters = rcp.rcp_cascade(D0, cls, box=12.0, seed=7, cfg=cfg)
+    print(f"cascade phi: binary64 {list(phi64)}, mixed {list(phi)}")
+    assert len(phi) == len(phi64) == 3
+    assert all(abs(a - b) < 2e-2 for a, b in zip(phi, phi64))
+    assert np.all(np.isfinite(x)) and np.all(dm > 0.0)
