@@ -174,6 +174,18 @@ __device__ __forceinline__ void contact_diameter2(const MixRec& r, const MixScal
 // Binary32 contact diameter (the same choice).
 __device__ __forceinline__ float contact_diameter(float D, const MixScalars& S) { return D > 0.0f ? S.kappa * D : -D; }
 
+// d = kappa (D_i + D_j) / 2 of two mobile spheres as hi + lo.
+__device__ __forceinline__ void mobile_pair_diameter(const MixRec& ri, const MixRec& rj, const MixScalars& S,
+                                                     float& dh, float& dl)
+{
+    float sh, se;
+    two_sum(rec_D(ri), rec_D(rj), sh, se);
+    const float sl = se + (rec_Dlo(ri) + rec_Dlo(rj));
+    float de;
+    two_prod(S.kappa, 0.5f * sh, dh, de);
+    dl = de + (S.kappa * (0.5f * sl) + S.kappa_lo * (0.5f * sh));
+}
+
 // FZ: the packing holds frozen spheres (D^0 = -F < 0), whose contact
 // diameter does not scale with kappa.
 template <bool FZ>
@@ -196,20 +208,19 @@ __device__ __forceinline__ float precise_delta(const MixRec& ri, const MixRec& r
     // d = kappa (D_i + D_j) / 2; with a frozen sphere in the pair, the mean
     // of the two contact diameters
     float dh, dl;
-    if (!FZ || (rec_D(ri) > 0.0f && rec_D(rj) > 0.0f)) {
-        float sh, se;
-        two_sum(rec_D(ri), rec_D(rj), sh, se);
-        const float sl = se + (rec_Dlo(ri) + rec_Dlo(rj));
-        float de;
-        two_prod(S.kappa, 0.5f * sh, dh, de);
-        dl = de + (S.kappa * (0.5f * sl) + S.kappa_lo * (0.5f * sh));
+    if constexpr (FZ) {
+        if (rec_D(ri) > 0.0f && rec_D(rj) > 0.0f) {
+            mobile_pair_diameter(ri, rj, S, dh, dl);
+        } else {
+            float ai, ei, aj, ej, sh, se;
+            contact_diameter2(ri, S, ai, ei);
+            contact_diameter2(rj, S, aj, ej);
+            two_sum(ai, aj, sh, se);
+            dh = 0.5f * sh;
+            dl = 0.5f * (se + (ei + ej));
+        }
     } else {
-        float ai, ei, aj, ej, sh, se;
-        contact_diameter2(ri, S, ai, ei);
-        contact_diameter2(rj, S, aj, ej);
-        two_sum(ai, aj, sh, se);
-        dh = 0.5f * sh;
-        dl = 0.5f * (se + (ei + ej));
+        mobile_pair_diameter(ri, rj, S, dh, dl);
     }
     // d^2 - r^2
     float d2h, d2e;
@@ -241,8 +252,11 @@ __device__ __forceinline__ bool pretest_q(const int4& qi, const int4& qj, const 
     const float fy = (float)(int)((unsigned int)qi.y - (unsigned int)qj.y) * c.qscale[1];
     const float fz = (float)(int)((unsigned int)qi.z - (unsigned int)qj.z) * c.qscale[2];
     const float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
-    const float Di = __int_as_float(qi.w), Dj = __int_as_float(qj.w);
-    const float d = FZ ? 0.5f * (contact_diameter(Di, S) + contact_diameter(Dj, S)) : S.kappa * (0.5f * (Di + Dj));
+    float d;
+    if constexpr (FZ)
+        d = 0.5f * (contact_diameter(__int_as_float(qi.w), S) + contact_diameter(__int_as_float(qj.w), S));
+    else
+        d = S.kappa * (0.5f * (__int_as_float(qi.w) + __int_as_float(qj.w)));
     const float T = __fmaf_rn(d, 1.00001f, c.qmargin);
     return !(r2 > T * T);
 }
@@ -272,10 +286,17 @@ __device__ __forceinline__ void pair_term_precise(const MixRec& ri, const MixRec
     t0 = t1 = t2 = 0.0f;
     const float delta = precise_delta<FZ>(ri, rj, S, c, dx, dy, dz, r);
     if (!(delta > 0.0f)) return;
-    const float Di = rec_D(ri), Dj = rec_D(rj);
-    const bool mob = !FZ || (Di > 0.0f && Dj > 0.0f);
-    const float dd = mob ? S.kappa * (0.5f * (Di + Dj)) : 0.5f * (contact_diameter(Di, S) + contact_diameter(Dj, S));
-    if (r > 0.0f && (!FZ || Di > 0.0f)) {
+    float dd;
+    bool mob = true, grad_row = true;
+    if constexpr (FZ) {
+        const float Di = rec_D(ri), Dj = rec_D(rj);
+        mob = Di > 0.0f && Dj > 0.0f;
+        grad_row = Di > 0.0f;
+        dd = mob ? S.kappa * (0.5f * (Di + Dj)) : 0.5f * (contact_diameter(Di, S) + contact_diameter(Dj, S));
+    } else {
+        dd = S.kappa * (0.5f * (rec_D(ri) + rec_D(rj)));
+    }
+    if (r > 0.0f && grad_row) {
         const float coef = __fdividef(S.eps * delta, dd * r);
         t0 = -coef * dx;
         t1 = -coef * dy;
@@ -283,8 +304,13 @@ __device__ __forceinline__ void pair_term_precise(const MixRec& ri, const MixRec
     }
     if ((long long)j > i) {
         acc2(es, ec, (0.5f * S.eps) * (delta * delta));
-        const float ek = (S.eps * delta) * (1.0f - delta);
-        acc2(ks, kc, mob ? ek * S.rkappa : __fdividef(ek * (0.5f * (fmaxf(Di, 0.0f) + fmaxf(Dj, 0.0f))), dd));
+        if constexpr (FZ) {
+            const float ek = (S.eps * delta) * (1.0f - delta);
+            acc2(ks, kc, mob ? ek * S.rkappa
+                             : __fdividef(ek * (0.5f * (fmaxf(rec_D(ri), 0.0f) + fmaxf(rec_D(rj), 0.0f))), dd));
+        } else {
+            acc2(ks, kc, ((S.eps * delta) * (1.0f - delta)) * S.rkappa);
+        }
     }
     md = fmaxf(md, delta);
 }
@@ -324,17 +350,19 @@ __device__ __forceinline__ float row_epilogue(RcpCtl* ctl, const RcpConst& c, co
                                               const MixRec& ri, float g0, float g1, float g2, float* m, float* v,
                                               MixRec* rout, const MixRec* rb, int mode, double* g_out)
 {
-    if (FZ && !(rec_D(ri) > 0.0f)) {
-        // a frozen sphere: no Adam step (its record carries over to the
-        // other buffer), no gradient, no skin use
-        if (mode == RCP_MODE_ADAM) {
-            rout[i] = ri;
-        } else {
-            g_out[3 * i] = 0.0;
-            g_out[3 * i + 1] = 0.0;
-            g_out[3 * i + 2] = 0.0;
+    if constexpr (FZ) {
+        if (!(rec_D(ri) > 0.0f)) {
+            // a frozen sphere: no Adam step (its record carries over to the
+            // other buffer), no gradient, no skin use
+            if (mode == RCP_MODE_ADAM) {
+                rout[i] = ri;
+            } else {
+                g_out[3 * i] = 0.0;
+                g_out[3 * i + 1] = 0.0;
+                g_out[3 * i + 2] = 0.0;
+            }
+            return INFINITY;
         }
-        return INFINITY;
     }
     if (mode == RCP_MODE_ADAM) {
         MixRec rn = ri;
