@@ -282,7 +282,8 @@ def bench_rows(rcp, torch, large: bool = False):
       walls / container: lognormal N = 2e5 (sigma_ln 0.5, S = 10) at phi 0.5
                from uniform positions -- 20 iterations launched one by one
                (rcp_profile) with a periodic box, flat walls on every axis and
-               a ball container, and 3 oracle iterations of each."""
+               a ball container, in binary64 and in mixed precision, and 3
+               oracle iterations of each."""
     import oracle
     out = {}
     D0 = np.concatenate([np.full(160, 3.0), np.full(480, 1.5), np.full(800, 1.0)])
@@ -305,14 +306,17 @@ def bench_rows(rcp, torch, large: bool = False):
     xs = oracle.init_positions(0, D.size)
     rows = {}
     for name, walls, cont in (("periodic", 0, 0), ("walls_xyz", 7, 0), ("ball", 0, 1)):
-        p = rcp.Packing(D, box=1.0, seed=0, walls=walls, container=cont)
         with oracle.walls(walls, cont):
             k = oracle.kappa0(D, 1.0, 0.5)
-        p.set_positions(xs, k)
-        rcp.rcp_profile(p.h, 3)
-        ms_pair, ms_iter, n_pair = rcp.rcp_profile(p.h, 20)
-        ms_pair, ms_iter = ms_pair / max(n_pair, 1), ms_iter / 20.0
-        p.close()
+        timed = {}
+        for prec in (rcp.RCP_FP64, rcp.RCP_MIXED):
+            p = rcp.Packing(D, box=1.0, seed=0, walls=walls, container=cont, precision=prec)
+            p.set_positions(xs, k)
+            rcp.rcp_profile(p.h, 3)
+            ms_pair, ms_iter, n_pair = rcp.rcp_profile(p.h, 20)
+            timed[prec] = (ms_pair / max(n_pair, 1), ms_iter / 20.0)
+            p.close()
+        ms_pair, ms_iter = timed[rcp.RCP_FP64]
         xc = xs.copy()
         with oracle.walls(walls, cont):
             k0 = oracle.kappa0(D, 1.0, 0.05)
@@ -322,9 +326,11 @@ def bench_rows(rcp, torch, large: bool = False):
             oracle.sample_iterations(D, xc, k, 0.0, 1e-3 * k * dref, 1e-3 * k, 100.0 * (1e-3 * k0) * dref, 3,
                                      skin_s=0.02)
             dt = time.perf_counter() - t0
-        rows[name] = {"ms_pair": ms_pair, "ms_iter": ms_iter, "oracle_iters_per_s": 3.0 / dt}
+        rows[name] = {"ms_pair": ms_pair, "ms_iter": ms_iter, "oracle_iters_per_s": 3.0 / dt,
+                      "ms_pair_mixed": timed[rcp.RCP_MIXED][0], "ms_iter_mixed": timed[rcp.RCP_MIXED][1]}
     for name in ("walls_xyz", "ball"):
         rows[name]["pair_time_vs_periodic"] = rows[name]["ms_pair"] / rows["periodic"]["ms_pair"]
+        rows[name]["pair_time_vs_periodic_mixed"] = rows[name]["ms_pair_mixed"] / rows["periodic"]["ms_pair_mixed"]
     out["boundaries"] = {"workload": "lognormal-n2e5-s10 phi 0.5 uniform", **rows}
     # per-iteration cost of whole runs at small N, binary64 beside mixed: what
     # bounds the cascade's stages

@@ -103,8 +103,12 @@ typedef struct {
                                Eq. energy; shrink to contact also stops at the first
                                wall contact and placement keeps spheres off the
                                walls.  Positions on walled axes should stay within
-                               one box edge of the box.  Only the bits of the d
-                               axes; binary64 path only (0: periodic box) */
+                               one box edge of the box; in RCP_MIXED a bounded
+                               axis's fixed-point record spans [-L_a/2, 3 L_a/2)
+                               (a position outside saturates to its end) and the
+                               wall terms are taken in two-term binary32.  Only
+                               the bits of the d axes; either precision (0:
+                               periodic box) */
     int       container;    /* curved hard wall (Sec. II, Fig. 2): 0 none; 1 a ball
                                over every axis (a disk when d = 2); 2 a cylinder
                                about the z axis (d = 3).  Radius R = min L_a/2 over
@@ -114,7 +118,8 @@ typedef struct {
                                delta = 1 - h/rad as for a flat wall; kappa_0 and
                                phi use the container's volume.  Start from
                                placement = 1 (a uniform draw over the box leaves
-                               spheres outside).  Binary64 path only */
+                               spheres outside).  Either precision, the container's
+                               axes recorded in RCP_MIXED as walled axes are */
 } rcp_config;
 
 /* When rcp_run returns early. */
@@ -284,8 +289,7 @@ int rcp_dim(rcp_handle h);
  *   diameters: host [N] relative diameters D_i^0 of the mobile spheres;
  *   d, box, seed: as for rcp_create (the uniform draw covers all Nf + N
  *         indices; the frozen rows are then replaced by fixed_x);
- *   cfg: required, either precision (flat walls and containers remain
- *         binary64 only, as for rcp_create).
+ *   cfg: required, either precision, with or without walls or a container.
  * Pairs with a frozen sphere have d_ij = (F_i + kappa D_j^0)/2 (or (F_i +
  * F_j)/2), so dE/dkappa takes (mobile D^0)/2 from them; a frozen sphere's
  * gradient is zero and Adam does not move it; the growth term -mu kappa sum

@@ -551,9 +551,10 @@ int launch_iteration(rcp_ctx* h, int mode, cudaEvent_t* ev = nullptr)
     const unsigned int nb = pair_blocks(h);
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->cfg.precision == RCP_MIXED) {
-        // frozen spheres (a seated stage) take the kernel that tells their
-        // contact diameters apart; the rest the plain one
-        (h->c.nfrozen > 0 ? k_pair_mixed_fz : k_pair_mixed)<<<nb + h->c.long_blocks, RCP_PAIR_THREADS, 0, h->stream>>>(
+        // a bounded packing takes the kernel with the wall terms, frozen
+        // spheres (a seated stage) the one that tells their contact
+        // diameters apart, the rest the plain one
+        (h->c.bounded ? k_pair_mixed_wl : (h->c.nfrozen > 0 ? k_pair_mixed_fz : k_pair_mixed))<<<nb + h->c.long_blocks, RCP_PAIR_THREADS, 0, h->stream>>>(
             h->ctl, h->c, h->m32, h->v32, h->rA, h->rB, h->rowptr, h->col, h->long_rows, h->rb, h->part_e, h->part_k,
             mode, h->g);
     } else if (warp_rows(h)) {
@@ -864,9 +865,7 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     if (d != 2 && d != 3) return RCP_ERR_UNSUPPORTED;
     if (Nf >= (1LL << 31) || Nm >= (1LL << 31) - Nf) return RCP_ERR_ARG;
     if (cfg && (cfg->walls & ~((1 << d) - 1))) return RCP_ERR_ARG;   // one bit per axis of the caller
-    if (cfg && cfg->walls && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     if (cfg && (cfg->container < 0 || cfg->container > 2 || (cfg->container == 2 && d != 3))) return RCP_ERR_ARG;
-    if (cfg && cfg->container && cfg->precision != RCP_FP64) return RCP_ERR_UNSUPPORTED;
     const long long N = Nf + Nm;
     for (long long i = 0; i < Nf; ++i) {
         if (!(fixed_d[i] > 0.0) || !std::isfinite(fixed_d[i])) return RCP_ERR_ARG;
@@ -903,11 +902,25 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     c.nfrozen = Nf;
     c.Lmin = box[0];
     c.Lmax = box[0];
+    c.walls = h->cfg.walls;
+    c.container = h->cfg.container;
+    // the container: a ball over the caller's axes (a disk when d = 2) or a
+    // cylinder about z, radius min L_a / 2 over its axes, about the centre
+    c.caxes = c.container == 1 ? (1 << d) - 1 : (c.container == 2 ? 3 : 0);
+    c.bounded = c.walls | c.caxes;
     for (int a = 0; a < 3; ++a) {
         c.L[a] = box[a];
         c.halfL[a] = 0.5 * box[a];
-        c.qscale[a] = (float)(box[a] * 0x1.0p-32);
-        c.qinv[a] = (float)(0x1.0p32 / box[a]);
+        // a mixed record covers a periodic axis once (the integer wrap is the
+        // minimum image) and a bounded one twice over, from -L/2 (a sphere
+        // pushed past a wall stays representable)
+        const bool bnd = (c.bounded >> a) & 1;
+        c.qspan[a] = bnd ? 2.0 * box[a] : box[a];
+        c.qoff[a] = bnd ? -0.5 * box[a] : 0.0;
+        c.qo_hi[a] = (float)c.qoff[a];
+        c.qo_lo[a] = (float)(c.qoff[a] - (double)c.qo_hi[a]);
+        c.qscale[a] = (float)(c.qspan[a] * 0x1.0p-32);
+        c.qinv[a] = (float)(0x1.0p32 / c.qspan[a]);
         c.invL[a] = 1.0 / box[a];
         c.invLf[a] = (float)c.invL[a];
         {
@@ -915,11 +928,12 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
             if (std::frexp(box[a], &ex) == 0.5) c.pow2L |= 1 << a;
         }
         {
-            const double sc = box[a] * 0x1.0p-32;
+            const double sc = c.qspan[a] * 0x1.0p-32;
             c.qs_hi[a] = (float)sc;
             c.qs_lo[a] = (float)(sc - (double)c.qs_hi[a]);
         }
         c.Lf[a] = (float)box[a];
+        c.Llo[a] = (float)(box[a] - (double)c.Lf[a]);
         if (box[a] < c.Lmin) c.Lmin = box[a];
         if (box[a] > c.Lmax) c.Lmax = box[a];
     }
@@ -927,15 +941,11 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     // mixed pre-test leaves out (below one unit per axis, sqrt(3) in all)
     c.qmargin = 2.0f * std::max(c.qscale[0], std::max(c.qscale[1], c.qscale[2]));
     c.V = d == 2 ? box[0] * box[1] : (box[0] * box[1]) * box[2];   // area when d = 2
-    c.walls = h->cfg.walls;
-    c.container = h->cfg.container;
-    // the container: a ball over the caller's axes (a disk when d = 2) or a
-    // cylinder about z, radius min L_a / 2 over its axes, about the centre
-    c.caxes = c.container == 1 ? (1 << d) - 1 : (c.container == 2 ? 3 : 0);
-    c.bounded = c.walls | c.caxes;
     c.Rc = INFINITY;
     for (int a = 0; a < d; ++a)
         if (((c.caxes >> a) & 1) && 0.5 * box[a] < c.Rc) c.Rc = 0.5 * box[a];
+    c.Rc_hi = std::isfinite(c.Rc) ? (float)c.Rc : 0.0f;
+    c.Rc_lo = std::isfinite(c.Rc) ? (float)(c.Rc - (double)c.Rc_hi) : 0.0f;
     if (c.container == 1) c.Vs = d == 2 ? (RCP_PI * c.Rc) * c.Rc : (((4.0 / 3.0) * RCP_PI) * ((c.Rc * c.Rc) * c.Rc));
     else if (c.container == 2) c.Vs = ((RCP_PI * c.Rc) * c.Rc) * box[2];
     else c.Vs = c.V;
@@ -1782,6 +1792,7 @@ struct rcp_batch_ctx {
     bool tuned = false;
     int long_row = RCP_LONG_ROW;
     bool any_frozen = false;   // some packing holds frozen spheres
+    bool any_bounded = false;  // some packing has walls or a container
     std::vector<cudaEvent_t> ev;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     long long launches = 0;
@@ -1820,10 +1831,16 @@ rcp_status batch_refresh(rcp_batch_ctx* b)
     return RCP_OK;
 }
 
+// The batched mixed pair kernel for what the batch's packings hold.
+decltype(&k_pair_mixed_batch) mixed_batch_kernel(const rcp_batch_ctx* b)
+{
+    return b->any_bounded ? k_pair_mixed_batch_wl : (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch);
+}
+
 void batch_iteration(rcp_batch_ctx* b, int mode)
 {
     if (b->precision == RCP_MIXED)
-        (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
+        mixed_batch_kernel(b)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
     else
         k_pair64_batch<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B, mode);
     if (b->precision == RCP_MIXED)
@@ -1914,11 +1931,11 @@ rcp_status batch_autotune_rows(rcp_batch_ctx* b)
         for (rcp_ctx* h : b->hs) BK(cudaStreamSynchronize(h->stream));
         BKS(b->hs[0], batch_refresh(b));
         for (int w = 0; w < 2; ++w)
-            (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
+            mixed_batch_kernel(b)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
                                                                                     RCP_MODE_GRAD);
         BK(cudaEventRecord(b->t0, b->stream));
         for (int w = 0; w < 5; ++w)
-            (b->any_frozen ? k_pair_mixed_batch_fz : k_pair_mixed_batch)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
+            mixed_batch_kernel(b)<<<b->total_blocks, RCP_PAIR_THREADS, 0, b->stream>>>(b->d_packs, b->d_bstart, b->B,
                                                                                     RCP_MODE_GRAD);
         BK(cudaEventRecord(b->t1, b->stream));
         BK(cudaEventSynchronize(b->t1));
@@ -1976,6 +1993,7 @@ rcp_status rcp_batch_create(rcp_handle* hs, int B, int autotune, rcp_batch* out)
             blocks += q.nblocks;
             b->hs.push_back(h);
             if (h->c.nfrozen > 0) b->any_frozen = true;
+            if (h->c.bounded) b->any_bounded = true;
             h->stream = h->own_stream;
         }
         b->total_blocks = blocks;

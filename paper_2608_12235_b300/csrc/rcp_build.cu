@@ -65,11 +65,23 @@ __global__ void __launch_bounds__(256) k_rho(RcpCtl* ctl, RcpConst c, const doub
 }
 
 // Mixed path: the same radii and binary32 copy from the fixed-point records,
-// with no binary64 view of the positions: u_a = fl32(q_a) 2^-32 drops the
-// remainder (below one unit, 2^-32) and rounds q_a to 24 bits, so it is
-// within 2^-25 + 2^-32 of x_a / L_a -- the prefilter's error budget for
-// fl32(x_a / L_a) (2^-25) grows by under 1 %, far inside its margins.
-// rho_i from D_i^0 exactly as k_rho forms it.
+// with no binary64 view of the positions.  On a periodic axis u_a =
+// fl32(q_a) 2^-32 drops the remainder (below one unit, 2^-32) and rounds q_a
+// to 24 bits, so it is within 2^-25 + 2^-32 of x_a / L_a -- the prefilter's
+// error budget for fl32(x_a / L_a) (2^-25) grows by under 1 %, far inside
+// its margins.  A bounded axis (its record spans [-L/2, 3L/2)) takes
+// fl32(x_a / L_a) of the binary64 coordinate, as k_rho does.  rho_i from
+// D_i^0 exactly as k_rho forms it.
+__device__ __forceinline__ float unit_coord(const MixRec& r, const RcpConst& c, int a)
+{
+    const int q = a == 0 ? r.q.x : (a == 1 ? r.q.y : r.q.z);
+    if ((c.bounded >> a) & 1) {
+        const float l = a == 0 ? r.l.x : (a == 1 ? r.l.y : r.l.z);
+        return (float)(from_fixed(q, l, c, a) * c.invL[a]);
+    }
+    return __uint2float_rn((unsigned int)q) * 0x1.0p-32f;
+}
+
 __global__ void __launch_bounds__(256) k_rho_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB,
                                                    const double* D0, double* rho, float4* xf)
 {
@@ -77,12 +89,10 @@ __global__ void __launch_bounds__(256) k_rho_mixed(RcpCtl* ctl, RcpConst c, cons
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0.0;
     if (i < c.N) {
-        const int4 q = reinterpret_cast<const int4*>(ctl->parity ? rB : rA)[2 * i];
+        const MixRec rec = (ctl->parity ? rB : rA)[i];
         r = size_at(D0[i], ctl->kappa_b) * (0.5 + c.skin_s) + ctl->sigma0;
         rho[i] = r;
-        xf[i] = make_float4(__uint2float_rn((unsigned int)q.x) * 0x1.0p-32f,
-                            __uint2float_rn((unsigned int)q.y) * 0x1.0p-32f,
-                            __uint2float_rn((unsigned int)q.z) * 0x1.0p-32f, (float)r);
+        xf[i] = make_float4(unit_coord(rec, c, 0), unit_coord(rec, c, 1), unit_coord(rec, c, 2), (float)r);
     }
     for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r;
@@ -262,10 +272,19 @@ __global__ void k_cell_key(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const
 // Mixed path: the cell of a record from its integer part alone.  With n = 2^b
 // cells per axis, floor((q + l) 2^-32 n) = q >> (32 - b) because l < 1: the
 // same cell as floor(fl(x/L) n) for the binary64 position the record was made
-// from (q = floor(fl(x/L) 2^32)), in integer arithmetic.
-__device__ __forceinline__ unsigned int cell_q(int q, unsigned int n)
+// from (q = floor(fl(x/L) 2^32)), in integer arithmetic.  On a bounded axis
+// the record spans [-L/2, 3L/2): x/L = (q + l) 2^-31 - 1/2, so the cell is
+// (q >> (31 - b)) - n/2, clamped to the grid as cell_of clamps it (a sphere
+// past a wall stays in the edge cell; the search's windows carry margins
+// wider than the rounding at a cell edge).
+__device__ __forceinline__ unsigned int cell_q(int q, unsigned int n, bool bounded)
 {
-    return n <= 1u ? 0u : (unsigned int)q >> (32 - (31 - __clz(n)));
+    if (n <= 1u) return 0u;
+    const int b = 31 - __clz(n);
+    if (!bounded) return (unsigned int)q >> (32 - b);
+    int v = (int)((unsigned int)q >> (31 - b)) - (int)(n >> 1);
+    v = v < 0 ? 0 : (v > (int)n - 1 ? (int)n - 1 : v);
+    return (unsigned int)v;
 }
 
 __global__ void k_cell_key_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const MixRec* rB, const int* lvl,
@@ -275,8 +294,9 @@ __global__ void k_cell_key_mixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, cons
     if (i >= c.N) return;
     const int4 q = reinterpret_cast<const int4*>(ctl->parity ? rB : rA)[2 * i];
     const int k = lvl[i];
-    key[i] = pack_key((unsigned int)k, cell_q(q.z, (unsigned int)ctl->ng[k][2]), cell_q(q.y, (unsigned int)ctl->ng[k][1]),
-                      cell_q(q.x, (unsigned int)ctl->ng[k][0]));
+    key[i] = pack_key((unsigned int)k, cell_q(q.z, (unsigned int)ctl->ng[k][2], (c.bounded >> 2) & 1),
+                      cell_q(q.y, (unsigned int)ctl->ng[k][1], (c.bounded >> 1) & 1),
+                      cell_q(q.x, (unsigned int)ctl->ng[k][0], c.bounded & 1));
 }
 
 // Exclusive scan, 4096 items per block (1024 threads x 4); block totals are
@@ -452,8 +472,8 @@ __device__ __forceinline__ uint2 window_cell(const uint2* ck, const SearchWin& w
 // binary64 one.
 __device__ __forceinline__ double4_32a rec_position(const MixRec& r, const RcpConst& c)
 {
-    return make_double4_32a(from_fixed(r.q.x, r.l.x, c.L[0]), from_fixed(r.q.y, r.l.y, c.L[1]),
-                            from_fixed(r.q.z, r.l.z, c.L[2]), 0.0);
+    return make_double4_32a(from_fixed(r.q.x, r.l.x, c, 0), from_fixed(r.q.y, r.l.y, c, 1),
+                            from_fixed(r.q.z, r.l.z, c, 2), 0.0);
 }
 
 // Candidate t (a sorted position) against sphere i: its index j when the

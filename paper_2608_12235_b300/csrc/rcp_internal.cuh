@@ -97,25 +97,30 @@ struct RcpConst {
     double Lmin, Lmax;
     double stop_margin;     // 0: binary64 overlaps; > 0: relative band that triggers a binary64 check
     double cell_occ;        // target spheres per cell of a class grid
-    float qscale[3];        // L_a / 2^32: fixed-point unit of axis a
-    float qinv[3];          // 2^32 / L_a
+    float qscale[3];        // qspan_a / 2^32: fixed-point unit of axis a
+    float qinv[3];          // 2^32 / qspan_a
+    double qspan[3];        // length a record's axis covers: L_a (periodic), 2 L_a (bounded)
+    double qoff[3];         // coordinate of q = 0: 0 (periodic), -L_a / 2 (bounded)
+    float qo_hi[3], qo_lo[3];  // qoff as an unevaluated binary32 sum
+    float Llo[3];           // L_a - Lf[a]
     double invL[3];         // 1 / L_a
     float invLf[3];         // fl32(1 / L_a)
     int pow2L;              // bit a: L_a is a power of two, so x / L_a == x * (1 / L_a) exactly
     float Lf[3];            // L_a in binary32
-    float qs_hi[3], qs_lo[3];  // L_a 2^-32 as an unevaluated binary32 sum
+    float qs_hi[3], qs_lo[3];  // qspan_a 2^-32 as an unevaluated binary32 sum
     float qmargin;             // 2 max_a qscale[a]: absolute margin of the mixed pre-test
     unsigned int canon;        // 1: binary64 path (canonical sums); 0: mixed path
     int dim;                   // the caller's dimension: 3, or 2 (disks held in the plane z = L_z / 2)
     unsigned int long_row;     // rows longer than this get a warp (mixed; binary64 when long64)
     int long64;                // binary64 packing above RCP_WARP_ROW_MAX_N: long rows by k_pair64_long
     unsigned int long_blocks;  // blocks of the mixed pair kernel that serve long rows
-    long long nfrozen;         // frozen spheres (binary64 path only; 0 otherwise)
-    int walls;                 // bit a: flat walls at 0 and L_a bound axis a (binary64 path only)
+    long long nfrozen;         // frozen spheres
+    int walls;                 // bit a: flat walls at 0 and L_a bound axis a
     int container;             // curved wall: 0 none, 1 ball (disk when d = 2), 2 cylinder about z
     int caxes;                 // the container's axes (bit a)
     int bounded;               // axes without minimum image or wrap: flat walls and the container's
     double Rc;                 // container radius: min L_a / 2 over its axes (centre L / 2)
+    float Rc_hi, Rc_lo;        // Rc as an unevaluated binary32 sum (mixed wall terms)
     double Vs;                 // volume the spheres fill (kappa_0, phi): the container's, else V
 };
 
@@ -188,11 +193,14 @@ __device__ __forceinline__ void warp_sum2(float& s, float& c)
 }
 
 // ---- small helpers ----
-// Binary64 coordinate of a fixed-point record axis: (q + l) L 2^-32, in [0, L).
-__device__ __forceinline__ double from_fixed(int q, float l, double L)
+// Binary64 coordinate of a fixed-point record axis: (q + l) qspan 2^-32 +
+// qoff; a periodic axis (qoff = 0, qspan = L) wraps into [0, L), a bounded
+// one (qspan = 2 L, qoff = -L/2: room on both sides of the walls) does not.
+__device__ __forceinline__ double from_fixed(int q, float l, const RcpConst& c, int a)
 {
-    double v = ((double)(unsigned int)q + (double)l) * (L * 0x1.0p-32);
-    if (v >= L) v = v - L;
+    double v = ((double)(unsigned int)q + (double)l) * (c.qspan[a] * 0x1.0p-32);
+    if ((c.bounded >> a) & 1) return v + c.qoff[a];
+    if (v >= c.L[a]) v = v - c.L[a];
     return v;
 }
 
@@ -302,6 +310,7 @@ __global__ void k_pair64_warp(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_
 __global__ void k_kappa_step_batch(const PackDev* P, int mode);
 __global__ void k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode);
 __global__ void k_pair_mixed_batch_fz(const PackDev* P, const unsigned int* bstart, int B, int mode);
+__global__ void k_pair_mixed_batch_wl(const PackDev* P, const unsigned int* bstart, int B, int mode);
 __global__ void k_tree_pass2(const double* ina, const double* inb, long long n, double* outa, double* outb);
 __global__ void k_adam64(RcpCtl* ctl, RcpConst c, double4_32a* xA, double4_32a* xB, double* m, double* v,
                          const double* g, const double4_32a* xb, double eta_x);
@@ -320,6 +329,10 @@ __global__ void k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec
 __global__ void k_pair_mixed_fz(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB,
                                 const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
                                 const MixRec* rb, double* part_e, double* part_k, int mode, double* g_out);
+__global__ void k_pair_mixed_wl(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB,
+                                const unsigned int* rowptr, const unsigned int* col, const unsigned int* long_rows,
+                                const MixRec* rb, double* part_e, double* part_k, int mode, double* g_out);
+// in rcp_kernels.cu, beside the binary64 wall terms
 __global__ void k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB,
                              const unsigned int* rowptr, const unsigned int* col);
 __global__ void k_verify_final(RcpCtl* ctl, RcpConst c);

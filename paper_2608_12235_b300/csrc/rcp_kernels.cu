@@ -117,6 +117,42 @@ __device__ __forceinline__ void wall_terms(const RcpConst& c, double kappa, cons
     }
 }
 
+// Binary64 maximum overlap of the current binary64 positions over the
+// listed pairs and the walls, the pairs in k_pair64's arithmetic (confirms a
+// mixed path's binary32 stop candidate).
+__global__ void __launch_bounds__(RCP_PAIR_THREADS)
+k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const unsigned int* rowptr,
+             const unsigned int* col)
+{
+    const double4_32a* x = ctl->parity ? xB : xA;
+    const double kappa = ctl->kappa;
+    const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
+    double md = 0.0;
+    if (i < c.N) {
+        const double4_32a xi = x[i];
+        for (unsigned int t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+            const unsigned int j = col[t];
+            if ((long long)j < i) continue;
+            const double4_32a xj = x[j];
+            const double dx = axis_diff(c, 0, xi.x - xj.x), dy = axis_diff(c, 1, xi.y - xj.y),
+                         dz = axis_diff(c, 2, xi.z - xj.z);
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double dd = (xi.w > 0.0 && xj.w > 0.0) ? kappa * (0.5 * (xi.w + xj.w))
+                                                         : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
+            if (r2 > (dd * dd) * RCP_NO_OVERLAP_MARGIN) continue;   // certainly delta <= 0
+            const double r = sqrt(r2);
+            const double delta = 1.0 - r / dd;
+            if (delta > md) md = delta;
+        }
+        if (c.walls | c.container) {
+            double g0 = 0.0, g1 = 0.0, g2 = 0.0, e = 0.0, k = 0.0;
+            wall_terms(c, kappa, xi, g0, g1, g2, e, k, md);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_down_sync(0xffffffffu, md, o));
+    if ((threadIdx.x & 31) == 0 && md > 0.0) atomicMax(&ctl->md64_bits, dbits(md));
+}
+
 __global__ void k_init_positions(unsigned long long seed, long long N, RcpConst c, const double* D0, double4_32a* x)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

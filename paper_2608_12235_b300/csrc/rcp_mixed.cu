@@ -17,20 +17,22 @@
 // needs them (neighbour build, stopping-test confirmation, shrink, export).
 #include "rcp_internal.cuh"
 
-__device__ __forceinline__ void to_fixed(double x, double L, int& q, float& l)
+// Axis a of a record from a binary64 coordinate: t = (x - qoff) / qspan 2^32,
+// q = floor(t) (mod 2^32: a periodic x == L gives 0), l = t - q.
+__device__ __forceinline__ void to_fixed(double x, const RcpConst& c, int a, int& q, float& l)
 {
-    double t = (x / L) * 4294967296.0;
+    double t = ((x - c.qoff[a]) / c.qspan[a]) * 4294967296.0;
     double f = floor(t);
-    q = (int)(unsigned int)(unsigned long long)f;  // x == L would give 2^32, i.e. 0
+    q = (int)(unsigned int)(unsigned long long)f;
     l = (float)(t - f);
 }
 
 __device__ __forceinline__ MixRec make_rec(double4_32a p, const RcpConst& c)
 {
     MixRec r;
-    to_fixed(p.x, c.L[0], r.q.x, r.l.x);
-    to_fixed(p.y, c.L[1], r.q.y, r.l.y);
-    to_fixed(p.z, c.L[2], r.q.z, r.l.z);
+    to_fixed(p.x, c, 0, r.q.x, r.l.x);
+    to_fixed(p.y, c, 1, r.q.y, r.l.y);
+    to_fixed(p.z, c, 2, r.q.z, r.l.z);
     const float dh = (float)p.w;
     r.q.w = __float_as_int(dh);
     r.l.w = (float)(p.w - (double)dh);
@@ -69,8 +71,8 @@ __global__ void k_from_fixed(RcpCtl* ctl, RcpConst c, const MixRec* rA, const Mi
     const int parity = ctl->parity;
     const MixRec r = (parity ? rB : rA)[i];
     double4_32a* x = parity ? xB : xA;
-    x[i] = make_double4_32a(from_fixed(r.q.x, r.l.x, c.L[0]), from_fixed(r.q.y, r.l.y, c.L[1]),
-                            from_fixed(r.q.z, r.l.z, c.L[2]), D0[i]);
+    x[i] = make_double4_32a(from_fixed(r.q.x, r.l.x, c, 0), from_fixed(r.q.y, r.l.y, c, 1),
+                            from_fixed(r.q.z, r.l.z, c, 2), D0[i]);
 }
 
 // Snapshot of the current records at a neighbour build.
@@ -389,6 +391,121 @@ __device__ __forceinline__ float warp_sum(float s)
 }
 
 
+// Coordinate of a record along axis a as an unevaluated binary32 sum
+// (length units): qoff + (q + l) qspan 2^-32, the integer part split into its
+// upper 24 and low 8 bits (each exact), so exact to ~2^-44 of the span.
+__device__ __forceinline__ void rec_pos2(int qv, float l, const RcpConst& c, int a, float& hi, float& lo)
+{
+    const unsigned int q = (unsigned int)qv;
+    const float hq = (float)(q & 0xffffff00u), eq = (float)(q & 0xffu);
+    float s1, e1, xh, t;
+    two_sum(eq, l, s1, e1);
+    two_sum(hq, s1, xh, t);
+    const float xl = t + e1;
+    float p, pe;
+    two_prod(xh, c.qs_hi[a], p, pe);
+    const float l1 = pe + (xh * c.qs_lo[a] + xl * c.qs_hi[a]);
+    float s2, e2;
+    two_sum(p, c.qo_hi[a], s2, e2);
+    hi = s2;
+    lo = e2 + (l1 + c.qo_lo[a]);
+}
+
+// One wall contact of a sphere of radius rad = rh + rl at clearance h = hh +
+// hl: delta = (rad - h) / rad with the difference taken in two-term
+// arithmetic (no cancellation near contact); energy eps/2 delta^2, and for a
+// mobile sphere the force eps delta / rad (returned) and the kappa term eps
+// delta (1 - delta) / kappa, 1 - delta taken as h / rad (d delta / d kappa =
+// (h / rad) / kappa; no cancellation where the centre sits on the wall and
+// delta is near 1).  Returns false when the sphere clears the wall.
+template <bool FZ>
+__device__ __forceinline__ bool wall_contact(float hh, float hl, float rh, float rl, bool mob, const MixScalars& S,
+                                             float& es, float& ec, float& ks, float& kc, float& md, float& f)
+{
+    float nh, ne;
+    two_sum(rh, -hh, nh, ne);
+    const float n = nh + (ne + (rl - hl));
+    if (!(n > 0.0f)) return false;
+    const float delta = __fdividef(n, rh);
+    acc2(es, ec, (0.5f * S.eps) * (delta * delta));
+    f = 0.0f;
+    if (!FZ || mob) {
+        f = __fdividef(S.eps * delta, rh);
+        acc2(ks, kc, ((S.eps * delta) * __fdividef(hh + hl, rh)) * S.rkappa);
+    }
+    md = fmaxf(md, delta);
+    return true;
+}
+
+// A row's wall terms after its pairs (Sec. II boundaries): the flat walls at
+// 0 and L_a of every walled axis (h = x_a, then h = L_a - x_a), then the
+// curved container, h = R - |x - centre| over its axes (d h / d x_a =
+// -(x_a - c_a) / |x - c|).  Positions, clearances and distances in two-term
+// binary32, so a contact within 1e-8 of the radius still resolves.  A frozen
+// row takes the energy and the overlap but no force and no kappa term.
+template <bool FZ>
+__device__ __forceinline__ void wall_terms32(const RcpConst& c, const MixScalars& S, const MixRec& ri, float& g0,
+                                             float& c0, float& g1, float& c1, float& g2, float& c2, float& es,
+                                             float& ec, float& ks, float& kc, float& md)
+{
+    bool mob = true;
+    if constexpr (FZ) mob = rec_D(ri) > 0.0f;
+    float rh, rl;
+    contact_diameter2(ri, S, rh, rl);
+    rh *= 0.5f;
+    rl *= 0.5f;
+    const int qa[3] = {ri.q.x, ri.q.y, ri.q.z};
+    const float la[3] = {ri.l.x, ri.l.y, ri.l.z};
+    for (int a = 0; a < 3; ++a) {
+        if (!((c.walls >> a) & 1)) continue;
+        float xh, xl;
+        rec_pos2(qa[a], la[a], c, a, xh, xl);
+        float& g = a == 0 ? g0 : (a == 1 ? g1 : g2);
+        float& gc = a == 0 ? c0 : (a == 1 ? c1 : c2);
+        float f;
+        if (wall_contact<FZ>(xh, xl, rh, rl, mob, S, es, ec, ks, kc, md, f) && f != 0.0f) acc2(g, gc, -f);
+        float s, e;
+        two_sum(c.Lf[a], -xh, s, e);
+        if (wall_contact<FZ>(s, e + (c.Llo[a] - xl), rh, rl, mob, S, es, ec, ks, kc, md, f) && f != 0.0f)
+            acc2(g, gc, f);
+    }
+    if (c.container) {
+        float oh[3] = {0.f, 0.f, 0.f};
+        float d2h = 0.0f, d2l = 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            if (!((c.caxes >> a) & 1)) continue;
+            float xh, xl;
+            rec_pos2(qa[a], la[a], c, a, xh, xl);
+            // offset from the centre L_a / 2 (exact halves of Lf and Llo)
+            float s, e;
+            two_sum(xh, -0.5f * c.Lf[a], s, e);
+            const float ol = e + (xl - 0.5f * c.Llo[a]);
+            float oh2, ol2;
+            two_sum(s, ol, oh2, ol2);
+            oh[a] = oh2;
+            float p, pe;
+            two_prod(oh2, oh2, p, pe);
+            float t, te;
+            two_sum(d2h, p, t, te);
+            d2h = t;
+            d2l = d2l + (te + (pe + 2.0f * oh2 * ol2));
+        }
+        // |x - c| = sqrt(d2) as hi + lo (one Newton correction)
+        const float dh = sqrtf(d2h);
+        const float dl = dh > 0.0f ? __fdividef(__fmaf_rn(-dh, dh, d2h) + d2l, 2.0f * dh) : 0.0f;
+        // h = R - |x - c|
+        float s, e;
+        two_sum(c.Rc_hi, -dh, s, e);
+        float f;
+        if (wall_contact<FZ>(s, e + (c.Rc_lo - dl), rh, rl, mob, S, es, ec, ks, kc, md, f) && f != 0.0f && dh > 0.0f) {
+            const float fr = __fdividef(f, dh);
+            if (c.caxes & 1) acc2(g0, c0, fr * oh[0]);
+            if (c.caxes & 2) acc2(g1, c1, fr * oh[1]);
+            if (c.caxes & 4) acc2(g2, c2, fr * oh[2]);
+        }
+    }
+}
+
 // The pair kernel of the mixed path.  Listed entries far outnumber
 // overlapping pairs (about 3 % in the dense packings at S = 5e5, where most
 // small spheres rattle in the voids of the large ones), so every row is taken
@@ -422,7 +539,8 @@ __device__ __forceinline__ void prefetch_row(const float* m, const float* v, con
 
 __device__ __forceinline__ unsigned int lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
-template <bool FZ>
+// WL: the packing has flat walls or a container (wall terms per row).
+template <bool FZ, bool WL>
 __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, float* m, float* v, MixRec* rA,
                                                 MixRec* rB, const unsigned int* rowptr, const unsigned int* col,
                                                 const unsigned int* long_rows, const MixRec* rb, double* part_e, double* part_k, int mode,
@@ -484,7 +602,16 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
             g0 = warp_sum(g0 + c0);
             g1 = warp_sum(g1 + c1);
             g2 = warp_sum(g2 + c2);
-            if (lane == 0) bud = fminf(bud, row_epilogue<FZ>(ctl, c, S, i, rin[i], g0, g1, g2, m, v, rout, rb, mode, g_out));
+            if (lane == 0) {
+                if constexpr (WL) {
+                    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+                    wall_terms32<FZ>(c, S, rin[i], g0, e0, g1, e1, g2, e2, es, ec, ks, kc, md);
+                    g0 += e0;
+                    g1 += e1;
+                    g2 += e2;
+                }
+                bud = fminf(bud, row_epilogue<FZ>(ctl, c, S, i, rin[i], g0, g1, g2, m, v, rout, rb, mode, g_out));
+            }
         }
     } else {
         // one thread per row
@@ -530,6 +657,7 @@ __device__ __forceinline__ void pair_mixed_body(RcpCtl* ctl, const RcpConst& c, 
                     acc2(g1, c1, a1);
                     acc2(g2, c2, a2);
                 }
+                if constexpr (WL) wall_terms32<FZ>(c, S, ri, g0, c0, g1, c1, g2, c2, es, ec, ks, kc, md);
                 bud = row_epilogue<FZ>(ctl, c, S, i, ri, g0 + c0, g1 + c1, g2 + c2, m, v, rout, rb, mode, g_out);
             }
         }
@@ -588,8 +716,8 @@ k_pair_mixed(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB
              const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
              double* part_k, int mode, double* g_out)
 {
-    pair_mixed_body<false>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
-                           blockIdx.x);
+    pair_mixed_body<false, false>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
+                                  blockIdx.x);
 }
 
 // The same for a packing that holds frozen spheres (seated stages of the
@@ -599,8 +727,19 @@ k_pair_mixed_fz(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec*
                 const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
                 double* part_k, int mode, double* g_out)
 {
-    pair_mixed_body<true>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
-                          blockIdx.x);
+    pair_mixed_body<true, false>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
+                                 blockIdx.x);
+}
+
+// The same for a packing bounded by flat walls or a container (Sec. II),
+// frozen spheres or not.
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed_wl(RcpCtl* ctl, RcpConst c, float* m, float* v, MixRec* rA, MixRec* rB, const unsigned int* rowptr,
+                const unsigned int* col, const unsigned int* long_rows, const MixRec* rb, double* part_e,
+                double* part_k, int mode, double* g_out)
+{
+    pair_mixed_body<true, true>(ctl, c, m, v, rA, rB, rowptr, col, long_rows, rb, part_e, part_k, mode, g_out,
+                                blockIdx.x);
 }
 
 __device__ __forceinline__ int batch_pack_m(const unsigned int* bstart, int B, unsigned int block)
@@ -616,59 +755,32 @@ __device__ __forceinline__ int batch_pack_m(const unsigned int* bstart, int B, u
 
 // Batched mixed pair kernel: block b serves packing p with local block
 // b - bstart[p], so each packing computes exactly what its own launch would.
-// FZ: some packing of the batch holds frozen spheres.
-template <bool FZ>
+// FZ: some packing of the batch holds frozen spheres; WL: walls or a container.
+template <bool FZ, bool WL>
 __device__ __forceinline__ void pair_mixed_batch_body(const PackDev* P, const unsigned int* bstart, int B, int mode)
 {
     const int p = batch_pack_m(bstart, B, blockIdx.x);
     const PackDev& q = P[p];
-    pair_mixed_body<FZ>(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e,
+    pair_mixed_body<FZ, WL>(q.ctl, q.c, q.m32, q.v32, q.rA, q.rB, q.rowptr, q.col, q.long_rows, q.rb, q.part_e,
                         q.part_k, mode, q.g, blockIdx.x - bstart[p]);
 }
 
 __global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
 k_pair_mixed_batch(const PackDev* P, const unsigned int* bstart, int B, int mode)
 {
-    pair_mixed_batch_body<false>(P, bstart, B, mode);
+    pair_mixed_batch_body<false, false>(P, bstart, B, mode);
 }
 
 __global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
 k_pair_mixed_batch_fz(const PackDev* P, const unsigned int* bstart, int B, int mode)
 {
-    pair_mixed_batch_body<true>(P, bstart, B, mode);
+    pair_mixed_batch_body<true, false>(P, bstart, B, mode);
 }
 
-// Binary64 maximum overlap over the listed pairs of the current binary64
-// positions, same arithmetic as k_pair64 (confirms a binary32 stop candidate).
-__global__ void __launch_bounds__(RCP_PAIR_THREADS)
-k_maxdelta64(RcpCtl* ctl, RcpConst c, const double4_32a* xA, const double4_32a* xB, const unsigned int* rowptr,
-             const unsigned int* col)
+__global__ void __launch_bounds__(RCP_PAIR_THREADS, RCP_MIX_MINB)
+k_pair_mixed_batch_wl(const PackDev* P, const unsigned int* bstart, int B, int mode)
 {
-    const double4_32a* x = ctl->parity ? xB : xA;
-    const double kappa = ctl->kappa;
-    const long long i = (long long)blockIdx.x * RCP_PAIR_THREADS + threadIdx.x;
-    double md = 0.0;
-    if (i < c.N) {
-        const double4_32a xi = x[i];
-        for (unsigned int t = rowptr[i]; t < rowptr[i + 1]; ++t) {
-            const unsigned int j = col[t];
-            if ((long long)j < i) continue;
-            const double4_32a xj = x[j];
-            double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-            if (dx > c.halfL[0]) dx = dx - c.L[0]; else if (dx < -c.halfL[0]) dx = dx + c.L[0];
-            if (dy > c.halfL[1]) dy = dy - c.L[1]; else if (dy < -c.halfL[1]) dy = dy + c.L[1];
-            if (dz > c.halfL[2]) dz = dz - c.L[2]; else if (dz < -c.halfL[2]) dz = dz + c.L[2];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double dd = (xi.w > 0.0 && xj.w > 0.0) ? kappa * (0.5 * (xi.w + xj.w))
-                                                         : 0.5 * (size_at(xi.w, kappa) + size_at(xj.w, kappa));
-            if (r2 > (dd * dd) * RCP_NO_OVERLAP_MARGIN) continue;   // certainly delta <= 0
-            const double r = sqrt(r2);
-            const double delta = 1.0 - r / dd;
-            if (delta > md) md = delta;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_down_sync(0xffffffffu, md, o));
-    if ((threadIdx.x & 31) == 0 && md > 0.0) atomicMax(&ctl->md64_bits, dbits(md));
+    pair_mixed_batch_body<true, true>(P, bstart, B, mode);
 }
 
 // Standalone Adam step in mixed precision (rcp_adam_step): binary32 moments

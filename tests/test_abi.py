@@ -56,10 +56,9 @@ def test_create_rejects_bad_input_before_touching_the_gpu(lib):
 def test_seated_and_cascade_reject_bad_input_before_touching_the_gpu(lib):
     from paper_2608_12235_b300 import rcp
     import numpy as np
-    mixed_walls = rcp.rcp_config_default(precision=rcp.RCP_MIXED, walls=1)
-    with pytest.raises(rcp.RcpError) as e:   # frozen spheres in either precision, walls binary64 only
-        rcp.rcp_create_seated([1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0, mixed_walls)
-    assert e.value.status == 9
+    with pytest.raises(rcp.RcpError) as e:   # one wall bit per axis of the caller
+        rcp.rcp_create_seated([1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0, rcp.rcp_config_default(walls=8))
+    assert e.value.status == 1
     with pytest.raises(rcp.RcpError) as e:   # a frozen diameter must be positive
         rcp.rcp_create_seated([-1.0], [[0.5, 0.5, 0.5]], [1.0], 1.0, 0)
     assert e.value.status == 1
@@ -69,17 +68,17 @@ def test_seated_and_cascade_reject_bad_input_before_touching_the_gpu(lib):
     with pytest.raises(rcp.RcpError) as e:   # class 1 is empty
         rcp.rcp_cascade([1.0, 1.0], [0, 2])
     assert e.value.status == 1
-    with pytest.raises(rcp.RcpError) as e:   # walls: binary64 only, whatever the call
-        rcp.rcp_cascade([1.0, 1.0], [0, 1], cfg=mixed_walls)
-    assert e.value.status == 9
+    with pytest.raises(rcp.RcpError) as e:   # no such container, whatever the call
+        rcp.rcp_cascade([1.0, 1.0], [0, 1], cfg=rcp.rcp_config_default(container=3, precision=rcp.RCP_MIXED))
+    assert e.value.status == 1
 
 
 def test_walls_are_checked_before_touching_the_gpu(lib):
     from paper_2608_12235_b300 import rcp
     import numpy as np
-    with pytest.raises(rcp.RcpError) as e:   # walls: binary64 path only
-        rcp.rcp_create(np.ones(4), 1.0, 0, rcp.rcp_config_default(precision=rcp.RCP_MIXED, walls=1))
-    assert e.value.status == 9
+    with pytest.raises(rcp.RcpError) as e:   # one bit per axis, either precision
+        rcp.rcp_create(np.ones(4), 1.0, 0, rcp.rcp_config_default(precision=rcp.RCP_MIXED, walls=8))
+    assert e.value.status == 1
     with pytest.raises(rcp.RcpError) as e:   # no z axis when d = 2
         rcp.rcp_create(np.ones(4), 1.0, 0, rcp.rcp_config_default(walls=4), d=2)
     assert e.value.status == 1
@@ -90,7 +89,7 @@ def test_container_is_checked_before_touching_the_gpu(lib):
     import numpy as np
     for cfg, d, want in [(rcp.rcp_config_default(container=3), 3, 1),
                          (rcp.rcp_config_default(container=2), 2, 1),   # a cylinder needs z
-                         (rcp.rcp_config_default(container=1, precision=rcp.RCP_MIXED), 3, 9)]:
+                         (rcp.rcp_config_default(container=-1, precision=rcp.RCP_MIXED), 3, 1)]:
         with pytest.raises(rcp.RcpError) as e:
             rcp.rcp_create(np.ones(4), 1.0, 0, cfg, d=d)
         assert e.value.status == want

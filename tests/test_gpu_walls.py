@@ -1,7 +1,9 @@
-"""Flat hard walls (Sec. II): the binary64 CUDA path against the oracle, bit
-for bit, on the same seeded inputs -- lists with spheres on and beyond the
-walls, energy and gradient, placement, whole runs in d = 3 and d = 2, and a
-seated stage inside walls.
+"""Flat hard walls and the curved container (Sec. II): the binary64 CUDA
+path against the oracle, bit for bit, on the same seeded inputs -- lists with
+spheres on and beyond the walls, energy and gradient, placement, whole runs
+in d = 3 and d = 2, and a seated stage inside walls; the mixed path against
+the oracle within its tolerances (lists exact), whole mixed runs beside the
+binary64 ones, and batches of bounded packings in both precisions.
 """
 import numpy as np
 import pytest
@@ -150,6 +152,127 @@ def test_batch_of_bounded_and_seated_packings_runs_as_solo(rcp):
         return [rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=1, walls=0b111),
                 rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=2, container=1, placement=1),
                 rcp.Packing(np.linspace(0.6, 1.0, 200), box=8.0, seed=4, fixed_d=F, fixed_x=X, placement=1)]
+    solo = make()
+    ref = [p.run() for p in solo]
+    packs = make()
+    b = rcp.Batch(packs)
+    res = b.run()
+    for r, q, p, s in zip(res, ref, packs, solo):
+        assert r.stopped and r.iters == q.iters and r.phi == q.phi and r.kappa_c == q.kappa_c
+        assert np.array_equal(p.positions(), s.positions())
+    b.close()
+    for p in solo + packs:
+        p.close()
+
+
+# ------------------------------------------------------------------ mixed precision
+def _bounded_axes(mask, container, d):
+    cax = list(range(d)) if container == 1 else ([0, 1] if container == 2 else [])
+    return sorted(set([a for a in range(d) if (mask >> a) & 1] + cax))
+
+
+@pytest.mark.parametrize("mask,container,d", [(0b001, 0, 3), (0b111, 0, 3), (0b11, 0, 2),
+                                              (0, 1, 3), (0, 2, 3), (0, 1, 2), (0b100, 2, 3)])
+def test_bounded_list_and_energy_mixed(rcp, orc, term_scale, grad_check, sums_check, kappa_mag, mask, container,
+                                       d):
+    """Walls and the container in mixed precision (each wall a sphere meets is
+    one more term of its row, taken in two-term binary32 from the fixed-point
+    record): the list is the oracle's, E and dE/dkappa within the mixed sums'
+    bound, the gradient element by element within the row-term bound, and
+    the largest overlap within 1e-5 of itself; spheres on and beyond the
+    walls."""
+    n = 3000 if d == 3 else 1500
+    rng = np.random.default_rng(100 + mask + 7 * container + 10 * d)
+    D0 = inputs.lognormal(n, 0.5, 10.0)
+    x = rng.uniform(0.0, 1.0, (n, d))
+    for a in _bounded_axes(mask, container, d):
+        x[:, a] = rng.uniform(-0.01, 1.01, n)
+    wm = (mask, container)
+    p = rcp.Packing(D0, box=1.0, seed=1, d=d, walls=mask, container=container, precision=rcp.RCP_MIXED)
+    with orc.walls(wm):
+        k = orc.kappa0(D0, 1.0, 0.3, d=d)
+        k0 = orc.kappa0(D0, 1.0, 0.05, d=d)
+    p.set_positions(x, k)
+    rp, col = p.neighbors()
+    s0 = _sigma0(orc, D0, k0, p.cfg)
+    orp, ocol = orc.list_brute(x, D0, 1.0, k, p.cfg.skin_s, s0, d=d, wall_mask=wm)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    for mu in (0.0, 0.01):
+        E, g, dk, md = p.energy_grad(mu)
+        oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, mu, d=d, wall_mask=wm)
+        assert omd > 0.0
+        # spheres past a wall give negative kappa terms: the bound takes the
+        # terms' magnitudes
+        sums_check(E, oE, dk, odk, mu, k, D0, what=f"mixed walls {mask} container {container}",
+                   k_mag=kappa_mag(x, D0, 1.0, k, d=d, wall_mask=wm))
+        assert abs(md - omd) <= 1e-5 * omd
+        w = grad_check(g, og, term_scale(x, D0, 1.0, k, d=d, wall_mask=wm),
+                       what=f"mixed walls {mask} container {container}")
+        print(f"walls {mask} container {container} d={d} mu {mu}: worst gradient error / bound {w:.3g}")
+    # positions on bounded axes come back as given, not wrapped (to the
+    # records' resolution)
+    assert np.allclose(p.positions(), x, rtol=0.0, atol=1e-15)
+    p.close()
+
+
+def test_wall_terms_mixed_near_contact(rcp, orc, term_scale, grad_check, sums_check, kappa_mag):
+    """Small overlaps with the walls and between spheres (a relaxed walled
+    packing inflated by 0.2 %): the wall clearance rad - h taken in two-term
+    arithmetic, where a binary32 difference would cancel."""
+    D0 = inputs.lognormal(500, 0.5, 10.0)
+    ref = orc.run(D0, seed=3, walls=0b111)
+    k = ref.kappa_c * 1.002
+    x = ref.x
+    p = rcp.Packing(D0, box=1.0, seed=3, walls=0b111, precision=rcp.RCP_MIXED)
+    p.set_positions(x, k)
+    for mu in (0.0, 0.01):
+        E, g, dk, md = p.energy_grad(mu)
+        oE, og, odk, omd = orc.energy_grad(x, D0, 1.0, k, mu, wall_mask=0b111)
+        assert 5e-4 < omd < 5e-3
+        sums_check(E, oE, dk, odk, mu, k, D0, what="mixed walls near contact",
+                   k_mag=kappa_mag(x, D0, 1.0, k, wall_mask=(0b111, 0)))
+        assert abs(md - omd) <= 1e-5 * omd
+        w = grad_check(g, og, term_scale(x, D0, 1.0, k, wall_mask=(0b111, 0)), what="mixed walls near contact")
+        print(f"mu {mu}: worst gradient error / bound {w:.3g}")
+    p.close()
+
+
+@pytest.mark.parametrize("mask,container,d", [(0b111, 0, 3), (0b11, 0, 2), (0, 1, 3), (0, 2, 3)])
+def test_bounded_run_mixed(rcp, orc, mask, container, d):
+    """A bounded packing in mixed precision to the stop and the shrink: no
+    binary64 overlap with a sphere or a wall at kappa_c, and phi beside the
+    binary64 run's (a whole run is chaotic in the rounding)."""
+    D0 = inputs.lognormal(600, 0.5, 10.0)
+    out = {}
+    for prec in (rcp.RCP_FP64, rcp.RCP_MIXED):
+        p = rcp.Packing(D0, box=1.0, seed=2, d=d, walls=mask, container=container, placement=1, precision=prec)
+        r = p.run()
+        x = p.positions()
+        p.close()
+        assert r.stopped and r.max_delta < 5e-4
+        assert orc.energy_grad(x, D0, 1.0, r.kappa_c, 0.0, d=d, wall_mask=(mask, container))[3] == 0.0
+        out[prec] = r.phi
+    print(f"walls {mask} container {container} d={d}: phi binary64 {out[rcp.RCP_FP64]:.6f}, "
+          f"mixed {out[rcp.RCP_MIXED]:.6f}")
+    assert abs(out[rcp.RCP_MIXED] - out[rcp.RCP_FP64]) < 2e-2
+
+
+def test_batch_of_bounded_and_seated_packings_runs_as_solo_mixed(rcp):
+    """The batched mixed kernel with the wall terms: walled, contained and
+    seated packings stop at the same iteration, kappa_c and phi, at the same
+    positions, as when each runs alone."""
+    g = (np.arange(2) + 0.25) * 4.0
+    X = np.array([[a, b, c] for a in g for b in g for c in g])
+    F = np.full(len(X), 1.6)
+    M = rcp.RCP_MIXED
+
+    def make():
+        return [rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=1, walls=0b111, precision=M),
+                rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=2, container=1, placement=1,
+                            precision=M),
+                rcp.Packing(np.linspace(0.6, 1.0, 200), box=8.0, seed=4, fixed_d=F, fixed_x=X, placement=1,
+                            precision=M),
+                rcp.Packing(inputs.lognormal(400, 0.5, 10.0), box=1.0, seed=3, precision=M)]
     solo = make()
     ref = [p.run() for p in solo]
     packs = make()
