@@ -516,7 +516,7 @@ def main():
         rcp.load()
         clk = Clocks(0)
         res = bench_rows(rcp, torch, large=args.rows_large)
-        print(json.dumps({"metric": "widened rows on the binary64 path (GPU beside the oracle)",
+        print(json.dumps({"metric": "widened rows (GPU beside the oracle; boundaries in both precisions)",
                           "data": "synthetic", **res, "clocks": clk.stop()}))
         return
 
