@@ -500,9 +500,9 @@ rcp_status build(rcp_ctx* h)
 // ---------------------------------------------------------------- evaluation
 unsigned int pair_blocks(const rcp_ctx* h) { return rcp_ceil_div(h->N, RCP_PAIR_THREADS); }
 
-// Partial sums one pair-kernel launch writes: one per block in binary64 mode
-// (canonical trees), one per warp in mixed mode (which also adds the
-// long-row blocks).
+// Blocks of one pair-kernel launch, each writing one partial: the row
+// blocks in binary64 mode (canonical trees), the long-row blocks and the
+// row blocks in mixed mode.
 unsigned int launch_blocks(const rcp_ctx* h)
 {
     if (h->cfg.precision == RCP_MIXED) return pair_blocks(h) + h->c.long_blocks;
