@@ -72,11 +72,11 @@ __global__ void __launch_bounds__(256) k_rho(RcpCtl* ctl, RcpConst c, const doub
 // its margins.  A bounded axis (its record spans [-L/2, 3L/2)) takes
 // fl32(x_a / L_a) of the binary64 coordinate, as k_rho does.  rho_i from
 // D_i^0 exactly as k_rho forms it.
-__device__ __forceinline__ float unit_coord(const MixRec& r, const RcpConst& c, int a)
+__device__ __forceinline__ float unit_coord(const int4& qr, const float4& lr, const RcpConst& c, int a)
 {
-    const int q = a == 0 ? r.q.x : (a == 1 ? r.q.y : r.q.z);
+    const int q = a == 0 ? qr.x : (a == 1 ? qr.y : qr.z);
     if ((c.bounded >> a) & 1) {
-        const float l = a == 0 ? r.l.x : (a == 1 ? r.l.y : r.l.z);
+        const float l = a == 0 ? lr.x : (a == 1 ? lr.y : lr.z);
         return (float)(from_fixed(q, l, c, a) * c.invL[a]);
     }
     return __uint2float_rn((unsigned int)q) * 0x1.0p-32f;
@@ -89,10 +89,13 @@ __global__ void __launch_bounds__(256) k_rho_mixed(RcpCtl* ctl, RcpConst c, cons
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0.0;
     if (i < c.N) {
-        const MixRec rec = (ctl->parity ? rB : rA)[i];
+        // the integer parts alone unless an axis is bounded (half the bytes)
+        const MixRec* R = ctl->parity ? rB : rA;
+        const int4 q = reinterpret_cast<const int4*>(R)[2 * i];
+        const float4 l = c.bounded ? reinterpret_cast<const float4*>(R)[2 * i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
         r = size_at(D0[i], ctl->kappa_b) * (0.5 + c.skin_s) + ctl->sigma0;
         rho[i] = r;
-        xf[i] = make_float4(unit_coord(rec, c, 0), unit_coord(rec, c, 1), unit_coord(rec, c, 2), (float)r);
+        xf[i] = make_float4(unit_coord(q, l, c, 0), unit_coord(q, l, c, 1), unit_coord(q, l, c, 2), (float)r);
     }
     for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r;

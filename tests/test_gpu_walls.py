@@ -284,3 +284,75 @@ def test_batch_of_bounded_and_seated_packings_runs_as_solo_mixed(rcp):
     b.close()
     for p in solo + packs:
         p.close()
+
+
+def test_seated_stage_inside_walls_mixed(rcp, orc):
+    """Frozen spheres inside walls in mixed precision (the kernel with the wall
+    terms, instantiated for frozen spheres too): the frozen spheres keep their
+    positions bit for bit, nothing overlaps in binary64 at kappa_c, and phi
+    lands beside the binary64 stage's."""
+    g = (np.arange(2) + 0.25) * 4.0
+    X = np.array([[a, b, c] for a in g for b in g for c in g])
+    F = np.full(len(X), 1.6)
+    D = np.linspace(0.6, 1.0, 200)
+    out = {}
+    for prec in (rcp.RCP_FP64, rcp.RCP_MIXED):
+        p = rcp.Packing(D, box=8.0, seed=4, fixed_d=F, fixed_x=X, placement=1, walls=0b011, precision=prec)
+        r = p.run()
+        x = p.positions()
+        p.close()
+        assert r.stopped and r.max_delta < 5e-4
+        assert np.array_equal(x[:F.size], X)
+        Dall = np.concatenate([-F, D])
+        assert orc.energy_grad(x, Dall, 8.0, r.kappa_c, 0.0, wall_mask=0b011)[3] == 0.0
+        out[prec] = r.phi
+    print(f"seated inside walls: phi binary64 {out[rcp.RCP_FP64]:.6f}, mixed {out[rcp.RCP_MIXED]:.6f}")
+    assert abs(out[rcp.RCP_MIXED] - out[rcp.RCP_FP64]) < 2e-2
+
+
+def test_seated_stage_in_a_ball_mixed(rcp, orc):
+    """A seated stage inside a ball in mixed precision, from the same frozen
+    configuration as the binary64 stage (class 0 packed in binary64): frozen
+    spheres kept to the records' resolution, no binary64 overlap with a
+    sphere or the wall at kappa_c, and phi beside the binary64 stage's (on
+    eight seeds: within 3e-6 on seven, 3.7e-3 on the eighth, where the two
+    trajectories part)."""
+    p = rcp.Packing(np.full(24, 4.0), box=14.0, seed=5, placement=1, container=1)
+    r0 = p.run()
+    X = p.positions()
+    p.close()
+    F = np.full(24, 4.0 * r0.kappa_c)
+    D1 = np.full(120, 1.0)
+    Dall = np.concatenate([-F, D1])
+    out = {}
+    for prec in (rcp.RCP_FP64, rcp.RCP_MIXED):
+        q = rcp.Packing(D1, box=14.0, seed=6, fixed_d=F, fixed_x=X, placement=1, container=1, precision=prec)
+        r = q.run()
+        x = q.positions()
+        q.close()
+        assert r.stopped and r.max_delta < 5e-4
+        assert np.allclose(x[:F.size], X, rtol=0.0, atol=1e-13)
+        assert orc.energy_grad(x, Dall, 14.0, r.kappa_c, 0.0, wall_mask=(0, 1))[3] == 0.0
+        out[prec] = r.phi
+    print(f"seated in a ball: phi binary64 {out[rcp.RCP_FP64]:.7f}, mixed {out[rcp.RCP_MIXED]:.7f}")
+    assert abs(out[rcp.RCP_MIXED] - out[rcp.RCP_FP64]) < 1e-2
+
+
+def test_cascade_in_a_ball_mixed(rcp, orc):
+    """The two-class cascade inside a ball in mixed precision: three stages,
+    the seated stage denser than the coarse class alone, and the final
+    packing inside the ball without overlap.  Its phi is not compared seed by
+    seed with the binary64 cascade's: with 24 coarse spheres the stage-0
+    configuration decides the seated phi (binary64 over ten seeds: stage 1
+    0.569-0.583), and a mixed stage 0 ends in another configuration of the
+    same ensemble."""
+    D0 = np.concatenate([np.full(24, 4.0), np.full(120, 1.0)])
+    cls = np.concatenate([np.zeros(24, int), np.ones(120, int)])
+    cfg = rcp.rcp_config_default(placement=1, container=1, precision=rcp.RCP_MIXED)
+    x, dm, phi, iters = rcp.rcp_cascade(D0, cls, box=14.0, seed=5, cfg=cfg)
+    print(f"cascade in a ball, mixed: phi {list(phi)}, iterations {list(iters)}")
+    assert len(phi) == 3 and np.all(iters > 0)
+    assert phi[1] > phi[0] + 0.05 and phi[2] >= phi[1] - 1e-3
+    rc = np.sqrt(np.sum((x - 7.0) ** 2, axis=1))
+    assert np.all(rc + 0.5 * dm <= 7.0 * (1.0 + 1e-9))
+    assert orc.energy_grad(x, dm, 14.0, 1.0, 0.0, wall_mask=(0, 1))[3] < 1e-12
