@@ -370,11 +370,16 @@ def bench_rows(rcp, torch, large: bool = False):
     return out
 
 
-def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0):
+def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False):
     """Mixed precision beside binary64, each run to App. A's stopping
     criterion (max delta < 5e-4) and shrunk to contact (Sec. II), per seed:
     final phi, iterations, wall time and the device memory the handle holds
-    (free memory before creation minus free memory after the run)."""
+    (free memory before creation minus free memory after the run).
+
+    perturb: a third run per seed, binary64 again from the same start with
+    one coordinate of one sphere moved by one unit in the last place: how far
+    the protocol itself carries a difference of one rounding to the final
+    phi (dphi_perturbed = its phi less the binary64 run's)."""
     out = {}
     for name in workloads:
         w = WORKLOADS[name]
@@ -396,10 +401,22 @@ def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0):
                             "max_delta": r.max_delta, "device_bytes": int(free0 - free1)}
             if row["mixed"]["stopped"] and row["fp64"]["stopped"]:
                 row["dphi"] = row["mixed"]["phi"] - row["fp64"]["phi"]
+            if perturb:
+                p = rcp.Packing(D0, box=1.0, seed=seed, precision=rcp.RCP_FP64)
+                x = p.positions()
+                x[0, 0] = np.nextafter(x[0, 0], 1.0)
+                p.set_positions(x, p.state()[3].kappa)
+                r = p.run(max_seconds=max_fp64_s)
+                p.close()
+                row["fp64_perturbed"] = {"phi": r.phi, "stopped": r.stopped, "iters": r.iters}
+                if r.stopped and row["fp64"]["stopped"]:
+                    row["dphi_perturbed"] = r.phi - row["fp64"]["phi"]
             rows.append(row)
             print(json.dumps({"workload": name, **row}), file=sys.stderr, flush=True)
         d = [r["dphi"] for r in rows if "dphi" in r]
+        dp = [r["dphi_perturbed"] for r in rows if "dphi_perturbed" in r]
         out[name] = {"runs": rows, "mean_dphi": float(np.mean(d)) if d else None,
+                     "mean_abs_dphi_perturbed": float(np.mean(np.abs(dp))) if dp else None,
                      "mean_abs_dphi": float(np.mean(np.abs(d))) if d else None,
                      "max_abs_dphi": float(np.max(np.abs(d))) if d else None,
                      "seed_scatter_fp64": float(np.std([r["fp64"]["phi"] for r in rows], ddof=1))
@@ -495,6 +512,8 @@ def main():
     ap.add_argument("--phi-parity", default="",
                     help="comma-separated workloads: mixed beside binary64 runs to the stop; one JSON line")
     ap.add_argument("--phi-seeds", default="0,1,2,3,4")
+    ap.add_argument("--phi-perturb", action="store_true",
+                    help="with --phi-parity: also binary64 from the same start moved by one ulp")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -506,7 +525,8 @@ def main():
         from paper_2608_12235_b300 import rcp
         rcp.load()
         clk = Clocks(0)
-        res = phi_parity(rcp, torch, args.phi_parity.split(","), [int(v) for v in args.phi_seeds.split(",")])
+        res = phi_parity(rcp, torch, args.phi_parity.split(","), [int(v) for v in args.phi_seeds.split(",")],
+                         perturb=args.phi_perturb)
         print(json.dumps({"metric": "final phi, mixed precision beside binary64, runs to the stopping criterion",
                           "data": "synthetic", **res, "clocks": clk.stop()}))
         return
