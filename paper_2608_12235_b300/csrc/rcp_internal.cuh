@@ -127,7 +127,9 @@ struct RcpConst {
 // Pair record of one sphere: 32-bit fixed-point position q_a = floor(x_a/L_a
 // 2^32) (integer subtraction wraps, which is exactly the minimum image), the
 // binary32 remainder l_a = x_a/L_a 2^32 - q_a in [0, 1), and D_i^0 as an
-// unevaluated binary32 sum.  One 32-byte sector per gather; the first 16
+// unevaluated binary32 sum.  A bounded axis (flat walls or the container's)
+// records (x_a + L_a/2) / (2 L_a) instead, so the plain difference of two
+// listed spheres never wraps.  One 32-byte sector per gather; the first 16
 // bytes (integer position and fl32(D_i^0)) are all the pre-test reads.
 struct __align__(32) MixRec {
     int4 q;    // qx, qy, qz, and the bits of fl32(D_i^0)

@@ -7,7 +7,10 @@
 // the wrap-around of 32-bit integer arithmetic: the minimum-image separation
 // of a pair is (q_i - q_j) as a signed 32-bit integer plus (l_i - l_j),
 // exactly formed to binary32 relative precision at any scale (from the largest
-// spheres down to D_max / 5e5).  Distance, overlap and the pair terms are
+// spheres down to D_max / 5e5).  An axis bounded by flat walls or the
+// container records [-L/2, 3L/2) instead (no wrap; spheres past a wall stay
+// representable), and the wall terms take the record's position as a
+// two-term binary32 sum.  Distance, overlap and the pair terms are
 // binary32; each row sums them with a compensated (2Sum) accumulation; block
 // and global sums are widened to binary64; the Adam moments are binary32 and
 // the position update adds the step to the fixed-point record, carrying the
