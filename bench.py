@@ -370,7 +370,7 @@ def bench_rows(rcp, torch, large: bool = False):
     return out
 
 
-def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False):
+def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False, bounds=None):
     """Mixed precision beside binary64, each run to App. A's stopping
     criterion (max delta < 5e-4) and shrunk to contact (Sec. II), per seed:
     final phi, iterations, wall time and the device memory the handle holds
@@ -379,7 +379,11 @@ def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False):
     perturb: a third run per seed, binary64 again from the same start with
     one coordinate of one sphere moved by one unit in the last place: how far
     the protocol itself carries a difference of one rounding to the final
-    phi (dphi_perturbed = its phi less the binary64 run's)."""
+    phi (dphi_perturbed = its phi less the binary64 run's).
+
+    bounds: rcp_config keys of a bounded box (walls, container, placement)
+    for every run."""
+    bounds = bounds or {}
     out = {}
     for name in workloads:
         w = WORKLOADS[name]
@@ -390,7 +394,7 @@ def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False):
             for prec, tag in ((rcp.RCP_MIXED, "mixed"), (rcp.RCP_FP64, "fp64")):
                 torch.cuda.synchronize()
                 free0 = torch.cuda.mem_get_info()[0]
-                p = rcp.Packing(D0, box=1.0, seed=seed, precision=prec)
+                p = rcp.Packing(D0, box=1.0, seed=seed, precision=prec, **bounds)
                 t0 = time.perf_counter()
                 r = p.run(max_seconds=max_fp64_s if (tag == "fp64" and max_fp64_s > 0) else 0.0)
                 dt = time.perf_counter() - t0
@@ -402,7 +406,7 @@ def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False):
             if row["mixed"]["stopped"] and row["fp64"]["stopped"]:
                 row["dphi"] = row["mixed"]["phi"] - row["fp64"]["phi"]
             if perturb:
-                p = rcp.Packing(D0, box=1.0, seed=seed, precision=rcp.RCP_FP64)
+                p = rcp.Packing(D0, box=1.0, seed=seed, precision=rcp.RCP_FP64, **bounds)
                 x = p.positions()
                 x[0, 0] = np.nextafter(x[0, 0], 1.0)
                 p.set_positions(x, p.state()[3].kappa)
@@ -424,13 +428,26 @@ def phi_parity(rcp, torch, workloads, seeds, max_fp64_s=0.0, perturb=False):
     return out
 
 
+def bounds_of(args):
+    """rcp_config keys of the bounded box --walls / --container ask for (a
+    container starts from the non-overlapping placement, App. A)."""
+    b = {}
+    if args.walls:
+        b["walls"] = args.walls
+    if args.container:
+        b["container"] = args.container
+        b["placement"] = 1
+    return b
+
+
 def profile_window(args, w):
     """A bounded window of the workload for ncu (--profile-from-start off)."""
     import torch
     from paper_2608_12235_b300 import rcp
     rcp.load()
     D0 = diameters(w)
-    p = rcp.Packing(D0, box=1.0, seed=0, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs, skin_s=args.skin_s)
+    p = rcp.Packing(D0, box=1.0, seed=0, precision=rcp.RCP_MIXED, skin_abs=args.skin_abs, skin_s=args.skin_s,
+                    **bounds_of(args))
     r = p.run(max_iters=args.densify, shrink=False)
     rcp.rcp_build_neighbors(p.h)
     listed = int(p.neighbors()[1].size)   # entries of the list the window walks
@@ -446,7 +463,11 @@ def profile_window(args, w):
         rcp.rcp_profile(p.h, 100)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print(f"window done: iters={r.iters} listed entries={listed}")
+    # the same class of state timed live after the window (CUDA events,
+    # iterations launched one by one): the pair kernel's ms per launch
+    ms_pair, _, n_pair = rcp.rcp_profile(p.h, 20)
+    print(f"window done: iters={r.iters} listed entries={listed} "
+          f"pair kernel {ms_pair / max(n_pair, 1):.4f} ms per launch after it")
     p.close()
 
 
@@ -512,6 +533,10 @@ def main():
     ap.add_argument("--phi-parity", default="",
                     help="comma-separated workloads: mixed beside binary64 runs to the stop; one JSON line")
     ap.add_argument("--phi-seeds", default="0,1,2,3,4")
+    ap.add_argument("--walls", type=int, default=0,
+                    help="with --phi-parity or --profile-window: flat walls on the axes of this bit mask")
+    ap.add_argument("--container", type=int, default=0,
+                    help="with --phi-parity or --profile-window: 1 ball, 2 cylinder about z")
     ap.add_argument("--phi-perturb", action="store_true",
                     help="with --phi-parity: also binary64 from the same start moved by one ulp")
     args = ap.parse_args()
@@ -526,9 +551,9 @@ def main():
         rcp.load()
         clk = Clocks(0)
         res = phi_parity(rcp, torch, args.phi_parity.split(","), [int(v) for v in args.phi_seeds.split(",")],
-                         perturb=args.phi_perturb)
+                         perturb=args.phi_perturb, bounds=bounds_of(args))
         print(json.dumps({"metric": "final phi, mixed precision beside binary64, runs to the stopping criterion",
-                          "data": "synthetic", **res, "clocks": clk.stop()}))
+                          "data": "synthetic", "bounds": bounds_of(args), **res, "clocks": clk.stop()}))
         return
     if args.rows:
         import torch

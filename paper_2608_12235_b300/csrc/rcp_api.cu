@@ -944,6 +944,7 @@ rcp_status create_impl(const double* fixed_d, const double* fixed_x, long long N
     c.Rc = INFINITY;
     for (int a = 0; a < d; ++a)
         if (((c.caxes >> a) & 1) && 0.5 * box[a] < c.Rc) c.Rc = 0.5 * box[a];
+    c.wmargin = (float)(c.Lmax * 0x1.0p-20);
     c.Rc_hi = std::isfinite(c.Rc) ? (float)c.Rc : 0.0f;
     c.Rc_lo = std::isfinite(c.Rc) ? (float)(c.Rc - (double)c.Rc_hi) : 0.0f;
     if (c.container == 1) c.Vs = d == 2 ? (RCP_PI * c.Rc) * c.Rc : (((4.0 / 3.0) * RCP_PI) * ((c.Rc * c.Rc) * c.Rc));

@@ -121,6 +121,7 @@ struct RcpConst {
     int bounded;               // axes without minimum image or wrap: flat walls and the container's
     double Rc;                 // container radius: min L_a / 2 over its axes (centre L / 2)
     float Rc_hi, Rc_lo;        // Rc as an unevaluated binary32 sum (mixed wall terms)
+    float wmargin;             // 2^-20 max_a L_a: absolute margin of the mixed wall pre-test
     double Vs;                 // volume the spheres fill (kappa_0, phi): the container's, else V
 };
 

@@ -446,6 +446,11 @@ __device__ __forceinline__ bool wall_contact(float hh, float hl, float rh, float
 // -(x_a - c_a) / |x - c|).  Positions, clearances and distances in two-term
 // binary32, so a contact within 1e-8 of the radius still resolves.  A frozen
 // row takes the energy and the overlap but no force and no kappa term.
+// A pre-test on the integer parts alone skips the two-term work of a sphere
+// that clears every wall: x_a ~ fl32(q_a) qscale_a + qoff_a is within a few
+// 2^-24 L_a of the coordinate (the conversion of q_a keeps 24 bits, the
+// remainder is below one unit), so a clearance above rad + 2^-20 L_a
+// (c.wmargin) is certain.
 template <bool FZ>
 __device__ __forceinline__ void wall_terms32(const RcpConst& c, const MixScalars& S, const MixRec& ri, float& g0,
                                              float& c0, float& g1, float& c1, float& g2, float& c2, float& es,
@@ -459,8 +464,12 @@ __device__ __forceinline__ void wall_terms32(const RcpConst& c, const MixScalars
     rl *= 0.5f;
     const int qa[3] = {ri.q.x, ri.q.y, ri.q.z};
     const float la[3] = {ri.l.x, ri.l.y, ri.l.z};
+    float xc[3];
+    for (int a = 0; a < 3; ++a)
+        xc[a] = __fmaf_rn(__uint2float_rn((unsigned int)qa[a]), c.qscale[a], c.qo_hi[a]);
     for (int a = 0; a < 3; ++a) {
         if (!((c.walls >> a) & 1)) continue;
+        if (fminf(xc[a], c.Lf[a] - xc[a]) > rh + c.wmargin) continue;   // clears both walls of the axis
         float xh, xl;
         rec_pos2(qa[a], la[a], c, a, xh, xl);
         float& g = a == 0 ? g0 : (a == 1 ? g1 : g2);
@@ -473,6 +482,14 @@ __device__ __forceinline__ void wall_terms32(const RcpConst& c, const MixScalars
             acc2(g, gc, f);
     }
     if (c.container) {
+        float q2 = 0.0f;
+        for (int a = 0; a < 3; ++a)
+            if ((c.caxes >> a) & 1) {
+                const float o = xc[a] - 0.5f * c.Lf[a];
+                q2 = __fmaf_rn(o, o, q2);
+            }
+        const float clear = c.Rc_hi - rh - c.wmargin;   // certainly inside the ball / cylinder
+        if (clear > 0.0f && q2 < clear * clear * (1.0f - 1e-5f)) return;
         float oh[3] = {0.f, 0.f, 0.f};
         float d2h = 0.0f, d2l = 0.0f;
         for (int a = 0; a < 3; ++a) {
