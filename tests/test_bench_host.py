@@ -70,3 +70,14 @@ def test_oracle_leg_loads_nothing_of_the_cuda_library():
         "print('ok')\n")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr
+
+
+def test_bounded_box_options_map_to_the_configuration():
+    """--walls / --container become rcp_config keys; a container starts from
+    the non-overlapping placement (a uniform draw leaves spheres outside)."""
+    import bench
+    assert bench.bounds_of(types.SimpleNamespace(walls=0, container=0)) == {}
+    assert bench.bounds_of(types.SimpleNamespace(walls=7, container=0)) == {"walls": 7}
+    assert bench.bounds_of(types.SimpleNamespace(walls=0, container=1)) == {"container": 1, "placement": 1}
+    assert bench.bounds_of(types.SimpleNamespace(walls=4, container=2)) == {"walls": 4, "container": 2,
+                                                                             "placement": 1}
